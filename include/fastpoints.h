@@ -1,0 +1,218 @@
+/*
+ * fastpoints.h -- C ABI of the GB300 (sm_103a) octree-construction library.
+ *
+ * The library builds, on one GPU, the structure FastPoints (arxiv 2302.05002)
+ * needs before it can render a large unprocessed cloud: an immediate decimated
+ * preview (Sec. 3, Sec. 4.2) and a shallow level-of-detail octree built by the
+ * chunk -> index -> stitch method the paper adopts (Sec. 2.2, Sec. 4.4,
+ * Fig. "octree").  The calls follow those stages:
+ *
+ *   fp_bounds              cube of the cloud                    (Sec. 4.4, extent)
+ *   fp_decimate            hash-uniform preview                 (Sec. 3, Sec. 4.2)
+ *   fp_count               points per cell of the 2^g grid      (Sec. 4.4, "sorted into chunks")
+ *   fp_merge_chunks        cells merged into chunks under T     (Fig. "octree": chunk = node of the tree)
+ *   fp_distribute          stable scatter of points into chunks (Sec. 4.4, Fig. "octree")
+ *   fp_build_chunk_octree  local octrees of all chunks, stitched,
+ *                          and the LOD node that keeps each point (Sec. 4.4, Abstract "shallow octree")
+ *   fp_subsample           final LOD layout of the points        (Sec. 4.4, "stitched into a global octree")
+ *
+ * Conventions (all calls):
+ *   - Every pointer named d_* is device memory owned by the caller; h_* is host
+ *     memory.  The library never allocates device memory: scratch space is the
+ *     caller's workspace (d_ws, ws_bytes), sized by fp_workspace_size().
+ *     Workspace contents need not be initialised and are not preserved.
+ *   - Calls are asynchronous on `stream` and never synchronise the host.
+ *     Counts produced on the device (number of chunks, nodes, preview points)
+ *     are written to device memory.
+ *   - Argument errors are detected on the host and returned at once; nothing is
+ *     enqueued then.  Errors found on the device (an output capacity exceeded,
+ *     a bounded wait that ran out) are OR-ed into a sticky per-device error word
+ *     read with fp_get_device_error(); the affected outputs are then undefined.
+ *   - n == 0 is valid and gives empty outputs.
+ *   - Limits: n < 2^30; 1 <= grid_log2 <= 7; grid_log2 <= sub_log2;
+ *     grid_log2 <= max_level; max_level + sub_log2 <= 22;
+ *     1 <= node_capacity <= chunk_threshold; decim_modulus >= 1.
+ *   - Point records must be 16-byte aligned.
+ *   - Every kernel is CUDA for sm_103a; there is no CPU fallback.  Without a
+ *     usable device the calls return FP_ERR_CUDA.
+ *
+ * Outputs are exact (integer arithmetic only) and identical from run to run.
+ */
+#ifndef FASTPOINTS_H
+#define FASTPOINTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cudaStream_t;
+
+/* One point: integer position and 8-bit colour, 16 bytes. */
+typedef struct { int32_t x, y, z; uint8_t r, g, b, a; } fp_point;
+
+/* Bounding cube: origin o = per-axis minimum, mx = per-axis maximum,
+ * side S = max_a(mx_a - o_a) + 1 (1 <= S <= 2^32; S == 0 for an empty cloud). */
+typedef struct { int32_t o[3]; int32_t mx[3]; uint64_t S; } fp_cube;
+
+/* A chunk: node (level, Morton key at that level) of the count grid with its
+ * number of points. */
+typedef struct { uint64_t key; uint32_t count; uint32_t level; } fp_chunk;
+
+/* A node of the octree, nodes stored in preorder (parent first, children in
+ * Morton digit order).  Node i's subtree is nodes [i, i + n_desc].
+ *   key        Morton key of the node's cell at `level` (3*level bits)
+ *   first      start of the points the node keeps, in the final array
+ *   leaf_first start of the subtree's points in the leaf-grouped array
+ *   count      points in the subtree
+ *   n_own      points the node keeps after LOD subsampling
+ *   child_mask bit c set iff child with digit c exists (x bit = 4, y = 2, z = 1) */
+typedef struct {
+    uint64_t key, first, leaf_first;
+    uint32_t count, n_own, n_desc;
+    uint8_t level, child_mask, is_leaf, pad;
+} fp_node;
+
+/* Build parameters.
+ *   grid_log2       g: count grid of 2^g cells per axis (the paper's chunking grid)
+ *   sub_log2        s: an inner node at level L keeps one point per occupied
+ *                   cell of the level-(L+s) grid (2^s cells per axis per node)
+ *   max_level       deepest node level (root = 0)
+ *   decim_modulus   preview keeps index i iff splitmix64(i) % decim_modulus == 0
+ *   chunk_threshold T: most points in a chunk, unless it is one finest cell
+ *   node_capacity   C: a node with more than C points is split (below max_level) */
+typedef struct {
+    uint32_t grid_log2, sub_log2, max_level, decim_modulus;
+    uint64_t chunk_threshold, node_capacity;
+} fp_params;
+
+typedef enum {
+    FP_OK = 0,
+    FP_ERR_INVALID = 1,      /* a null pointer where one is required, or bad parameters */
+    FP_ERR_ALIGN = 2,        /* a point array is not 16-byte aligned */
+    FP_ERR_TOO_LARGE = 3,    /* n >= 2^30 */
+    FP_ERR_NOMEM = 4,        /* reserved for callers' allocators */
+    FP_ERR_WORKSPACE = 5,    /* ws_bytes smaller than fp_workspace_size() */
+    FP_ERR_TIMEOUT = 6,      /* device word: a bounded inter-block wait ran out */
+    FP_ERR_CUDA = 7,         /* a CUDA call failed (no device, launch error) */
+    FP_ERR_UNSUPPORTED = 8,  /* parameters outside the limits above */
+    FP_ERR_CAPACITY = 9      /* device word: an output array was too small */
+} fp_status;
+
+typedef enum {
+    FP_STAGE_BOUNDS = 0,
+    FP_STAGE_DECIMATE = 1,
+    FP_STAGE_BOUNDS_DECIMATE = 2,
+    FP_STAGE_COUNT = 3,
+    FP_STAGE_MERGE = 4,
+    FP_STAGE_DISTRIBUTE = 5,
+    FP_STAGE_OCTREE = 6,
+    FP_STAGE_SUBSAMPLE = 7
+} fp_stage;
+
+/* Bytes of workspace a stage needs for n points with these parameters
+ * (prm may be NULL for the stages before the octree).  For FP_STAGE_SUBSAMPLE
+ * the size assumes node_cap == fp_node_capacity_bound(n, prm). */
+size_t fp_workspace_size(fp_stage stage, uint64_t n, const fp_params* prm);
+
+/* An upper bound on the number of octree nodes of any cloud of n points under
+ * these parameters: a node_cap for fp_build_chunk_octree / fp_subsample that can
+ * never overflow (0 for invalid parameters). */
+uint32_t fp_node_capacity_bound(uint64_t n, const fp_params* prm);
+
+const char* fp_status_string(fp_status s);
+
+/* Sticky device error word of the current device (bits (1u << status)); the
+ * call synchronises `stream` and clears the word when `clear` is nonzero. */
+fp_status fp_get_device_error(cudaStream_t stream, uint32_t* h_bits, int clear);
+
+/* Cube of d_pts[0..n): per-axis min and max, S = largest extent + 1 (Sec. 4.4:
+ * the converter first needs the extent of the cloud).  d_cube: one record. */
+fp_status fp_bounds(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
+                    void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Preview (Sec. 3 "uniformly downsampling", Sec. 4.2): keeps d_pts[i] iff
+ * splitmix64(first_index + i) % modulus == 0, where splitmix64(v) is the first
+ * output of a splitmix64 generator seeded with v; the kept points are written to
+ * d_out in ascending i and their number to *d_out_count.  Points beyond out_cap
+ * are not written (FP_ERR_CAPACITY in the device word).  first_index lets a
+ * cloud streamed in pieces keep its global indices. */
+fp_status fp_decimate(const fp_point* d_pts, uint64_t n, uint64_t first_index, uint32_t modulus,
+                      fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
+                      void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* fp_bounds and fp_decimate in one pass over the points (one read of the cloud). */
+fp_status fp_bounds_decimate(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
+                             uint64_t first_index, uint32_t modulus,
+                             fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
+                             void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Count grid (Sec. 4.4, the first step of sorting points into chunks):
+ * d_counts[m] = number of points whose level-g cell has Morton key m, where the
+ * cell of axis a is floor((p_a - o_a) * 2^g / S) in exact integer arithmetic and
+ * the Morton key takes one bit per axis per level, x most significant.
+ * d_counts has 8^g entries; it is zeroed first unless `accumulate` is nonzero
+ * (pieces of one cloud, all with the same cube). */
+fp_status fp_count(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uint32_t grid_log2,
+                   uint32_t* d_counts, int accumulate,
+                   void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Chunks (Fig. "octree": each chunk is a node of the global tree): sums the count
+ * grid up to the root; a chunk is a node with 0 < count <= threshold whose parent
+ * holds more than threshold points (or the root itself), or a level-g cell holding
+ * more than threshold points.  Chunks are listed in Morton preorder in d_chunks
+ * (capacity 8^g), their number in *d_num_chunks, d_lut[m] = chunk of cell m
+ * (0xFFFFFFFF for empty cells, 8^g entries), d_offsets[0..K] = exclusive prefix
+ * sums of the chunk counts (capacity 8^g + 1). */
+fp_status fp_merge_chunks(const uint32_t* d_counts, uint32_t grid_log2, uint64_t threshold,
+                          fp_chunk* d_chunks, uint32_t* d_num_chunks, uint32_t* d_lut, uint64_t* d_offsets,
+                          void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Stable scatter into chunks (Sec. 4.4 "sorted into a number of chunks"):
+ * d_out[d_offsets[c] + r] = d_pts[i] where c is the chunk of point i and r the
+ * number of points of chunk c with an index below i; d_perm (nullable) receives
+ * i at the same position.  d_out must not alias d_pts. */
+fp_status fp_distribute(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uint32_t grid_log2,
+                        const uint32_t* d_lut, const uint64_t* d_offsets, const uint32_t* d_num_chunks,
+                        fp_point* d_out, uint32_t* d_perm,
+                        void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Local octrees of all chunks, stitched under the global nodes above them
+ * (Sec. 4.4, Fig. "octree"), and the level-of-detail selection.
+ * Input: the output of fp_distribute (d_sorted, d_perm) and of the earlier stages.
+ * Hierarchy: a node at level L exists iff it holds a point and (L == 0 or its
+ * parent holds more than node_capacity points and lies above max_level); it is
+ * a leaf iff it holds at most node_capacity points or L == max_level.
+ * Outputs:
+ *   d_nodes[0..M), *d_num_nodes = M (nodes beyond node_cap are not written,
+ *     FP_ERR_CAPACITY); every field but `first` is filled;
+ *   d_leaf_pts / d_leaf_perm (n each, nullable): points grouped by leaf, leaves
+ *     in preorder, ascending original index inside a leaf;
+ *   d_owner[j] (n, u32): node that keeps distributed point j after LOD
+ *     subsampling -- an inner node at level L keeps, of every occupied
+ *     level-(L + sub_log2) cell, the point with the smallest original index
+ *     among its children's remaining points (deepest nodes first); a point not
+ *     taken by any ancestor stays in its leaf. */
+fp_status fp_build_chunk_octree(const fp_point* d_sorted, const uint32_t* d_perm, uint64_t n,
+                                const fp_cube* d_cube, const fp_chunk* d_chunks, const uint32_t* d_num_chunks,
+                                const uint64_t* d_offsets, const uint32_t* d_counts, const fp_params* h_prm,
+                                fp_node* d_nodes, uint32_t node_cap, uint32_t* d_num_nodes,
+                                fp_point* d_leaf_pts, uint32_t* d_leaf_perm, uint32_t* d_owner,
+                                void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Final level-of-detail layout: nodes in preorder, each node's kept points in
+ * ascending original index (points kept by nodes above the chunks are merged
+ * across chunks: the stitch).  Fills d_nodes[*].first and writes d_final /
+ * d_final_perm (n each).  node_cap <= 2^23; the workspace is sized for this
+ * node_cap (fp_workspace_size(FP_STAGE_SUBSAMPLE) assumes the bound above). */
+fp_status fp_subsample(fp_node* d_nodes, const uint32_t* d_num_nodes, uint32_t node_cap,
+                       const fp_point* d_sorted, const uint32_t* d_perm, const uint32_t* d_owner, uint64_t n,
+                       fp_point* d_final, uint32_t* d_final_perm,
+                       void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,148 @@
+// fp_common.cuh -- device helpers shared by the kernels of libfastpoints.
+//
+// Cell arithmetic (paper Sec. 4.4; exact-integer reading): for axis a,
+//   c_a(l) = floor((p_a - o_a) * 2^l / S),   0 <= p_a - o_a < 2^32,  1 <= S <= 2^32.
+// It is evaluated once at l = 21 and shifted for coarser levels (floor of a
+// floor: c(l) = c(21) >> (21 - l)).  The level-21 quotient is first estimated in
+// fp32 (relative error < 2^-22, so the estimate is within 1 of the true floor
+// for quotients below 2^21) and then corrected exactly with one 64-bit
+// remainder test.  The Morton key interleaves one bit per axis per level with
+// the x bit most significant inside every 3-bit digit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/fastpoints.h"
+
+#define FP_DEV __device__ __forceinline__
+
+namespace fp {
+
+constexpr int kKeyLevels = 21;          // deepest level of the 63-bit key
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// Sticky per-device error word (passed to every kernel); bit (1u << fp_status)
+// marks each kind of fault.
+FP_DEV void raise(uint32_t* err, fp_status s) { atomicOr(err, 1u << (unsigned)s); }
+
+// ------------------------------------------------------------------ cube
+struct CubeDev {
+    int32_t o[3];
+    uint64_t S;
+    float scale21;   // 2^21 / S in fp32
+};
+
+FP_DEV CubeDev load_cube(const fp_cube* c)
+{
+    CubeDev d;
+    d.o[0] = c->o[0]; d.o[1] = c->o[1]; d.o[2] = c->o[2];
+    d.S = c->S;
+    d.scale21 = d.S ? 2097152.0f / (float)d.S : 0.f;
+    return d;
+}
+
+// floor(d * 2^21 / S) for 0 <= d < S <= 2^32
+FP_DEV uint32_t cell21(int32_t p, int32_t o, uint64_t S, float scale21)
+{
+    uint64_t d = (uint64_t)((int64_t)p - (int64_t)o);
+    int32_t q = (int32_t)((float)d * scale21);
+    if (q < 0) q = 0;
+    int64_t r = (int64_t)(d << 21) - (int64_t)q * (int64_t)S;
+    if (r < 0) --q;
+    else if (r >= (int64_t)S) ++q;
+    return (uint32_t)q;
+}
+
+FP_DEV uint64_t spread3(uint32_t v)   // 21 bits -> bits 0, 3, 6, ...
+{
+    uint64_t x = v & 0x1FFFFFu;
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// 63-bit Morton key of the level-21 cell of a point
+FP_DEV uint64_t key21(int32_t x, int32_t y, int32_t z, const CubeDev& c)
+{
+    uint32_t cx = cell21(x, c.o[0], c.S, c.scale21);
+    uint32_t cy = cell21(y, c.o[1], c.S, c.scale21);
+    uint32_t cz = cell21(z, c.o[2], c.S, c.scale21);
+    return (spread3(cx) << 2) | (spread3(cy) << 1) | spread3(cz);
+}
+
+FP_DEV uint64_t key_at(uint64_t k21, int level) { return k21 >> (3 * (kKeyLevels - level)); }
+
+// level of the deepest cell two level-21 keys share (-1: not even the root? no: >= 0)
+FP_DEV int common_level(uint64_t a, uint64_t b)
+{
+    uint64_t x = a ^ b;
+    if (x == 0) return kKeyLevels;
+    int lz = __clzll((long long)x) - 1;   // bit 63 is always 0
+    return lz / 3;
+}
+
+// ------------------------------------------------------------------ hash
+// first output of a splitmix64 generator seeded with v (Steele, Lea, Flood 2014)
+FP_DEV uint64_t splitmix64(uint64_t v)
+{
+    uint64_t z = v + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------------ memory
+FP_DEV int4 ld_point(const fp_point* p, uint64_t i) { return __ldg(reinterpret_cast<const int4*>(p) + i); }
+FP_DEV int4 ld_point_cs(const fp_point* p, uint64_t i)
+{
+    return __ldcs(reinterpret_cast<const int4*>(p) + i);
+}
+FP_DEV void st_point(fp_point* p, uint64_t i, int4 v) { reinterpret_cast<int4*>(p)[i] = v; }
+
+FP_DEV uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// volatile load for inter-block flags
+FP_DEV uint32_t ld_volatile(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+FP_DEV uint64_t ld_volatile64(const uint64_t* p) { return *(const volatile uint64_t*)p; }
+
+// ------------------------------------------------------------------ block scan
+// Exclusive scan of one value per thread over a block of NT threads (NT % 32 == 0).
+template <int NT, typename T>
+FP_DEV T block_exclusive_scan(T v, T* smem_warp /* NT/32 entries */, T& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < NT / 32 ? smem_warp[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) smem_warp[lane] = w;
+    }
+    __syncthreads();
+    total = smem_warp[NT / 32 - 1];
+    T before = warp ? smem_warp[warp - 1] : T(0);
+    __syncthreads();
+    return before + x - v;
+}
+
+// Bounded spin: number of polls before an inter-block wait gives up.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+}  // namespace fp

@@ -1,0 +1,385 @@
+// fp_core.cu -- bounds, preview decimation, count grid and chunk merge.
+//
+//   k_bounds_decimate  one pass over the cloud: per-axis min/max (Sec. 4.4) and,
+//                      optionally, the preview compaction (Sec. 3 / Sec. 4.2):
+//                      index i is kept iff splitmix64(first + i) % m == 0.  Kept
+//                      points keep ascending index order through a single-pass
+//                      scan with decoupled look-back across tiles.
+//   k_count            count grid: one level-g Morton key per point, warp-
+//                      aggregated atomics into an L2-resident 8^g histogram.
+//   k_pyramid / k_chunk_mark / k_chunk_write
+//                      bottom-up sums of the grid and the chunk rule of Fig.
+//                      "octree" (maximal nodes with 0 < count <= T, plus
+//                      overflowing finest cells), listed in Morton preorder.
+#include "fp_internal.cuh"
+
+namespace fp {
+
+// ----------------------------------------------------------------- bounds
+constexpr int kBdNT = 256;
+constexpr int kBdIPT = 16;
+constexpr int kBdTile = kBdNT * kBdIPT;   // 4096 points per tile
+
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagInc = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+
+template <bool BOUNDS, bool DECIM>
+__global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __restrict__ pts, uint64_t n,
+                                                           uint64_t first, uint32_t modulus, fp_point* __restrict__ out,
+                                                           uint64_t out_cap, uint64_t* __restrict__ out_count,
+                                                           int32_t* __restrict__ partial, uint64_t* tile_status,
+                                                           uint32_t* tile_counter, uint64_t ntiles, uint32_t* err)
+{
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_cnt[kBdIPT][kBdNT / 32];
+    __shared__ uint64_t s_base;
+    __shared__ int32_t s_red[6][kBdNT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool pow2 = (modulus & (modulus - 1)) == 0;
+    const uint64_t mmask = (uint64_t)modulus - 1;
+
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
+    int32_t hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        __syncthreads();
+        if (tile >= ntiles) break;
+        const uint64_t base = tile * kBdTile;
+
+        uint32_t keepmask = 0;   // bit r: item r of this thread kept
+        if (DECIM) {
+            // the keep decision depends on the index only: count first, publish early
+#pragma unroll
+            for (int r = 0; r < kBdIPT; ++r) {
+                uint64_t i = base + (uint64_t)r * kBdNT + threadIdx.x;
+                bool k = false;
+                if (i < n) {
+                    uint64_t h = splitmix64(first + i);
+                    k = pow2 ? (h & mmask) == 0 : (h % modulus) == 0;
+                }
+                uint32_t bal = __ballot_sync(0xFFFFFFFFu, k);
+                if (lane == 0) s_cnt[r][warp] = __popc(bal);
+                keepmask |= (uint32_t)k << r;
+            }
+            __syncthreads();
+            // exclusive scan over (r, warp) order = index order
+            if (threadIdx.x < 32) {
+                uint32_t v[kBdIPT * (kBdNT / 32) / 32];   // 4 entries per lane
+                uint32_t s = 0;
+                constexpr int per = kBdIPT * (kBdNT / 32) / 32;
+#pragma unroll
+                for (int q = 0; q < per; ++q) {
+                    int e = lane * per + q;
+                    v[q] = s_cnt[e / (kBdNT / 32)][e % (kBdNT / 32)];
+                    s += v[q];
+                }
+                uint32_t x = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                    if (lane >= o) x += y;
+                }
+                uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+                uint32_t ex = x - s;
+#pragma unroll
+                for (int q = 0; q < per; ++q) {
+                    int e = lane * per + q;
+                    s_cnt[e / (kBdNT / 32)][e % (kBdNT / 32)] = ex;
+                    ex += v[q];
+                }
+                // decoupled look-back for the tile's global offset
+                if (lane == 0) {
+                    uint64_t excl = 0;
+                    if (tile == 0) {
+                        atomicExch((unsigned long long*)&tile_status[0], (unsigned long long)(kFlagInc | total));
+                    } else {
+                        atomicExch((unsigned long long*)&tile_status[tile], (unsigned long long)(kFlagAgg | total));
+                        int64_t t = (int64_t)tile - 1;
+                        uint32_t spins = 0;
+                        while (t >= 0) {
+                            uint64_t s2 = ld_volatile64(&tile_status[t]);
+                            if ((s2 >> 62) == 0) {
+                                if (++spins > kSpinLimit) { raise(err, FP_ERR_TIMEOUT); break; }
+                                continue;
+                            }
+                            excl += s2 & kValMask;
+                            if ((s2 >> 62) == 2) break;
+                            --t;
+                        }
+                        atomicExch((unsigned long long*)&tile_status[tile],
+                                   (unsigned long long)(kFlagInc | (excl + total)));
+                    }
+                    s_base = excl;
+                    if (tile == ntiles - 1) {
+                        *out_count = excl + total;
+                        if (excl + total > out_cap) raise(err, FP_ERR_CAPACITY);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        if (BOUNDS) {
+#pragma unroll 4
+            for (int r = 0; r < kBdIPT; ++r) {
+                uint64_t i = base + (uint64_t)r * kBdNT + threadIdx.x;
+                if (i < n) {
+                    int4 p = ld_point_cs(pts, i);
+                    lo[0] = min(lo[0], p.x); hi[0] = max(hi[0], p.x);
+                    lo[1] = min(lo[1], p.y); hi[1] = max(hi[1], p.y);
+                    lo[2] = min(lo[2], p.z); hi[2] = max(hi[2], p.z);
+                }
+            }
+        }
+        if (DECIM) {
+            // second sweep for the writes (ballots need converged warps)
+#pragma unroll 4
+            for (int r = 0; r < kBdIPT; ++r) {
+                bool kept = (keepmask >> r) & 1u;
+                uint32_t bal = __ballot_sync(0xFFFFFFFFu, kept);
+                if (kept) {
+                    uint64_t i = base + (uint64_t)r * kBdNT + threadIdx.x;
+                    uint64_t pos = s_base + s_cnt[r][warp] + __popc(bal & lanemask_lt());
+                    if (pos < out_cap) st_point(out, pos, ld_point(pts, i));
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    if (BOUNDS) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[a] = min(lo[a], __shfl_xor_sync(0xFFFFFFFFu, lo[a], o));
+                hi[a] = max(hi[a], __shfl_xor_sync(0xFFFFFFFFu, hi[a], o));
+            }
+        }
+        if (lane == 0) {
+            for (int a = 0; a < 3; ++a) { s_red[a][warp] = lo[a]; s_red[3 + a][warp] = hi[a]; }
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            int a = threadIdx.x;
+            int32_t v = s_red[a][0];
+            for (int w = 1; w < kBdNT / 32; ++w) v = a < 3 ? min(v, s_red[a][w]) : max(v, s_red[a][w]);
+            partial[blockIdx.x * 6 + a] = v;
+        }
+    }
+}
+
+__global__ void k_bounds_final(const int32_t* partial, int nblocks, uint64_t n, fp_cube* cube)
+{
+    if (threadIdx.x != 0) return;
+    fp_cube c;
+    for (int a = 0; a < 3; ++a) { c.o[a] = 0; c.mx[a] = 0; }
+    c.S = 0;
+    if (n > 0) {
+        int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+        for (int b = 0; b < nblocks; ++b)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = min(lo[a], partial[b * 6 + a]);
+                hi[a] = max(hi[a], partial[b * 6 + 3 + a]);
+            }
+        uint64_t ext = 0;
+        for (int a = 0; a < 3; ++a) {
+            c.o[a] = lo[a];
+            c.mx[a] = hi[a];
+            uint64_t e = (uint64_t)((int64_t)hi[a] - (int64_t)lo[a]);
+            ext = e > ext ? e : ext;
+        }
+        c.S = ext + 1;
+    }
+    *cube = c;
+}
+
+__global__ void k_zero_count(uint64_t* out_count) { *out_count = 0; }
+
+// a[*idx] = *val  (writes the grand total behind a device-sized prefix array)
+__global__ void k_put_at(uint64_t* a, const uint32_t* idx, const uint64_t* val) { a[*idx] = *val; }
+
+// ----------------------------------------------------------------- count
+template <bool AGG>
+__global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts, uint64_t n,
+                                               const fp_cube* __restrict__ cube, int g, uint32_t* __restrict__ counts)
+{
+    const CubeDev c = load_cube(cube);
+    const int sh = 3 * (kKeyLevels - g);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride * 4) {
+        uint32_t key[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            uint64_t i = i0 + u * stride + threadIdx.x;
+            key[u] = kNone;
+            if (i < n) {
+                int4 p = ld_point_cs(pts, i);
+                key[u] = (uint32_t)(fp::key21(p.x, p.y, p.z, c) >> sh);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (AGG) {
+                uint32_t peers = __match_any_sync(0xFFFFFFFFu, key[u]);
+                if (key[u] != kNone && lane == __ffs(peers) - 1) atomicAdd(&counts[key[u]], (uint32_t)__popc(peers));
+            } else if (key[u] != kNone) {
+                atomicAdd(&counts[key[u]], 1u);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- merge
+// pyramid[level l] at offset (8^l - 1) / 7 for l < g; level g is the count grid
+__global__ void k_pyramid_level(const uint32_t* __restrict__ child, uint32_t* __restrict__ parent, uint64_t nparent)
+{
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nparent) return;
+    // level offsets (8^l - 1) / 7 are only 4-byte aligned: scalar loads
+    const uint32_t* c = child + 8 * k;
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += c[q];
+    parent[k] = s;
+}
+
+FP_DEV uint32_t pyr_count(const uint32_t* pyr, const uint32_t* counts, int g, int l, uint64_t key)
+{
+    return l == g ? counts[key] : pyr[((1ull << (3 * l)) - 1) / 7 + key];
+}
+
+// block node of cell m: shallowest ancestor-or-self with count <= T, or the cell
+FP_DEV void block_of(const uint32_t* pyr, const uint32_t* counts, int g, uint64_t T, uint64_t m, int& lvl,
+                     uint32_t& cnt)
+{
+    for (int l = 0; l <= g; ++l) {
+        uint32_t c = pyr_count(pyr, counts, g, l, m >> (3 * (g - l)));
+        if (c <= T || l == g) { lvl = l; cnt = c; return; }
+    }
+}
+
+__global__ void k_chunk_mark(const uint32_t* __restrict__ pyr, const uint32_t* __restrict__ counts, int g,
+                             uint64_t T, uint32_t* __restrict__ start)
+{
+    uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= (1ull << (3 * g))) return;
+    int l;
+    uint32_t c;
+    block_of(pyr, counts, g, T, m, l, c);
+    uint64_t align = (1ull << (3 * (g - l))) - 1;
+    start[m] = (c > 0 && (m & align) == 0) ? 1u : 0u;
+}
+
+__global__ void k_chunk_write(const uint32_t* __restrict__ pyr, const uint32_t* __restrict__ counts, int g,
+                              uint64_t T, const uint32_t* __restrict__ start, const uint32_t* __restrict__ excl,
+                              fp_chunk* __restrict__ chunks, uint32_t* __restrict__ lut, uint32_t* __restrict__ ccount)
+{
+    uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= (1ull << (3 * g))) return;
+    uint32_t id = excl[m] + start[m] - 1;   // chunk holding cell m when the cell is in a chunk
+    if (start[m]) {
+        int l;
+        uint32_t c;
+        block_of(pyr, counts, g, T, m, l, c);
+        fp_chunk ch;
+        ch.key = m >> (3 * (g - l));
+        ch.count = c;
+        ch.level = (uint32_t)l;
+        chunks[id] = ch;
+        ccount[id] = c;
+    }
+    lut[m] = counts[m] > 0 ? id : kNone;
+}
+
+// ----------------------------------------------------------------- host side
+cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cube, bool bounds, bool decim,
+                                   uint64_t first, uint32_t modulus, fp_point* out, uint64_t out_cap,
+                                   uint64_t* out_count, const Workspace& ws, cudaStream_t st)
+{
+    uint64_t ntiles = (n + kBdTile - 1) / kBdTile;
+    int grid = (int)std::min<uint64_t>(ntiles ? ntiles : 1, (uint64_t)ws.num_sms * 8);
+    int32_t* partial = ws.take<int32_t>(6 * (size_t)grid);
+    uint64_t* status = ws.take<uint64_t>(ntiles ? ntiles : 1);
+    uint32_t* counter = ws.take<uint32_t>(4);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 4 * sizeof(uint32_t), st);
+    if (e) return e;
+    if (decim && ntiles) {
+        e = cudaMemsetAsync(status, 0, ntiles * sizeof(uint64_t), st);
+        if (e) return e;
+    }
+    if (decim && n == 0) k_zero_count<<<1, 1, 0, st>>>(out_count);
+    if (n) {
+        if (bounds && decim)
+            k_bounds_decimate<true, true><<<grid, kBdNT, 0, st>>>(pts, n, first, modulus, out, out_cap, out_count,
+                                                                   partial, status, counter, ntiles, ws.err);
+        else if (bounds)
+            k_bounds_decimate<true, false><<<grid, kBdNT, 0, st>>>(pts, n, first, modulus, out, out_cap, out_count,
+                                                                    partial, status, counter, ntiles, ws.err);
+        else
+            k_bounds_decimate<false, true><<<grid, kBdNT, 0, st>>>(pts, n, first, modulus, out, out_cap,
+                                                                    out_count, partial, status, counter, ntiles, ws.err);
+    }
+    if (bounds) k_bounds_final<<<1, 32, 0, st>>>(partial, n ? grid : 0, n, cube);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, uint32_t* counts,
+                         bool accumulate, const Workspace& ws, cudaStream_t st)
+{
+    uint64_t cells = 1ull << (3 * g);
+    if (!accumulate) {
+        cudaError_t e = cudaMemsetAsync(counts, 0, cells * sizeof(uint32_t), st);
+        if (e) return e;
+    }
+    if (n == 0) return cudaSuccess;
+    uint64_t want = (n + 1023) / 1024;
+    int grid = (int)std::min<uint64_t>(want, (uint64_t)ws.num_sms * 8);
+    k_count<true><<<grid, 256, 0, st>>>(pts, n, cube, g, counts);
+    return cudaGetLastError();
+}
+
+size_t merge_ws_bytes(int g)
+{
+    uint64_t cells = 1ull << (3 * g);
+    uint64_t pyr = ((1ull << (3 * g)) - 1) / 7;
+    return Workspace::bytes_for({pyr * 4, cells * 4, cells * 4, cells * 4, (size_t)kScanMaxTiles * 8,
+                                 (size_t)kScanMaxTiles * 8, 8});
+}
+
+cudaError_t launch_merge(const uint32_t* counts, int g, uint64_t T, fp_chunk* chunks, uint32_t* num_chunks,
+                         uint32_t* lut, uint64_t* offsets, const Workspace& ws, cudaStream_t st)
+{
+    uint64_t cells = 1ull << (3 * g);
+    uint64_t npyr = ((1ull << (3 * g)) - 1) / 7;
+    uint32_t* pyr = ws.take<uint32_t>(npyr ? npyr : 1);
+    uint32_t* start = ws.take<uint32_t>(cells);
+    uint32_t* excl = ws.take<uint32_t>(cells);
+    uint32_t* ccount = ws.take<uint32_t>(cells);
+    uint32_t* tiles32 = ws.take<uint32_t>(kScanMaxTiles);
+    uint64_t* tiles64 = ws.take<uint64_t>(kScanMaxTiles);
+    for (int l = g - 1; l >= 0; --l) {
+        uint64_t np = 1ull << (3 * l);
+        const uint32_t* child = l + 1 == g ? counts : pyr + ((1ull << (3 * (l + 1))) - 1) / 7;
+        uint32_t* parent = pyr + (np - 1) / 7;
+        k_pyramid_level<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(child, parent, np);
+    }
+    unsigned gb = (unsigned)((cells + 255) / 256);
+    k_chunk_mark<<<gb, 256, 0, st>>>(pyr, counts, g, T, start);
+    cudaError_t e = scan_exclusive<uint32_t, uint32_t>(start, excl, cells, nullptr, tiles32, num_chunks,
+                                                       (uint32_t*)nullptr, st);
+    if (e) return e;
+    k_chunk_write<<<gb, 256, 0, st>>>(pyr, counts, g, T, start, excl, chunks, lut, ccount);
+    // offsets[0..K] = exclusive prefix of chunk counts; offsets[K] = total
+    uint64_t* total = ws.take<uint64_t>(1);
+    e = scan_exclusive<uint32_t, uint64_t>(ccount, offsets, cells, num_chunks, tiles64, total, (uint64_t*)nullptr, st);
+    if (e) return e;
+    k_put_at<<<1, 1, 0, st>>>(offsets, num_chunks, total);
+    return cudaGetLastError();
+}
+
+}  // namespace fp

@@ -1,0 +1,70 @@
+// fp_internal.cuh -- host-side helpers shared by the translation units of
+// libfastpoints: the workspace carve-up and the launch functions each unit
+// exports to fp_api.cu.
+#pragma once
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+#include <initializer_list>
+#include "fp_common.cuh"
+#include "fp_scan.cuh"
+
+namespace fp {
+
+// Bump allocator over the caller's workspace; every piece is 256-byte aligned.
+struct Workspace {
+    char* base = nullptr;
+    size_t bytes = 0;
+    mutable size_t used = 0;
+    int num_sms = 152;
+    uint32_t* err = nullptr;   // device error word
+
+    static constexpr size_t kAlign = 256;
+    static size_t round(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+    static size_t bytes_for(std::initializer_list<size_t> parts)
+    {
+        size_t t = 0;
+        for (size_t p : parts) t += round(p ? p : 1);
+        return t;
+    }
+    template <typename T>
+    T* take(size_t count) const
+    {
+        size_t b = round(count * sizeof(T) ? count * sizeof(T) : 1);
+        char* p = base + used;
+        used += b;
+        return reinterpret_cast<T*>(p);
+    }
+};
+
+// fp_core.cu
+cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cube, bool bounds, bool decim,
+                                   uint64_t first, uint32_t modulus, fp_point* out, uint64_t out_cap,
+                                   uint64_t* out_count, const Workspace& ws, cudaStream_t st);
+size_t bounds_ws_bytes(uint64_t n, int num_sms);
+cudaError_t launch_count(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, uint32_t* counts,
+                         bool accumulate, const Workspace& ws, cudaStream_t st);
+size_t merge_ws_bytes(int g);
+cudaError_t launch_merge(const uint32_t* counts, int g, uint64_t T, fp_chunk* chunks, uint32_t* num_chunks,
+                         uint32_t* lut, uint64_t* offsets, const Workspace& ws, cudaStream_t st);
+
+// fp_sort.cu
+size_t distribute_ws_bytes(uint64_t n, int g);
+cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
+                              const uint64_t* offsets, const uint32_t* num_chunks, fp_point* out, uint32_t* perm,
+                              const Workspace& ws, cudaStream_t st);
+
+// fp_octree.cu
+size_t octree_ws_bytes(uint64_t n, const fp_params& p);
+size_t subsample_ws_bytes(uint64_t n, uint64_t node_cap);
+uint64_t node_capacity_bound(uint64_t n, const fp_params& p);
+cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t n, const fp_cube* cube,
+                          const fp_chunk* chunks, const uint32_t* num_chunks, const uint64_t* offsets,
+                          const uint32_t* counts, const fp_params& prm, fp_node* nodes, uint32_t node_cap,
+                          uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
+                          const Workspace& ws, cudaStream_t st);
+cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const fp_point* sorted,
+                             const uint32_t* perm, const uint32_t* owner, uint64_t n, fp_point* final_pts,
+                             uint32_t* final_perm, const Workspace& ws, cudaStream_t st);
+
+}  // namespace fp

@@ -1,0 +1,1210 @@
+// fp_octree.cu -- local octrees of the chunks, the stitch above them and the
+// level-of-detail selection (paper Sec. 4.4, Fig. "octree"; "shallow octree",
+// Abstract).
+//
+// Definitions (exact-integer reading):
+//   * node (L, k) exists iff it holds a point and (L == 0 or its parent holds
+//     more than C points and lies above max_level); it is a leaf iff it holds
+//     at most C points or L == max_level;
+//   * an inner node at level L keeps, per occupied level-(L+s) cell among its
+//     children's remaining points, the smallest original index (deepest first).
+// Closed form used here: with lambda(p) the shallowest level at which p has the
+// smallest index of its cell, p is kept by its ancestor at level
+// min(max(0, lambda(p) - s), leaf level of p).  Every cell at a level >= s >= g
+// lies inside one level-g cell, hence inside one chunk, so lambda is decided
+// per level-g cell.  Inside a chunk the distributed order is index order.
+//
+// Steps:
+//   1. group the distributed points by level-g cell (stable scatter: records
+//      (key21, j) with j the position in the chunk array, i.e. index order);
+//   2. cells with more than kPieceMax points are key-sorted and cut into
+//      node-aligned pieces of at most kPieceMax points (split tree, one warp per
+//      open node); the split tree also gives the nodes between level g and the
+//      pieces, and which piece minimum is the minimum of which coarser node;
+//   3. one CTA per window of pieces: sort by key in shared memory, all nearest
+//      smaller values of the index along the key order give each point's
+//      lambda, deep subtrees inside pieces are split by binary search, and each
+//      point gets its owner level and leaf level;
+//   4. node records (levels <= g from the count pyramid, deeper ones from steps
+//      2-3) are sorted into preorder; ids are resolved per point;
+//   5. the points are scattered stably by leaf id (leaf-grouped output) and,
+//      in fp_subsample, by owner id (final output); owner segments of nodes
+//      above the chunks (the stitch) are re-sorted by original index.
+#include "fp_sort.cuh"
+
+namespace fp {
+
+constexpr int kPieceMax = 2048;                 // largest piece handled in shared memory
+constexpr int kWindow = 2048;                   // pieces starting in one window form a unit
+constexpr int kUnitCap = kPieceMax + kWindow;   // records of one unit
+constexpr int kUnitNT = 512;
+constexpr int kUnitWarps = kUnitNT / 32;
+constexpr uint8_t kInner = 0xFF;                // hierarchy still inner at this level
+constexpr uint8_t kEmpty = 0xFE;
+
+struct NodeRec {   // a node before preorder numbering
+    uint64_t key;
+    uint32_t count, leaf_first;
+    uint8_t level, is_leaf, pad[6];
+};
+static_assert(sizeof(NodeRec) == 24, "NodeRec layout");
+
+struct Piece {
+    uint32_t begin, count;   // record range in the cell-grouped arrays
+    uint8_t q, hier, A, dup; // level, leaf level or kInner, first-min level of its minimum, oversized
+    uint32_t pad;
+};
+static_assert(sizeof(Piece) == 16, "Piece layout");
+
+struct OpenNode {
+    uint64_t key;
+    uint32_t begin, count, minj;
+    uint8_t q, hier, A, pad;
+};
+static_assert(sizeof(OpenNode) == 24, "OpenNode layout");
+
+struct OctCtx {   // device pointers of one fp_build_chunk_octree call
+    const uint32_t* counts;
+    const uint32_t* pyr;
+    const uint32_t* cstart;
+    uint8_t* cell_leaf;
+    uint64_t* gk;
+    uint32_t* gj;
+    Piece* pieces;
+    uint32_t* npieces;
+    uint32_t piece_cap;
+    NodeRec* nrec;
+    uint32_t* nnode;
+    uint32_t node_cap_ws;
+    uint8_t* own_code;
+    uint8_t* leaf_code;
+    uint32_t open_cap;
+    int g, s, lmax, dl;
+    uint64_t C;
+    uint32_t* err;
+};
+
+FP_DEV uint32_t pyr_at(const uint32_t* pyr, const uint32_t* counts, int g, int l, uint64_t key)
+{
+    return l == g ? counts[key] : pyr[((1ull << (3 * l)) - 1) / 7 + key];
+}
+
+__global__ void k_pyr_level(const uint32_t* __restrict__ child, uint32_t* __restrict__ parent, uint64_t np)
+{
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    // level offsets (8^l - 1) / 7 are only 4-byte aligned: scalar loads
+    const uint32_t* c = child + 8 * k;
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += c[q];
+    parent[k] = s;
+}
+
+FP_DEV void emit_node(const OctCtx& c, uint64_t key, int level, uint32_t count, uint32_t leaf_first, bool leaf)
+{
+    uint32_t id = atomicAdd(c.nnode, 1u);
+    if (id >= c.node_cap_ws) { raise(c.err, FP_ERR_CAPACITY); return; }
+    NodeRec r;
+    r.key = key;
+    r.count = count;
+    r.leaf_first = leaf_first;
+    r.level = (uint8_t)level;
+    r.is_leaf = leaf ? 1 : 0;
+    for (int q = 0; q < 6; ++q) r.pad[q] = 0;
+    c.nrec[id] = r;
+}
+
+FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, uint8_t hier, uint8_t A)
+{
+    uint32_t id = atomicAdd(c.npieces, 1u);
+    if (id >= c.piece_cap) { raise(c.err, FP_ERR_CAPACITY); return; }
+    Piece p;
+    p.begin = begin;
+    p.count = count;
+    p.q = (uint8_t)q;
+    p.hier = hier;
+    p.A = A;
+    p.dup = count > (uint32_t)kPieceMax ? 1 : 0;
+    p.pad = 0;
+    c.pieces[id] = p;
+}
+
+// ---------------------------------------------------------------- cells
+// Per level-g cell: leaf level if the hierarchy ends at or above g, kInner if
+// the cell node is inner, kEmpty for an empty cell.  Nonempty cells with at
+// most kPieceMax points become pieces; larger ones open the split tree.
+__global__ void k_cell_setup(OctCtx c, OpenNode* open0, uint32_t* nopen0)
+{
+    uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t cells = 1ull << (3 * c.g);
+    if (m >= cells) return;
+    uint32_t cnt = c.counts[m];
+    if (cnt == 0) { c.cell_leaf[m] = kEmpty; return; }
+    uint8_t hier = kInner;
+    for (int l = 0; l <= c.g; ++l) {
+        uint32_t v = pyr_at(c.pyr, c.counts, c.g, l, m >> (3 * (c.g - l)));
+        if (v <= c.C || l == c.lmax) { hier = (uint8_t)l; break; }
+    }
+    c.cell_leaf[m] = hier;
+    if (cnt <= (uint32_t)kPieceMax) {
+        emit_piece(c, c.cstart[m], cnt, c.g, hier, (uint8_t)c.g);
+    } else {
+        uint32_t id = atomicAdd(nopen0, 1u);
+        if (id >= c.open_cap) { raise(c.err, FP_ERR_CAPACITY); return; }
+        OpenNode o;
+        o.key = m;
+        o.begin = c.cstart[m];
+        o.count = cnt;
+        o.minj = c.gj[c.cstart[m]];   // the cell's records are still in index order here
+        o.q = (uint8_t)c.g;
+        o.hier = hier;
+        o.A = (uint8_t)c.g;
+        o.pad = 0;
+        open0[id] = o;
+    }
+}
+
+// nodes at levels <= g, from the count pyramid
+__global__ void k_nodes_upper(OctCtx c)
+{
+    uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int L = 0;
+    uint64_t base = 0;
+    while (L <= c.g && f >= base + (1ull << (3 * L))) { base += 1ull << (3 * L); ++L; }
+    if (L > c.g) return;
+    uint64_t k = f - base;
+    uint32_t cnt = pyr_at(c.pyr, c.counts, c.g, L, k);
+    if (cnt == 0) return;
+    for (int a = 0; a < L; ++a) {   // every ancestor must be inner
+        uint32_t v = pyr_at(c.pyr, c.counts, c.g, a, k >> (3 * (L - a)));
+        if (v <= c.C || a >= c.lmax) return;
+    }
+    bool leaf = cnt <= c.C || L == c.lmax;
+    emit_node(c, k, L, cnt, c.cstart[k << (3 * (c.g - L))], leaf);
+}
+
+// ------------------------------------------------------- big cells: gather
+// records of cells with more than kPieceMax points, key (big rank, sub-key)
+__global__ void k_big_gather(const OpenNode* open0, const uint32_t* nopen0, const uint32_t* bigstart,
+                             const uint64_t* gk, const uint32_t* gj, uint64_t* bk, uint32_t* bj, int g, int dl)
+{
+    const uint32_t nb = *nopen0;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int sub_bits = 3 * (dl - g);
+    const uint64_t sub_mask = (1ull << sub_bits) - 1;
+    for (uint32_t b = warp; b < nb; b += nwarps) {
+        const OpenNode o = open0[b];
+        const uint32_t dst = bigstart[b];
+        for (uint32_t r = lane; r < o.count; r += 32) {
+            uint64_t k = gk[o.begin + r];
+            bk[dst + r] = ((uint64_t)b << sub_bits) | ((k >> (3 * (kKeyLevels - dl))) & sub_mask);
+            bj[dst + r] = gj[o.begin + r];
+        }
+    }
+}
+
+// write the key-sorted big records back into their cells (keys truncated at level dl)
+__global__ void k_big_scatter(const OpenNode* open0, const uint32_t* nopen0, const uint32_t* bigstart,
+                              const uint64_t* bk, const uint32_t* bj, uint64_t* gk, uint32_t* gj, int g, int dl)
+{
+    const uint32_t nb = *nopen0;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int sub_bits = 3 * (dl - g);
+    const uint64_t sub_mask = (1ull << sub_bits) - 1;
+    for (uint32_t b = warp; b < nb; b += nwarps) {
+        const OpenNode o = open0[b];
+        const uint32_t src = bigstart[b];
+        for (uint32_t r = lane; r < o.count; r += 32) {
+            uint64_t k = bk[src + r];
+            gk[o.begin + r] = (o.key << (3 * (kKeyLevels - g))) | ((k & sub_mask) << (3 * (kKeyLevels - dl)));
+            gj[o.begin + r] = bj[src + r];
+        }
+    }
+}
+
+__global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uint32_t* cnt_out, uint32_t cap)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap) return;
+    cnt_out[i] = i < *nopen0 ? open0[i].count : 0;
+}
+
+// --------------------------------------------------- big cells: split tree
+// One warp per open node at level q: child ranges by binary search on the
+// key-sorted records, smallest index of every child, hierarchy status, first-min
+// level; children that are still too large stay open, the others become pieces.
+__global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, OpenNode* nxt, uint32_t* nnxt,
+                        uint32_t open_cap)
+{
+    const uint32_t nc = *ncur;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = warp; w < nc; w += nwarps) {
+        const OpenNode o = cur[w];
+        const int q1 = o.q + 1;
+        const int sh = 3 * (kKeyLevels - q1);
+        // lane d (0..8): first record whose child digit is >= d
+        uint32_t lo = o.begin + o.count;
+        if (lane <= 8) {
+            uint32_t a = o.begin, b = o.begin + o.count;
+            while (a < b) {
+                uint32_t mid = (a + b) >> 1;
+                if ((int)((c.gk[mid] >> sh) & 7) < lane) a = mid + 1;
+                else b = mid;
+            }
+            lo = a;
+        }
+        for (int d = 0; d < 8; ++d) {
+            uint32_t cb = __shfl_sync(0xFFFFFFFFu, lo, d);
+            uint32_t ce = __shfl_sync(0xFFFFFFFFu, lo, d + 1);
+            uint32_t cn = ce - cb;
+            if (cn == 0) continue;
+            uint32_t mj = 0xFFFFFFFFu;
+            for (uint32_t r = cb + lane; r < ce; r += 32) mj = min(mj, c.gj[r]);
+            for (int off = 16; off > 0; off >>= 1) mj = min(mj, __shfl_xor_sync(0xFFFFFFFFu, mj, off));
+            if (lane == 0) {
+                uint64_t key = (o.key << 3) | (uint64_t)d;
+                uint8_t hier;
+                if (o.hier != kInner) hier = o.hier;
+                else hier = (cn <= c.C || q1 == c.lmax) ? (uint8_t)q1 : kInner;
+                // the child's minimum is the parent's minimum: it keeps the parent's first-min level
+                uint8_t A = mj == o.minj ? o.A : (uint8_t)q1;
+                if (o.hier == kInner) emit_node(c, key, q1, cn, cb, hier != kInner);
+                uint32_t id = 0;
+                const bool open_child = cn > (uint32_t)kPieceMax && q1 < c.dl;
+                if (open_child) id = atomicAdd(nnxt, 1u);
+                if (open_child && id >= open_cap) {
+                    raise(c.err, FP_ERR_CAPACITY);
+                } else if (open_child) {
+                    OpenNode ch;
+                    ch.key = key;
+                    ch.begin = cb;
+                    ch.count = cn;
+                    ch.minj = mj;
+                    ch.q = (uint8_t)q1;
+                    ch.hier = hier;
+                    ch.A = A;
+                    ch.pad = 0;
+                    nxt[id] = ch;
+                } else {
+                    emit_piece(c, cb, cn, q1, hier, A);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ units
+struct UnitSmem {
+    uint64_t key[kUnitCap];
+    uint64_t key2[kUnitCap];
+    uint32_t j[kUnitCap];       // by local index
+    int16_t ps[kUnitCap];       // by sorted position: left chain pointer (see k_units)
+    int16_t ns[kUnitCap];       // right chain pointer
+    uint16_t v[kUnitCap];       // local index by sorted position
+    uint16_t v2[kUnitCap];
+    uint16_t piece[kUnitCap];   // piece of a local index
+    uint8_t cl[kUnitCap];       // common level with the nearest smaller index on the left (255: none)
+    uint8_t cr[kUnitCap];       // ... on the right
+    uint8_t leaf[kUnitCap];     // leaf level by sorted position (pieces with a deep subtree)
+    uint32_t pbeg[kWindow + 1];
+    uint16_t pcnt[kWindow + 1]; // 0 for an oversized piece (handled elsewhere)
+    uint16_t psrt[kWindow + 1]; // start of each piece in the unit (load order = sorted order)
+    uint8_t pq[kWindow + 1], phier[kWindow + 1], pA[kWindow + 1];
+    uint16_t whist[kUnitWarps][256];
+    uint32_t scan[64];
+    unsigned long long kmin, kmax;
+    uint32_t np, cnt, p0, dl;
+};
+
+// stable LSD pass over the unit's records by 8 key bits at `shift`
+FP_DEV void unit_sort_pass(UnitSmem& S, const uint64_t* kin, const uint16_t* vin, uint64_t* kout, uint16_t* vout,
+                           int cnt, int shift)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int per_warp = kUnitCap / kUnitWarps;   // 256 records per warp, 8 rounds
+    for (int q = threadIdx.x; q < kUnitWarps * 256; q += kUnitNT) (&S.whist[0][0])[q] = 0;
+    __syncthreads();
+    uint32_t pack[per_warp / 32];
+#pragma unroll
+    for (int r = 0; r < per_warp / 32; ++r) {
+        int p = warp * per_warp + r * 32 + lane;
+        uint32_t d = p < cnt ? (uint32_t)(kin[p] >> shift) & 255u : 0xFFFFu;
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && d != 0xFFFFu) {
+            old = S.whist[warp][d];
+            S.whist[warp][d] = (uint16_t)(old + __popc(peers));
+        }
+        old = __shfl_sync(0xFFFFFFFFu, old, leader);
+        pack[r] = d | ((old + __popc(peers & lanemask_lt())) << 16);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over (digit, warp): the first 256 threads own one digit each
+    uint32_t tot_d = 0;
+    if (threadIdx.x < 256) {
+        for (int w = 0; w < kUnitWarps; ++w) {
+            uint32_t v = S.whist[w][threadIdx.x];
+            S.whist[w][threadIdx.x] = (uint16_t)tot_d;
+            tot_d += v;
+        }
+    }
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan<kUnitNT, uint32_t>(threadIdx.x < 256 ? tot_d : 0u, S.scan, tot);
+    if (threadIdx.x < 256)
+        for (int w = 0; w < kUnitWarps; ++w) S.whist[w][threadIdx.x] = (uint16_t)(S.whist[w][threadIdx.x] + ex);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < per_warp / 32; ++r) {
+        int p = warp * per_warp + r * 32 + lane;
+        if (p < cnt) {
+            uint32_t d = pack[r] & 0xFFFFu;
+            uint32_t pos = S.whist[warp][d] + (pack[r] >> 16);
+            kout[pos] = kin[p];
+            vout[pos] = vin[p];
+        }
+    }
+    __syncthreads();
+}
+
+// last piece whose start is <= r (pieces of zero length share starts)
+FP_DEV int piece_of(const UnitSmem& S, int np, int r)
+{
+    int a = 0, b = np;
+    while (a < b) {
+        int m = (a + b) >> 1;
+        if ((int)S.psrt[m] <= r) a = m + 1;
+        else b = m;
+    }
+    return a - 1;
+}
+
+// One CTA per window of kWindow record positions: the pieces starting in it.
+// Per unit:
+//   sort the records by key (stable, 8-bit LSD passes in shared memory);
+//   nearest smaller index on each side along the key order (chain jumping:
+//   while the candidate's index is larger, jump to the candidate's own
+//   pointer; every skipped position holds a larger index).  The level shared
+//   with the nearer of the two, plus one, is lambda unless the record is the
+//   minimum of its piece, whose lambda comes from the split tree;
+//   deep subtrees of inner pieces by binary search on the sorted keys.
+__global__ void __launch_bounds__(kUnitNT, 1) k_units(OctCtx c, const uint64_t* piece_begin_sorted,
+                                                      const uint32_t* piece_order, uint64_t n)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    UnitSmem& S = *reinterpret_cast<UnitSmem*>(smem_raw);
+    const uint32_t np_all = *c.npieces < c.piece_cap ? *c.npieces : c.piece_cap;
+    const uint64_t nunits = (n + kWindow - 1) / kWindow;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const uint64_t wlo = u * kWindow, whi = wlo + kWindow;
+        if (threadIdx.x == 0) {
+            uint32_t a = 0, b = np_all;
+            while (a < b) { uint32_t m = (a + b) >> 1; if (piece_begin_sorted[m] < wlo) a = m + 1; else b = m; }
+            uint32_t p0 = a;
+            b = np_all;
+            while (a < b) { uint32_t m = (a + b) >> 1; if (piece_begin_sorted[m] < whi) a = m + 1; else b = m; }
+            S.p0 = p0;
+            S.np = a - p0;
+            S.kmin = ~0ull;
+            S.kmax = 0;
+            S.dl = 0;
+        }
+        __syncthreads();
+        const int np = (int)S.np;
+        // piece descriptors; a block scan gives their starts in the unit
+        {
+            constexpr int per = (kWindow + kUnitNT - 1) / kUnitNT;   // 4
+            uint32_t cn[per];
+            uint32_t sum = 0;
+            for (int q = 0; q < per; ++q) {
+                int pi = threadIdx.x * per + q;
+                cn[q] = 0;
+                if (pi < np) {
+                    Piece p = c.pieces[piece_order[S.p0 + pi]];
+                    S.pbeg[pi] = p.begin;
+                    S.pq[pi] = p.q;
+                    S.phier[pi] = p.hier;
+                    S.pA[pi] = p.A;
+                    cn[q] = p.dup ? 0u : p.count;
+                    S.pcnt[pi] = (uint16_t)cn[q];
+                    if (cn[q]) {
+                        uint32_t d = p.hier == kInner ? (uint32_t)c.dl
+                                                      : (uint32_t)min(kKeyLevels, c.s + (int)p.hier - 1);
+                        atomicMax(&S.dl, d);
+                    }
+                }
+                sum += cn[q];
+            }
+            uint32_t tot;
+            uint32_t ex = block_exclusive_scan<kUnitNT, uint32_t>(sum, S.scan, tot);
+            for (int q = 0; q < per; ++q) {
+                int pi = threadIdx.x * per + q;
+                if (pi < np) S.psrt[pi] = (uint16_t)ex;
+                ex += cn[q];
+            }
+            if (threadIdx.x == 0) S.cnt = tot;
+        }
+        __syncthreads();
+        const int cnt = (int)S.cnt;
+        if (cnt == 0) { __syncthreads(); continue; }
+        // records; local index = position in load order
+        for (int r = threadIdx.x; r < cnt; r += kUnitNT) {
+            int pi = piece_of(S, np, r);
+            uint32_t g = S.pbeg[pi] + (uint32_t)(r - S.psrt[pi]);
+            uint64_t k = c.gk[g];
+            S.key[r] = k;
+            S.j[r] = c.gj[g];
+            S.v[r] = (uint16_t)r;
+            S.piece[r] = (uint16_t)pi;
+            atomicMin(&S.kmin, (unsigned long long)k);
+            atomicMax(&S.kmax, (unsigned long long)k);
+        }
+        __syncthreads();
+        {
+            const int dl_unit = (int)S.dl;
+            const int clev = common_level(S.kmin, S.kmax);
+            const int hi_bit = 3 * (kKeyLevels - clev);
+            const int lo_bit = 3 * (kKeyLevels - max(dl_unit, clev));
+            bool in_key = true;
+            for (int sh = lo_bit; sh < hi_bit; sh += 8) {
+                if (in_key) unit_sort_pass(S, S.key, S.v, S.key2, S.v2, cnt, sh);
+                else unit_sort_pass(S, S.key2, S.v2, S.key, S.v, cnt, sh);
+                in_key = !in_key;
+            }
+            if (!in_key) {
+                for (int r = threadIdx.x; r < cnt; r += kUnitNT) { S.key[r] = S.key2[r]; S.v[r] = S.v2[r]; }
+            }
+        }
+        __syncthreads();
+        // ---- nearest smaller index along the key order, inside each thread's block first
+        const int per = (cnt + kUnitNT - 1) / kUnitNT;   // <= 8
+        const int b0 = min(cnt, (int)threadIdx.x * per), b1 = min(cnt, b0 + per);
+        for (int r = b0; r < b1; ++r) {
+            const uint32_t jr = S.j[S.v[r]];
+            int x = r - 1;
+            while (x >= b0 && S.j[S.v[x]] > jr) x = S.ps[x];
+            S.ps[r] = (int16_t)x;   // x < b0: continue from x later (every index in (x, r) is larger)
+        }
+        for (int r = b1 - 1; r >= b0; --r) {
+            const uint32_t jr = S.j[S.v[r]];
+            int x = r + 1;
+            while (x < b1 && S.j[S.v[x]] > jr) x = S.ns[x];
+            S.ns[r] = (int16_t)x;
+        }
+        __syncthreads();
+        for (int r = b0; r < b1; ++r) {
+            const uint32_t jr = S.j[S.v[r]];
+            const uint64_t kr = S.key[r];
+            int x = S.ps[r];
+            while (x >= 0 && S.j[S.v[x]] > jr) x = S.ps[x];
+            S.cl[r] = x >= 0 ? (uint8_t)common_level(kr, S.key[x]) : (uint8_t)255;
+            x = S.ns[r];
+            while (x < cnt && S.j[S.v[x]] > jr) x = S.ns[x];
+            S.cr[r] = x < cnt ? (uint8_t)common_level(kr, S.key[x]) : (uint8_t)255;
+        }
+        __syncthreads();
+        // ---- deep subtrees inside pieces whose node is still inner: one warp per piece
+        for (int pi = warp; pi < np; pi += kUnitWarps) {
+            if (S.phier[pi] != kInner || S.pcnt[pi] == 0) continue;
+            const int ps0 = S.psrt[pi], pn = S.pcnt[pi];
+            int st_b[8 * 22], st_e[8 * 22], st_l[8 * 22];   // used by lane 0 only
+            int sp = 0;
+            if (lane == 0) { st_b[0] = ps0; st_e[0] = ps0 + pn; st_l[0] = S.pq[pi]; sp = 1; }
+            for (;;) {
+                int nb_ = 0, ne_ = 0, L = 0, more = 0;
+                if (lane == 0 && sp > 0) { --sp; nb_ = st_b[sp]; ne_ = st_e[sp]; L = st_l[sp]; more = 1; }
+                more = __shfl_sync(0xFFFFFFFFu, more, 0);
+                if (!more) break;
+                nb_ = __shfl_sync(0xFFFFFFFFu, nb_, 0);
+                ne_ = __shfl_sync(0xFFFFFFFFu, ne_, 0);
+                L = __shfl_sync(0xFFFFFFFFu, L, 0);
+                const int L1 = L + 1;
+                const int sh = 3 * (kKeyLevels - L1);
+                int lo = ne_;
+                if (lane <= 8) {   // lane d: first position whose child digit is >= d
+                    int a2 = nb_, b2 = ne_;
+                    while (a2 < b2) {
+                        int mid = (a2 + b2) >> 1;
+                        if ((int)((S.key[mid] >> sh) & 7) < lane) a2 = mid + 1;
+                        else b2 = mid;
+                    }
+                    lo = a2;
+                }
+                for (int d = 0; d < 8; ++d) {
+                    const int cb = __shfl_sync(0xFFFFFFFFu, lo, d);
+                    const int ce = __shfl_sync(0xFFFFFFFFu, lo, d + 1);
+                    const int cn = ce - cb;
+                    if (cn <= 0) continue;
+                    const bool leaf = (uint64_t)cn <= c.C || L1 == c.lmax;
+                    if (lane == 0) {
+                        emit_node(c, S.key[cb] >> sh, L1, (uint32_t)cn, S.pbeg[pi] + (uint32_t)(cb - ps0), leaf);
+                        if (!leaf && sp < 8 * 22) { st_b[sp] = cb; st_e[sp] = ce; st_l[sp] = L1; ++sp; }
+                    }
+                    if (leaf)
+                        for (int r = cb + lane; r < ce; r += 32) S.leaf[r] = (uint8_t)L1;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- owner level and leaf level of every record
+        for (int r = threadIdx.x; r < cnt; r += kUnitNT) {
+            const int vv = S.v[r];
+            const int pi = S.piece[vv];
+            const int ql = S.cl[r] == 255 ? -1 : (int)S.cl[r];
+            const int qr = S.cr[r] == 255 ? -1 : (int)S.cr[r];
+            const int lm = max(ql, qr);
+            const int q = S.pq[pi];
+            const int lambda = lm < q ? (int)S.pA[pi] : lm + 1;   // the piece minimum: from the split tree
+            const int leafl = S.phier[pi] == kInner ? (int)S.leaf[r] : (int)S.phier[pi];
+            int K = lambda - c.s;
+            if (K < 0) K = 0;
+            if (K > leafl) K = leafl;
+            const uint32_t jj = S.j[vv];
+            c.own_code[jj] = (uint8_t)K;
+            c.leaf_code[jj] = (uint8_t)leafl;
+        }
+        __syncthreads();
+    }
+}
+
+// oversized pieces (more than kPieceMax identical keys down to the deepest
+// needed level): only their first record, the smallest index, can be a minimum
+__global__ void k_dup_pieces(OctCtx c)
+{
+    const uint32_t np_all = *c.npieces < c.piece_cap ? *c.npieces : c.piece_cap;
+    for (uint32_t pi = blockIdx.x; pi < np_all; pi += gridDim.x) {
+        const Piece p = c.pieces[pi];
+        if (!p.dup) continue;
+        const int leafl = p.hier == kInner ? c.lmax : (int)p.hier;
+        for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) {
+            uint32_t jj = c.gj[p.begin + r];
+            int K = leafl;
+            if (r == 0) {
+                K = (int)p.A - c.s;
+                if (K < 0) K = 0;
+                if (K > leafl) K = leafl;
+            }
+            c.own_code[jj] = (uint8_t)K;
+            c.leaf_code[jj] = (uint8_t)leafl;
+        }
+    }
+}
+
+__global__ void k_piece_keys(const Piece* pieces, const uint32_t* npieces, uint32_t cap, uint64_t* keys)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t np = *npieces < cap ? *npieces : cap;
+    if (i < np) keys[i] = pieces[i].begin;
+}
+
+__global__ void k_clamp(uint32_t* v, uint32_t cap)
+{
+    if (*v > cap) *v = cap;
+}
+
+// ------------------------------------------------------------ node table
+__global__ void k_node_keys(const NodeRec* nrec, const uint32_t* nnode, uint64_t* start, uint32_t* level, int lmax)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *nnode) return;
+    NodeRec r = nrec[i];
+    start[i] = r.key << (3 * (lmax - r.level));
+    level[i] = r.level;
+}
+
+// preorder id of node (level, start); kNone when absent
+FP_DEV uint32_t node_lookup(const uint64_t* sorted_start, const uint8_t* sorted_level, uint32_t M, uint64_t start,
+                            int level)
+{
+    uint32_t a = 0, b = M;
+    while (a < b) {
+        uint32_t m = (a + b) >> 1;
+        if (sorted_start[m] < start) a = m + 1;
+        else b = m;
+    }
+    if (a >= M || sorted_start[a] != start || (int)sorted_level[a] > level) return kNone;
+    uint32_t id = a + (uint32_t)(level - (int)sorted_level[a]);
+    if (id >= M || sorted_start[id] != start || (int)sorted_level[id] != level) return kNone;
+    return id;
+}
+
+// fp_node records in preorder; lookup structures for the id resolution
+__global__ void k_node_write(const NodeRec* nrec, const uint32_t* nnode, const uint32_t* order,
+                             const uint64_t* sorted_start, uint8_t* sorted_level, fp_node* nodes, uint32_t node_cap,
+                             uint32_t* num_nodes, uint32_t* idxtab, uint32_t* leafw, int g, int lmax, uint32_t* err)
+{
+    const uint32_t M = *nnode;
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        *num_nodes = M;
+        if (M > node_cap) raise(err, FP_ERR_CAPACITY);
+    }
+    if (i >= M) return;
+    NodeRec r = nrec[order[i]];
+    sorted_level[i] = r.level;
+    leafw[i] = r.is_leaf ? r.count : 0;
+    if (r.level <= g) idxtab[((1ull << (3 * r.level)) - 1) / 7 + r.key] = i;
+}
+
+__global__ void k_node_fill(const NodeRec* nrec, const uint32_t* nnode, const uint32_t* order,
+                            const uint64_t* sorted_start, const uint8_t* sorted_level, fp_node* nodes,
+                            uint32_t node_cap, int lmax)
+{
+    const uint32_t M = *nnode;
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M || i >= node_cap) return;
+    NodeRec r = nrec[order[i]];
+    fp_node o;
+    o.key = r.key;
+    o.first = 0;
+    o.leaf_first = r.leaf_first;
+    o.count = r.count;
+    o.n_own = 0;
+    uint64_t end = (r.key + 1) << (3 * (lmax - r.level));
+    uint32_t a = i + 1, b = M;
+    while (a < b) {
+        uint32_t m = (a + b) >> 1;
+        if (sorted_start[m] < end) a = m + 1;
+        else b = m;
+    }
+    o.n_desc = a - i - 1;
+    o.level = r.level;
+    o.child_mask = 0;
+    o.is_leaf = r.is_leaf;
+    o.pad = 0;
+    nodes[i] = o;
+}
+
+__global__ void k_node_children(const uint32_t* nnode, const uint64_t* sorted_start, const uint8_t* sorted_level,
+                                fp_node* nodes, uint32_t node_cap, int lmax)
+{
+    const uint32_t M = *nnode;
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M || i >= node_cap || sorted_level[i] == 0) return;
+    const int L = sorted_level[i];
+    const uint64_t key = sorted_start[i] >> (3 * (lmax - L));
+    uint32_t p = node_lookup(sorted_start, sorted_level, M, (key >> 3) << (3 * (lmax - L + 1)), L - 1);
+    if (p != kNone && p < node_cap) {
+        // child_mask is byte 37 of the 40-byte record
+        unsigned char* rec = reinterpret_cast<unsigned char*>(nodes + p);
+        uint32_t* word = reinterpret_cast<uint32_t*>(rec + 36);
+        atomicOr(word, (1u << (key & 7)) << 8);
+    }
+}
+
+// owner and leaf ids of every distributed point; owned counts per node
+__global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp_cube* cube,
+                          const uint8_t* own_code, const uint8_t* leaf_code, const uint32_t* idxtab,
+                          const uint64_t* sorted_start, const uint8_t* sorted_level, const uint32_t* nnode,
+                          uint32_t* owner, uint32_t* leafid, uint32_t* n_own, int g, int lmax, uint32_t* err)
+{
+    const CubeDev cb = load_cube(cube);
+    const uint32_t M = *nnode;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        uint64_t j = i0 + threadIdx.x;
+        uint32_t oid = kNone;
+        if (j < n) {
+            int4 p = ld_point(pts, j);
+            uint64_t k21 = key21(p.x, p.y, p.z, cb);
+            int ks[2] = {own_code[j], leaf_code[j]};
+            uint32_t ids[2];
+            for (int t = 0; t < 2; ++t) {
+                int L = ks[t];
+                uint64_t k = k21 >> (3 * (kKeyLevels - L));
+                ids[t] = L <= g ? idxtab[((1ull << (3 * L)) - 1) / 7 + k]
+                                : node_lookup(sorted_start, sorted_level, M, k << (3 * (lmax - L)), L);
+                if (L > lmax) ids[t] = kNone;
+            }
+            if (ids[0] >= M || ids[1] >= M) {   // never for a consistent tree
+                raise(err, FP_ERR_CAPACITY);
+                ids[0] = ids[1] = 0;
+            }
+            owner[j] = ids[0];
+            leafid[j] = ids[1];
+            oid = ids[0];
+        }
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, oid);
+        if (oid != kNone && lane == __ffs(peers) - 1) atomicAdd(&n_own[oid], (uint32_t)__popc(peers));
+    }
+}
+
+__global__ void k_write_nown(fp_node* nodes, const uint32_t* nnode, uint32_t node_cap, const uint32_t* n_own)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *nnode && i < node_cap) nodes[i].n_own = n_own[i];
+}
+
+__global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
+
+__global__ void k_level_keys(const uint32_t* level, const uint32_t* nnode, uint64_t* keys)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *nnode) keys[i] = level[i];
+}
+
+__global__ void k_gather_u64(const uint64_t* src, const uint32_t* idx, const uint32_t* nn, uint64_t* dst)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *nn) dst[i] = src[idx[i]];
+}
+
+// ------------------------------------------------------------ host: octree
+struct OctLayout {
+    uint64_t cells, npyr, piece_cap, open_cap, node_cap;
+};
+
+static OctLayout oct_layout(uint64_t n, const fp_params& p)
+{
+    OctLayout L;
+    L.cells = 1ull << (3 * p.grid_log2);
+    L.npyr = (L.cells - 1) / 7;
+    L.piece_cap = L.cells + 16 * (n / kPieceMax) + 4096;
+    L.open_cap = n / kPieceMax + 1024;
+    const uint64_t upper = (L.cells * 8 - 1) / 7;
+    const uint64_t C = p.node_capacity ? p.node_capacity : 1;
+    // every deep node is a child of an inner node, and an inner node holds more than C points:
+    // at most n / C inner nodes per level, 8 children each
+    uint64_t deep = 8 * (n / C + 1) * (uint64_t)(p.max_level - p.grid_log2 + 1) + 4096;
+    if (deep > 2 * n + 4096) deep = 2 * n + 4096;
+    L.node_cap = upper + deep;
+    if (L.node_cap > 0xFFFFFFF0ull) L.node_cap = 0xFFFFFFF0ull;
+    return L;
+}
+
+uint64_t node_capacity_bound(uint64_t n, const fp_params& p) { return oct_layout(n, p).node_cap; }
+
+struct OctBufs {
+    SortScratch sc;
+    uint64_t *t_k1, *t_k2, *t_k3;
+    uint32_t *t_j1, *t_j2, *t_j3;
+    int4* lt_pt;
+    uint32_t *lt_val, *lt_k32;
+    uint32_t *pyr, *cstart;
+    uint8_t* cell_leaf;
+    uint64_t* gk;
+    uint32_t* gj;
+    Piece* pieces;
+    uint32_t* counters;
+    uint64_t *pk, *pk2, *pk3;
+    uint32_t *pv, *pv2;
+    OpenNode* open[2];
+    uint32_t *ocount, *bigstart;
+    NodeRec* nrec;
+    uint64_t *nk, *nk2, *nk3, *nk4;
+    uint32_t *nl, *nv2, *nv3;
+    uint8_t* slevel;
+    uint32_t *idxtab, *leafw, *nown;
+    uint8_t *own_code, *leaf_code;
+    uint32_t* leafid;
+};
+
+// one carve-up serves both the size query (base == nullptr) and the launch
+static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
+{
+    OctBufs B;
+    const uint64_t N = n ? n : 1;
+    B.sc = take_sort_scratch(ws, std::max<uint64_t>(N, std::max(Ly.node_cap, Ly.piece_cap)));
+    // aliased phase region: grouping temporaries, later the leaf scatter temporaries
+    const size_t phase_base = ws.used;
+    B.t_k1 = ws.take<uint64_t>(N); B.t_j1 = ws.take<uint32_t>(N);
+    B.t_k2 = ws.take<uint64_t>(N); B.t_j2 = ws.take<uint32_t>(N);
+    B.t_k3 = ws.take<uint64_t>(N); B.t_j3 = ws.take<uint32_t>(N);
+    const size_t phase_end = ws.used;
+    ws.used = phase_base;
+    B.lt_pt = ws.take<int4>(N); B.lt_val = ws.take<uint32_t>(N); B.lt_k32 = ws.take<uint32_t>(N);
+    ws.used = std::max(phase_end, ws.used);
+    B.pyr = ws.take<uint32_t>(Ly.npyr ? Ly.npyr : 1);
+    B.cstart = ws.take<uint32_t>(Ly.cells + 1);
+    B.cell_leaf = ws.take<uint8_t>(Ly.cells);
+    B.gk = ws.take<uint64_t>(N); B.gj = ws.take<uint32_t>(N);
+    B.pieces = ws.take<Piece>(Ly.piece_cap);
+    B.counters = ws.take<uint32_t>(4);
+    B.pk = ws.take<uint64_t>(Ly.piece_cap); B.pk2 = ws.take<uint64_t>(Ly.piece_cap);
+    B.pk3 = ws.take<uint64_t>(Ly.piece_cap);
+    B.pv = ws.take<uint32_t>(Ly.piece_cap); B.pv2 = ws.take<uint32_t>(Ly.piece_cap);
+    B.open[0] = ws.take<OpenNode>(Ly.open_cap); B.open[1] = ws.take<OpenNode>(Ly.open_cap);
+    B.ocount = ws.take<uint32_t>(4);
+    B.bigstart = ws.take<uint32_t>(Ly.open_cap + 1);
+    B.nrec = ws.take<NodeRec>(Ly.node_cap);
+    B.nk = ws.take<uint64_t>(Ly.node_cap); B.nk2 = ws.take<uint64_t>(Ly.node_cap);
+    B.nk3 = ws.take<uint64_t>(Ly.node_cap); B.nk4 = ws.take<uint64_t>(Ly.node_cap);
+    B.nl = ws.take<uint32_t>(Ly.node_cap); B.nv2 = ws.take<uint32_t>(Ly.node_cap);
+    B.nv3 = ws.take<uint32_t>(Ly.node_cap);
+    B.slevel = ws.take<uint8_t>(Ly.node_cap);
+    B.idxtab = ws.take<uint32_t>(Ly.cells * 8 / 7 + 8);
+    B.leafw = ws.take<uint32_t>(std::max<uint64_t>(Ly.node_cap, kScanMaxTiles));
+    B.nown = ws.take<uint32_t>(Ly.node_cap);
+    B.own_code = ws.take<uint8_t>(N); B.leaf_code = ws.take<uint8_t>(N);
+    B.leafid = ws.take<uint32_t>(N);
+    return B;
+}
+
+size_t octree_ws_bytes(uint64_t n, const fp_params& p)
+{
+    Workspace dry;
+    oct_carve(dry, n, oct_layout(n, p));
+    return dry.used;
+}
+
+template <int DIG, bool CPT, bool CK64, bool CK32>
+static cudaError_t run_sort(const SortScratch& sc, SortArgs a, const Workspace& ws, cudaStream_t st)
+{
+    for (int slot = 0; slot < kSortMaxPass; ++slot) {
+        cudaError_t e = sort_run_pass<DIG, CPT, CK64, CK32>(sc, a, slot, ws.num_sms, st);
+        if (e) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t n, const fp_cube* cube,
+                          const fp_chunk* chunks, const uint32_t* num_chunks, const uint64_t* offsets,
+                          const uint32_t* counts, const fp_params& prm, fp_node* nodes, uint32_t node_cap,
+                          uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
+                          const Workspace& ws, cudaStream_t st)
+{
+    (void)chunks; (void)num_chunks; (void)offsets;   // chunk ranges are implied by the cell grouping
+    cudaError_t e;
+    if (n == 0) {
+        k_set_u32<<<1, 1, 0, st>>>(num_nodes, 0);
+        return cudaGetLastError();
+    }
+    const int g = (int)prm.grid_log2, s = (int)prm.sub_log2, lmax = (int)prm.max_level;
+    const int dl = std::min(kKeyLevels, std::max(s + lmax - 1, g + 1));
+    const OctLayout Ly = oct_layout(n, prm);
+    const uint64_t N = n;
+    const OctBufs B = oct_carve(ws, n, Ly);
+    const SortScratch& sc = B.sc;
+    uint32_t* npieces = B.counters;
+    uint32_t* nnode = B.counters + 3;
+    if ((e = cudaMemsetAsync(B.counters, 0, 4 * sizeof(uint32_t), st))) return e;
+    if ((e = cudaMemsetAsync(B.ocount, 0, 4 * sizeof(uint32_t), st))) return e;
+
+    // 1. pyramid and per-cell starts
+    for (int l = g - 1; l >= 0; --l) {
+        uint64_t np_ = 1ull << (3 * l);
+        const uint32_t* child = l + 1 == g ? counts : B.pyr + ((1ull << (3 * (l + 1))) - 1) / 7;
+        k_pyr_level<<<(unsigned)((np_ + 255) / 256), 256, 0, st>>>(child, B.pyr + (np_ - 1) / 7, np_);
+    }
+    if ((e = scan_exclusive<uint32_t, uint32_t>(counts, B.cstart, Ly.cells, nullptr, B.leafw, B.cstart + Ly.cells,
+                                                (uint32_t*)nullptr, st)))
+        return e;
+    OctCtx c;
+    c.counts = counts; c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
+    c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
+    c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
+    c.own_code = B.own_code; c.leaf_code = B.leaf_code; c.open_cap = (uint32_t)Ly.open_cap;
+    c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
+
+    // 2. group by level-g cell: stable scatter of (key21, j) by cell id
+    {
+        if ((e = sort_plan_weights(sc, counts, nullptr, nullptr, Ly.cells, 3 * (kKeyLevels - g), st))) return e;
+        SortArgs a{};
+        a.b.pt_src = reinterpret_cast<const int4*>(sorted);
+        a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.gk;
+        a.b.val_src = nullptr; a.b.val_tmp = B.t_j1; a.b.val_dst = B.gj;
+        a.n = N; a.cube = cube; a.g = g; a.err = ws.err;
+        if ((e = sort_run_pass<DIG_CELL, false, true, false>(sc, a, 0, ws.num_sms, st))) return e;
+        for (int slot = 1; slot < kSortMaxPass; ++slot)
+            if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a, slot, ws.num_sms, st))) return e;
+    }
+    // 3. cells: pieces, leaf levels, open big cells
+    k_cell_setup<<<(unsigned)((Ly.cells + 255) / 256), 256, 0, st>>>(c, B.open[0], B.ocount);
+    // 4. big cells: key-sort their records (key = big rank, sub-key to level dl), write back, split
+    {
+        const uint32_t cap = (uint32_t)Ly.open_cap;
+        k_open_counts<<<(cap + 255) / 256, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, cap);
+        if ((e = scan_exclusive<uint32_t, uint32_t>(B.bigstart, B.bigstart, cap, nullptr, B.leafw, B.ocount + 3,
+                                                    (uint32_t*)nullptr, st)))
+            return e;
+        int gw = std::max(1, std::min(ws.num_sms * 16, (int)(((uint64_t)cap * 32 + 255) / 256)));
+        k_big_gather<<<gw, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.gk, B.gj, B.t_k2, B.t_j2, g, dl);
+        int rank_bits = 1;
+        while ((1ull << rank_bits) < std::min<uint64_t>(Ly.open_cap, Ly.cells)) ++rank_bits;
+        const uint32_t total_bits = (uint32_t)(3 * (dl - g) + rank_bits);
+        if ((e = sort_plan_keys(sc, B.t_k2, N, B.ocount + 3, 0, total_bits, st))) return e;
+        SortArgs a{};
+        a.b.k64_src = B.t_k2; a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.t_k3;
+        a.b.val_src = B.t_j2; a.b.val_tmp = B.t_j1; a.b.val_dst = B.t_j3;
+        a.n = N; a.d_n = B.ocount + 3; a.err = ws.err;
+        if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
+        k_big_scatter<<<gw, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.t_k3, B.t_j3, B.gk, B.gj, g, dl);
+        int cur = 0;
+        for (int q = g; q < dl; ++q) {
+            k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
+            k_split<<<gw, 256, 0, st>>>(c, B.open[cur], B.ocount + cur, B.open[1 - cur], B.ocount + (1 - cur), cap);
+            cur = 1 - cur;
+        }
+    }
+    // 5. nodes at levels <= g
+    {
+        uint64_t total = (Ly.cells * 8 - 1) / 7;
+        k_nodes_upper<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c);
+    }
+    // 6. pieces in record order, then the units
+    {
+        const uint32_t pcap = (uint32_t)Ly.piece_cap;
+        k_clamp<<<1, 1, 0, st>>>(npieces, pcap);
+        k_piece_keys<<<(pcap + 255) / 256, 256, 0, st>>>(B.pieces, npieces, pcap, B.pk);
+        int bits = 1;
+        while ((1ull << bits) <= N) ++bits;
+        if ((e = sort_plan_keys(sc, B.pk, pcap, npieces, 0, (uint32_t)bits, st))) return e;
+        SortArgs a{};
+        a.b.k64_src = B.pk; a.b.k64_tmp = B.pk2; a.b.k64_dst = B.pk3;
+        a.b.val_src = nullptr; a.b.val_tmp = B.pv2; a.b.val_dst = B.pv;
+        a.n = pcap; a.d_n = npieces; a.err = ws.err;
+        if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
+        const size_t smem = sizeof(UnitSmem);
+        if ((e = cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        uint64_t nunits = (N + kWindow - 1) / kWindow;
+        int grid = (int)std::min<uint64_t>(nunits, (uint64_t)ws.num_sms * 2);
+        k_units<<<grid, kUnitNT, smem, st>>>(c, B.pk3, B.pv, N);
+        k_dup_pieces<<<ws.num_sms, 256, 0, st>>>(c);
+    }
+    // 7. node table in preorder: stable sort by level, then by start at max_level resolution
+    {
+        const uint32_t ncap = (uint32_t)Ly.node_cap;
+        const unsigned gn = (ncap + 255) / 256;
+        k_clamp<<<1, 1, 0, st>>>(nnode, ncap);
+        k_node_keys<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nk, B.nl, lmax);
+        k_level_keys<<<gn, 256, 0, st>>>(B.nl, nnode, B.nk3);
+        if ((e = sort_plan_keys(sc, B.nk3, ncap, nnode, 0, 5, st))) return e;
+        SortArgs a{};
+        a.b.k64_src = B.nk3; a.b.k64_tmp = B.nk2; a.b.k64_dst = B.nk4;
+        a.b.val_src = nullptr; a.b.val_tmp = B.nv2; a.b.val_dst = B.nv3;
+        a.n = ncap; a.d_n = nnode; a.err = ws.err;
+        if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
+        k_gather_u64<<<gn, 256, 0, st>>>(B.nk, B.nv3, nnode, B.nk3);
+        if ((e = sort_plan_keys(sc, B.nk3, ncap, nnode, 0, (uint32_t)std::max(1, 3 * lmax), st))) return e;
+        SortArgs b2{};
+        b2.b.k64_src = B.nk3; b2.b.k64_tmp = B.nk2; b2.b.k64_dst = B.nk;   // nk <- sorted starts
+        b2.b.val_src = B.nv3; b2.b.val_tmp = B.nv2; b2.b.val_dst = B.nl;   // nl <- record of preorder position
+        b2.n = ncap; b2.d_n = nnode; b2.err = ws.err;
+        if ((e = run_sort<DIG_K64, false, true, false>(sc, b2, ws, st))) return e;
+        k_node_write<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, num_nodes, B.idxtab,
+                                         B.leafw, g, lmax, ws.err);
+        k_node_fill<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, lmax);
+        k_node_children<<<gn, 256, 0, st>>>(nnode, B.nk, B.slevel, nodes, node_cap, lmax);
+        if ((e = cudaMemsetAsync(B.nown, 0, (size_t)ncap * sizeof(uint32_t), st))) return e;
+    }
+    // 8. owner and leaf ids per distributed point, owned counts
+    {
+        int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
+        k_resolve<<<grid, 256, 0, st>>>(sorted, N, cube, B.own_code, B.leaf_code, B.idxtab, B.nk, B.slevel, nnode,
+                                        owner, B.leafid, B.nown, g, lmax, ws.err);
+        k_write_nown<<<(unsigned)((Ly.node_cap + 255) / 256), 256, 0, st>>>(nodes, nnode, node_cap, B.nown);
+    }
+    // 9. leaf-grouped points: stable scatter by leaf id
+    if (leaf_pts || leaf_perm) {
+        if ((e = sort_plan_weights(sc, B.leafw, nullptr, nnode, Ly.node_cap, 0, st))) return e;
+        SortArgs a{};
+        a.b.pt_src = reinterpret_cast<const int4*>(sorted);
+        a.b.pt_tmp = B.lt_pt;
+        a.b.pt_dst = reinterpret_cast<int4*>(leaf_pts);
+        a.b.val_src = perm; a.b.val_tmp = B.lt_val; a.b.val_dst = leaf_perm;
+        a.b.k32_src = B.leafid; a.b.k32_tmp = B.lt_k32; a.b.k32_dst = nullptr;
+        a.n = N; a.err = ws.err;
+        if (leaf_pts) e = run_sort<DIG_K32, true, false, true>(sc, a, ws, st);
+        else e = run_sort<DIG_K32, false, false, true>(sc, a, ws, st);
+        if (e) return e;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ subsample
+__global__ void k_nown_in(const fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, uint32_t* nown)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t M = *num_nodes < node_cap ? *num_nodes : node_cap;
+    if (i < M) nown[i] = nodes[i].n_own;
+}
+
+__global__ void k_first_out(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const uint64_t* first)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t M = *num_nodes < node_cap ? *num_nodes : node_cap;
+    if (i < M) nodes[i].first = first[i];
+}
+
+// owner segments whose original indices are not ascending (owners above the chunks)
+__global__ void k_mark_unsorted(const uint32_t* fown, const uint32_t* fperm, uint64_t n, uint32_t* mark,
+                                const uint32_t* nm)
+{
+    const uint32_t M = *nm;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f + 1 < n; f += stride)
+        if (fown[f] == fown[f + 1] && fperm[f] > fperm[f + 1] && fown[f] < M) mark[fown[f]] = 1;
+}
+
+__global__ void k_clamp_copy(const uint32_t* v, uint32_t cap, uint32_t* out) { *out = *v < cap ? *v : cap; }
+
+__global__ void k_stitch_list(const uint32_t* mark, const uint32_t* mrank, const uint32_t* num_nodes,
+                              uint32_t node_cap, uint32_t* mlist, const uint32_t* nown, uint32_t* mown)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t M = *num_nodes < node_cap ? *num_nodes : node_cap;
+    if (i < M && mark[i]) {
+        mlist[mrank[i]] = i;
+        mown[mrank[i]] = nown[i];
+    }
+}
+
+// keys (rank << 32 | original index) of the points of marked nodes, value = final position
+__global__ void k_stitch_keys(const uint32_t* mlist, const uint32_t* nmarked, const uint32_t* soff,
+                              const uint32_t* nown, const uint64_t* first, const uint32_t* fperm, uint64_t* key,
+                              uint32_t* val)
+{
+    const uint32_t nm = *nmarked;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = warp; r < nm; r += nwarps) {
+        const uint32_t node = mlist[r];
+        const uint32_t cnt = nown[node];
+        const uint64_t f0 = first[node];
+        for (uint32_t t = lane; t < cnt; t += 32) {
+            key[soff[r] + t] = ((uint64_t)r << 32) | fperm[f0 + t];
+            val[soff[r] + t] = (uint32_t)(f0 + t);
+        }
+    }
+}
+
+__global__ void k_stitch_gather(const uint32_t* nstitch, const uint32_t* val, const int4* fin, const uint32_t* fperm,
+                                int4* tpt, uint32_t* tperm)
+{
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *nstitch) return;
+    tpt[t] = fin[val[t]];
+    tperm[t] = fperm[val[t]];
+}
+
+__global__ void k_stitch_put(const uint32_t* nstitch, const uint64_t* key, const uint32_t* mlist, const uint32_t* soff,
+                             const uint64_t* first, const int4* tpt, const uint32_t* tperm, int4* fin, uint32_t* fperm)
+{
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *nstitch) return;
+    uint32_t r = (uint32_t)(key[t] >> 32);
+    uint64_t f = first[mlist[r]] + (t - soff[r]);
+    fin[f] = tpt[t];
+    fperm[f] = tperm[t];
+}
+
+static const uint64_t kMaxScanNodes = (uint64_t)kScanTile * kScanMaxTiles;
+
+struct SubBufs {
+    SortScratch sc;
+    uint32_t *nown, *mark, *mrank, *mlist, *mown, *soff, *cnt;
+    uint64_t* first;
+    int4* t_pt;
+    uint32_t *t_val, *t_k32, *fown;
+    uint64_t *s_key, *s_key2, *s_key3;
+    uint32_t *s_val, *s_val2, *s_val3;
+    int4* s_pt;
+    uint32_t* s_perm;
+    uint64_t* tiles64;
+    uint32_t* tiles32;
+};
+
+static SubBufs sub_carve(const Workspace& ws, uint64_t n, uint64_t M)
+{
+    SubBufs B;
+    const uint64_t N = n ? n : 1;
+    B.sc = take_sort_scratch(ws, N);
+    B.nown = ws.take<uint32_t>(M); B.first = ws.take<uint64_t>(M + 1);
+    B.mark = ws.take<uint32_t>(M); B.mrank = ws.take<uint32_t>(M); B.mlist = ws.take<uint32_t>(M);
+    B.mown = ws.take<uint32_t>(M); B.soff = ws.take<uint32_t>(M + 1); B.cnt = ws.take<uint32_t>(4);
+    B.t_pt = ws.take<int4>(N); B.t_val = ws.take<uint32_t>(N); B.t_k32 = ws.take<uint32_t>(N);
+    B.fown = ws.take<uint32_t>(N);
+    B.s_key = ws.take<uint64_t>(N); B.s_val = ws.take<uint32_t>(N);
+    B.s_key2 = ws.take<uint64_t>(N); B.s_val2 = ws.take<uint32_t>(N);
+    B.s_key3 = ws.take<uint64_t>(N); B.s_val3 = ws.take<uint32_t>(N);
+    B.s_pt = ws.take<int4>(N); B.s_perm = ws.take<uint32_t>(N);
+    B.tiles64 = ws.take<uint64_t>(kScanMaxTiles); B.tiles32 = ws.take<uint32_t>(kScanMaxTiles);
+    return B;
+}
+
+size_t subsample_ws_bytes(uint64_t n, uint64_t node_cap)
+{
+    Workspace dry;
+    sub_carve(dry, n, std::max<uint64_t>(node_cap, 1));
+    return dry.used;
+}
+
+cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const fp_point* sorted,
+                             const uint32_t* perm, const uint32_t* owner, uint64_t n, fp_point* final_pts,
+                             uint32_t* final_perm, const Workspace& ws, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    if (node_cap > kMaxScanNodes) return cudaErrorInvalidValue;
+    cudaError_t e;
+    const uint64_t N = n;
+    const uint32_t M = node_cap;
+    const SubBufs B = sub_carve(ws, n, M);
+    const SortScratch& sc = B.sc;
+    uint32_t *nown = B.nown, *mark = B.mark, *mrank = B.mrank, *mlist = B.mlist, *mown = B.mown, *soff = B.soff;
+    uint32_t* cnt = B.cnt;
+    uint64_t* first = B.first;
+    int4* t_pt = B.t_pt;
+    uint32_t *t_val = B.t_val, *t_k32 = B.t_k32, *fown = B.fown;
+    uint64_t *s_key = B.s_key, *s_key2 = B.s_key2, *s_key3 = B.s_key3;
+    uint32_t *s_val = B.s_val, *s_val2 = B.s_val2, *s_val3 = B.s_val3;
+    int4* s_pt = B.s_pt;
+    uint32_t* s_perm = B.s_perm;
+    uint64_t* tiles64 = B.tiles64;
+    uint32_t* tiles32 = B.tiles32;
+    const unsigned gM = (M + 255) / 256;
+
+    uint32_t* nm = cnt + 2;   // node count clamped to the capacity
+    k_clamp_copy<<<1, 1, 0, st>>>(num_nodes, node_cap, nm);
+    k_nown_in<<<gM, 256, 0, st>>>(nodes, num_nodes, node_cap, nown);
+    if ((e = scan_exclusive<uint32_t, uint64_t>(nown, first, M, nm, tiles64, (uint64_t*)nullptr,
+                                                (uint64_t*)nullptr, st)))
+        return e;
+    k_first_out<<<gM, 256, 0, st>>>(nodes, num_nodes, node_cap, first);
+    // stable scatter by owner id (index order inside every chunk)
+    if ((e = sort_plan_weights(sc, nown, nullptr, nm, M, 0, st))) return e;
+    SortArgs a{};
+    a.b.pt_src = reinterpret_cast<const int4*>(sorted); a.b.pt_tmp = t_pt;
+    a.b.pt_dst = reinterpret_cast<int4*>(final_pts);
+    a.b.val_src = perm; a.b.val_tmp = t_val; a.b.val_dst = final_perm;
+    a.b.k32_src = owner; a.b.k32_tmp = t_k32; a.b.k32_dst = fown;
+    a.n = N; a.err = ws.err;
+    for (int slot = 0; slot < kSortMaxPass; ++slot)
+        if ((e = sort_run_pass<DIG_K32, true, false, true>(sc, a, slot, ws.num_sms, st))) return e;
+    // stitch: owner segments spanning several chunks, re-sorted by original index
+    if ((e = cudaMemsetAsync(mark, 0, (size_t)M * 4, st))) return e;
+    int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
+    k_mark_unsorted<<<grid, 256, 0, st>>>(fown, final_perm, N, mark, nm);
+    if ((e = scan_exclusive<uint32_t, uint32_t>(mark, mrank, M, nm, tiles32, cnt, (uint32_t*)nullptr, st)))
+        return e;
+    k_stitch_list<<<gM, 256, 0, st>>>(mark, mrank, num_nodes, node_cap, mlist, nown, mown);
+    if ((e = scan_exclusive<uint32_t, uint32_t>(mown, soff, M, cnt, tiles32, cnt + 1, (uint32_t*)nullptr, st)))
+        return e;
+    int gw = std::max(1, std::min(ws.num_sms * 16, (int)((M * 32ull + 255) / 256)));
+    k_stitch_keys<<<gw, 256, 0, st>>>(mlist, cnt, soff, nown, first, final_perm, s_key, s_val);
+    int rank_bits = 1;
+    while ((1ull << rank_bits) < M) ++rank_bits;
+    if ((e = sort_plan_keys(sc, s_key, N, cnt + 1, 0, (uint32_t)(32 + rank_bits), st))) return e;
+    SortArgs b{};
+    b.b.k64_src = s_key; b.b.k64_tmp = s_key2; b.b.k64_dst = s_key3;
+    b.b.val_src = s_val; b.b.val_tmp = s_val2; b.b.val_dst = s_val3;
+    b.n = N; b.d_n = cnt + 1; b.err = ws.err;
+    for (int slot = 0; slot < kSortMaxPass; ++slot)
+        if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, b, slot, ws.num_sms, st))) return e;
+    unsigned gN = (unsigned)((N + 255) / 256);
+    k_stitch_gather<<<gN, 256, 0, st>>>(cnt + 1, s_val3, reinterpret_cast<const int4*>(final_pts), final_perm, s_pt,
+                                        s_perm);
+    k_stitch_put<<<gN, 256, 0, st>>>(cnt + 1, s_key3, mlist, soff, first, s_pt, s_perm,
+                                     reinterpret_cast<int4*>(final_pts), final_perm);
+    return cudaGetLastError();
+}
+
+
+
+}  // namespace fp

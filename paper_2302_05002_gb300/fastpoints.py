@@ -1,0 +1,287 @@
+"""Python binding of libfastpoints (the C ABI in include/fastpoints.h).
+
+Argument marshalling only: every stage runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  Points are int32 tensors of shape
+(n, 4) on the device: x, y, z and the four colour bytes packed in the last
+column (the 16-byte fp_point record).  Functions keep the C names; each raises
+FastPointsError on a non-zero status.  There is no CPU path: without the built
+library or a CUDA device the calls fail.
+"""
+import ctypes
+import os
+import re
+
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "fastpoints.h")
+
+
+class FastPointsError(RuntimeError):
+    pass
+
+
+class fp_params(ctypes.Structure):
+    _fields_ = [("grid_log2", ctypes.c_uint32), ("sub_log2", ctypes.c_uint32), ("max_level", ctypes.c_uint32),
+                ("decim_modulus", ctypes.c_uint32), ("chunk_threshold", ctypes.c_uint64),
+                ("node_capacity", ctypes.c_uint64)]
+
+
+STAGE = dict(bounds=0, decimate=1, bounds_decimate=2, count=3, merge=4, distribute=5, octree=6, subsample=7)
+ERR_BITS = {1 << 6: "timeout", 1 << 9: "capacity"}
+NODE_BYTES, CHUNK_BYTES, CUBE_BYTES = 40, 16, 32
+
+_lib = None
+
+
+def load():
+    """Load libfastpoints.so (building it in-tree when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    p, u64, u32, sz, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "fp_workspace_size": (sz, [i32, u64, p]),
+        "fp_status_string": (ctypes.c_char_p, [st]),
+        "fp_node_capacity_bound": (u32, [u64, p]),
+        "fp_get_device_error": (st, [p, p, i32]),
+        "fp_bounds": (st, [p, u64, p, p, sz, p]),
+        "fp_decimate": (st, [p, u64, u64, u32, p, u64, p, p, sz, p]),
+        "fp_bounds_decimate": (st, [p, u64, p, u64, u32, p, u64, p, p, sz, p]),
+        "fp_count": (st, [p, u64, p, u32, p, i32, p, sz, p]),
+        "fp_merge_chunks": (st, [p, u32, u64, p, p, p, p, p, sz, p]),
+        "fp_distribute": (st, [p, u64, p, u32, p, p, p, p, p, p, sz, p]),
+        "fp_build_chunk_octree": (st, [p, p, u64, p, p, p, p, p, p, p, u32, p, p, p, p, p, sz, p]),
+        "fp_subsample": (st, [p, p, u32, p, p, p, u64, p, p, p, sz, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+def declared_functions():
+    """Names of the functions include/fastpoints.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:fp_status|size_t|const char\*)\s+(fp_\w+)\s*\(", text, re.M)))
+
+
+def params(grid_log2=7, sub_log2=7, max_level=15, decim_modulus=16, chunk_threshold=100000, node_capacity=20000):
+    return fp_params(grid_log2, sub_log2, max_level, decim_modulus, chunk_threshold, node_capacity)
+
+
+def _check(status, what):
+    if status != 0:
+        msg = load().fp_status_string(status).decode()
+        raise FastPointsError("%s failed: %s (status %d)" % (what, msg, status))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t):
+    return t.device if t is not None else torch.device("cuda", torch.cuda.current_device())
+
+
+def workspace_size(stage, n, prm=None):
+    return int(load().fp_workspace_size(STAGE[stage], n, ctypes.byref(prm) if prm is not None else None))
+
+
+def _ws(stage, n, prm, device, ws=None):
+    need = workspace_size(stage, n, prm)
+    if ws is not None and ws.numel() >= need:
+        return ws, need
+    return torch.empty(max(need, 1), dtype=torch.uint8, device=device), need
+
+
+def as_points(x, device="cuda"):
+    """numpy structured array / bytes / int32 (n, 4) tensor -> int32 (n, 4) CUDA tensor."""
+    if isinstance(x, torch.Tensor):
+        t = x
+    else:
+        import numpy as np
+        a = np.ascontiguousarray(x).view(np.int32).reshape(-1, 4)
+        t = torch.from_numpy(a)
+    assert t.dtype == torch.int32 and t.dim() == 2 and t.shape[1] == 4
+    return t.to(device).contiguous()
+
+
+def get_device_error(stream=None, clear=True):
+    v = ctypes.c_uint32(0)
+    _check(load().fp_get_device_error(_stream(stream), ctypes.byref(v), int(clear)), "fp_get_device_error")
+    return v.value
+
+
+# ------------------------------------------------------------------ stages
+def fp_bounds(pts, stream=None, ws=None):
+    n = pts.shape[0]
+    cube = torch.empty(CUBE_BYTES // 4, dtype=torch.int32, device=_dev(pts))
+    w, need = _ws("bounds", n, None, _dev(pts), ws)
+    _check(load().fp_bounds(_ptr(pts), n, _ptr(cube), _ptr(w), w.numel(), _stream(stream)), "fp_bounds")
+    return cube
+
+
+def _preview_cap(n, modulus):
+    # the kept count is a sum of n Bernoulli(1/m) draws: mean n/m, far below this bound
+    return n if modulus <= 2 else min(n, n // modulus + 64 + 8 * int((n / modulus) ** 0.5 + 1) * 4)
+
+
+def fp_decimate(pts, first_index=0, modulus=16, out=None, stream=None, ws=None):
+    n = pts.shape[0]
+    cap = out.shape[0] if out is not None else _preview_cap(n, modulus)
+    if out is None:
+        out = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=_dev(pts))
+    count = torch.zeros(1, dtype=torch.int64, device=_dev(pts))
+    w, need = _ws("decimate", n, None, _dev(pts), ws)
+    _check(load().fp_decimate(_ptr(pts), n, first_index, modulus, _ptr(out), cap, _ptr(count), _ptr(w), w.numel(),
+                              _stream(stream)), "fp_decimate")
+    return out, count
+
+
+def fp_bounds_decimate(pts, first_index=0, modulus=16, out=None, stream=None, ws=None):
+    n = pts.shape[0]
+    cap = out.shape[0] if out is not None else _preview_cap(n, modulus)
+    if out is None:
+        out = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=_dev(pts))
+    cube = torch.empty(CUBE_BYTES // 4, dtype=torch.int32, device=_dev(pts))
+    count = torch.zeros(1, dtype=torch.int64, device=_dev(pts))
+    w, need = _ws("bounds_decimate", n, None, _dev(pts), ws)
+    _check(load().fp_bounds_decimate(_ptr(pts), n, _ptr(cube), first_index, modulus, _ptr(out), cap, _ptr(count),
+                                     _ptr(w), w.numel(), _stream(stream)), "fp_bounds_decimate")
+    return cube, out, count
+
+
+def fp_count(pts, cube, grid_log2=7, counts=None, accumulate=False, stream=None):
+    n = pts.shape[0]
+    if counts is None:
+        counts = torch.empty(1 << (3 * grid_log2), dtype=torch.int32, device=_dev(pts))
+    _check(load().fp_count(_ptr(pts), n, _ptr(cube), grid_log2, _ptr(counts), int(accumulate), None, 0,
+                           _stream(stream)), "fp_count")
+    return counts
+
+
+def fp_merge_chunks(counts, grid_log2, threshold, stream=None, ws=None):
+    dev = counts.device
+    cells = 1 << (3 * grid_log2)
+    chunks = torch.empty((cells, CHUNK_BYTES // 8), dtype=torch.int64, device=dev)
+    num = torch.zeros(1, dtype=torch.int32, device=dev)
+    lut = torch.empty(cells, dtype=torch.int32, device=dev)
+    offsets = torch.empty(cells + 1, dtype=torch.int64, device=dev)
+    prm = params(grid_log2=grid_log2)
+    w, need = _ws("merge", 0, prm, dev, ws)
+    _check(load().fp_merge_chunks(_ptr(counts), grid_log2, threshold, _ptr(chunks), _ptr(num), _ptr(lut),
+                                  _ptr(offsets), _ptr(w), w.numel(), _stream(stream)), "fp_merge_chunks")
+    return chunks, num, lut, offsets
+
+
+def fp_distribute(pts, cube, grid_log2, lut, offsets, num_chunks, with_perm=True, out=None, perm=None,
+                  stream=None, ws=None):
+    n = pts.shape[0]
+    dev = _dev(pts)
+    if out is None:
+        out = torch.empty_like(pts)
+    if with_perm and perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+    prm = params(grid_log2=grid_log2)
+    w, need = _ws("distribute", n, prm, dev, ws)
+    _check(load().fp_distribute(_ptr(pts), n, _ptr(cube), grid_log2, _ptr(lut), _ptr(offsets), _ptr(num_chunks),
+                                _ptr(out), _ptr(perm) if with_perm else None, _ptr(w), w.numel(), _stream(stream)),
+           "fp_distribute")
+    return out, perm
+
+
+def node_capacity_bound(n, prm):
+    return int(load().fp_node_capacity_bound(n, ctypes.byref(prm)))
+
+
+def fp_build_chunk_octree(sorted_pts, perm, cube, chunks, num_chunks, offsets, counts, prm, node_cap=None,
+                          leaf=True, stream=None, ws=None):
+    n = sorted_pts.shape[0]
+    dev = _dev(sorted_pts)
+    if node_cap is None:
+        node_cap = node_capacity_bound(n, prm)
+    nodes = torch.zeros((node_cap, NODE_BYTES // 8), dtype=torch.int64, device=dev)
+    num_nodes = torch.zeros(1, dtype=torch.int32, device=dev)
+    leaf_pts = torch.empty_like(sorted_pts) if leaf else None
+    leaf_perm = torch.empty(n, dtype=torch.int32, device=dev) if leaf else None
+    owner = torch.empty(n, dtype=torch.int32, device=dev)
+    w, need = _ws("octree", n, prm, dev, ws)
+    _check(load().fp_build_chunk_octree(_ptr(sorted_pts), _ptr(perm), n, _ptr(cube), _ptr(chunks), _ptr(num_chunks),
+                                        _ptr(offsets), _ptr(counts), ctypes.byref(prm), _ptr(nodes), node_cap,
+                                        _ptr(num_nodes), _ptr(leaf_pts), _ptr(leaf_perm), _ptr(owner), _ptr(w),
+                                        w.numel(), _stream(stream)), "fp_build_chunk_octree")
+    return nodes, num_nodes, leaf_pts, leaf_perm, owner
+
+
+def fp_subsample(nodes, num_nodes, sorted_pts, perm, owner, prm, stream=None, ws=None, final=None, final_perm=None):
+    """nodes must have been allocated with node_capacity_bound(n, prm) rows (the
+    workspace size assumes that node_cap)."""
+    n = sorted_pts.shape[0]
+    dev = _dev(sorted_pts)
+    if final is None:
+        final = torch.empty_like(sorted_pts)
+    if final_perm is None:
+        final_perm = torch.empty(n, dtype=torch.int32, device=dev)
+    w, need = _ws("subsample", n, prm, dev, ws)
+    _check(load().fp_subsample(_ptr(nodes), _ptr(num_nodes), nodes.shape[0], _ptr(sorted_pts), _ptr(perm),
+                               _ptr(owner), n, _ptr(final), _ptr(final_perm), _ptr(w), w.numel(), _stream(stream)),
+           "fp_subsample")
+    return final, final_perm
+
+
+# ------------------------------------------------------------------ decoding
+def cube_to_host(cube):
+    import numpy as np
+    b = cube.cpu().numpy().view(np.uint8)
+    o = b[0:12].view(np.int32)
+    mx = b[12:24].view(np.int32)
+    S = int(b[24:32].view(np.uint64)[0])
+    return o.tolist(), mx.tolist(), S
+
+
+def chunks_to_host(chunks, num):
+    import numpy as np
+    K = int(num.item())
+    a = chunks[:K].cpu().numpy().view(np.uint8).reshape(K, 16)
+    dt = np.dtype([("key", "<u8"), ("count", "<u4"), ("level", "<u4")])
+    return a.copy().view(dt).reshape(K)
+
+
+def nodes_to_host(nodes, num):
+    import numpy as np
+    M = int(num.item())
+    a = nodes[:M].cpu().numpy().view(np.uint8).reshape(M, 40)
+    dt = np.dtype([("key", "<u8"), ("first", "<u8"), ("leaf_first", "<u8"), ("count", "<u4"), ("n_own", "<u4"),
+                   ("n_desc", "<u4"), ("level", "u1"), ("child_mask", "u1"), ("is_leaf", "u1"), ("pad", "u1")])
+    return a.copy().view(dt).reshape(M)
+
+
+def build_octree(pts, prm, stream=None):
+    """The whole hot path on one cloud (int32 (n, 4) CUDA tensor); returns a dict
+    of device tensors: cube, preview (+count), counts, chunks (+count), lut,
+    offsets, distributed points + perm, nodes (+count), leaf-grouped points +
+    perm, owner per distributed point, final points + perm."""
+    n = pts.shape[0]
+    cube, prev, prev_n = fp_bounds_decimate(pts, 0, prm.decim_modulus, stream=stream)
+    counts = fp_count(pts, cube, prm.grid_log2, stream=stream)
+    chunks, num_chunks, lut, offsets = fp_merge_chunks(counts, prm.grid_log2, prm.chunk_threshold, stream=stream)
+    dist, perm = fp_distribute(pts, cube, prm.grid_log2, lut, offsets, num_chunks, stream=stream)
+    nodes, num_nodes, leaf_pts, leaf_perm, owner = fp_build_chunk_octree(dist, perm, cube, chunks, num_chunks, offsets,
+                                                                         counts, prm, stream=stream)
+    final, final_perm = fp_subsample(nodes, num_nodes, dist, perm, owner, prm, stream=stream)
+    return dict(cube=cube, preview=prev, preview_count=prev_n, counts=counts, chunks=chunks, num_chunks=num_chunks,
+                lut=lut, offsets=offsets, dist=dist, perm=perm, nodes=nodes, num_nodes=num_nodes, leaf_pts=leaf_pts,
+                leaf_perm=leaf_perm, owner=owner, final=final, final_perm=final_perm)
