@@ -1,0 +1,351 @@
+"""Benchmark of the octree-construction hot path (one step = every stage of one
+plain build: bounds + preview, count grid, chunk merge, stable distribution,
+chunk octrees + LOD selection, final LOD layout) on synthetic clouds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is whole-job throughput in Gpts/s with
+the cloud resident in HBM (N GPUs build N replicas: weak scaling, no data-path
+collective); `e2e` is the same metric through the C-ABI calls with the input in
+pinned host memory copied in and the node table read back every step.  The
+workload defaults to the 100M-point synthetic LiDAR scene.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, n, seed, grid_log2, sub_log2, max_level, chunk_threshold, node_capacity)
+    "lidar-100M": ("lidar", 100_000_000, 2, 7, 7, 15, 100_000, 20_000),
+    "uniform-1M": ("uniform", 1_000_000, 1, 7, 7, 15, 100_000, 20_000),
+    "uniform-1B": ("uniform", 1_000_000_000, 3, 7, 7, 8, 5_000_000, 50_000),
+    "lidar-10M": ("lidar", 10_000_000, 2, 7, 7, 15, 100_000, 20_000),
+}
+STAGES = ["bounds_decimate", "count", "merge", "distribute", "octree", "subsample"]
+# algorithmic HBM bytes per point of each stage (mandatory reads + writes), see the design doc
+ALG_BYTES = {"bounds_decimate": 17, "count": 16, "merge": 0, "distribute": 36, "octree": 44, "subsample": 44}
+FIXED_BYTES = {"merge": 3 * 4 * (1 << 21)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_cloud(kind, n, seed, out_tensor):
+    import synth
+    if kind == "lidar":
+        synth.lidar_into(out_tensor.data_ptr(), n, seed)
+    else:
+        synth.uniform_into(out_tensor.data_ptr(), n, seed)
+
+
+def oracle_rate(kind, seed, wl, budget_s):
+    """Oracle (single thread, plain C) on the first points of the same workload:
+    returns (points/s, sample size, seconds, cores)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    _, _, _, g, s, lmax, T, C = wl
+    prm = oracle.params(g, s, lmax, 16, T, C)
+    gen = synth.lidar if kind == "lidar" else synth.uniform
+    n = 20_000
+    while True:
+        pts = gen(n, seed)
+        t0 = time.perf_counter()
+        oracle.build_all(pts, prm)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s / 8 or n >= 4_000_000:
+            break
+        n = int(min(4_000_000, n * max(2.0, budget_s / 4 / max(dt, 1e-3))))
+    return n / dt, n, dt, 1
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    kind, n, seed = wl[0], wl[1], wl[2]
+    budget = float(os.environ.get("FP_ORACLE_BUDGET_S", "12"))
+    rates, samples = [], []
+    for _ in range(args.warmup):
+        oracle_rate(kind, seed, wl, budget / 4)
+    for _ in range(args.steps):
+        r, ns, dt, cores = oracle_rate(kind, seed, wl, budget)
+        rates.append(r)
+        samples.append(ns)
+    v = statistics.median(rates) / 1e9
+    line = {"impl": "reference", "metric": "octree build throughput (Gpts/s)", "value": v, "unit": "Gpts/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "points": n},
+            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+                             "sample": "first %d points of the %s workload, same parameters" % (samples[-1], args.workload)},
+            "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="lidar-100M", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_05002_gb300 import fastpoints as fp
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    kind, n, seed, g, s, lmax, T, C = wl
+    prm = fp.params(grid_log2=g, sub_log2=s, max_level=lmax, decim_modulus=16, chunk_threshold=T, node_capacity=C)
+    dev = torch.device("cuda", local)
+
+    # input: generated on the host (pinned), copied in once; a replica per rank
+    host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+    make_cloud(kind, n, seed, host)
+    pts = host.to(dev, non_blocking=False)
+    st = torch.cuda.Stream(dev)
+
+    # every output and workspace allocated once
+    cells = 1 << (3 * g)
+    ncap = fp.node_capacity_bound(n, prm)
+    O = dict(
+        cube=torch.empty(8, dtype=torch.int32, device=dev),
+        prev=torch.empty((fp._preview_cap(n, 16), 4), dtype=torch.int32, device=dev),
+        prev_n=torch.zeros(1, dtype=torch.int64, device=dev),
+        counts=torch.empty(cells, dtype=torch.int32, device=dev),
+        chunks=torch.empty((cells, 2), dtype=torch.int64, device=dev),
+        num_chunks=torch.zeros(1, dtype=torch.int32, device=dev),
+        lut=torch.empty(cells, dtype=torch.int32, device=dev),
+        offsets=torch.empty(cells + 1, dtype=torch.int64, device=dev),
+        dist=torch.empty_like(pts), perm=torch.empty(n, dtype=torch.int32, device=dev),
+        nodes=torch.zeros((ncap, 5), dtype=torch.int64, device=dev),
+        num_nodes=torch.zeros(1, dtype=torch.int32, device=dev),
+        leaf=torch.empty_like(pts), leaf_perm=torch.empty(n, dtype=torch.int32, device=dev),
+        owner=torch.empty(n, dtype=torch.int32, device=dev),
+        final=torch.empty_like(pts), final_perm=torch.empty(n, dtype=torch.int32, device=dev),
+    )
+    ws_need = max(fp.workspace_size(k, n, prm) for k in ("bounds_decimate", "merge", "distribute", "octree",
+                                                         "subsample"))
+    ws = torch.empty(ws_need, dtype=torch.uint8, device=dev)
+    L = fp.load()
+    P = lambda t: fp._ptr(t)
+    S = fp._stream(st)
+    import ctypes
+    prm_ref = ctypes.byref(prm)
+
+    def stage_calls(src):
+        return [
+            ("bounds_decimate", lambda: L.fp_bounds_decimate(P(src), n, P(O["cube"]), 0, 16, P(O["prev"]),
+                                                             O["prev"].shape[0], P(O["prev_n"]), P(ws), ws.numel(), S)),
+            ("count", lambda: L.fp_count(P(src), n, P(O["cube"]), g, P(O["counts"]), 0, None, 0, S)),
+            ("merge", lambda: L.fp_merge_chunks(P(O["counts"]), g, T, P(O["chunks"]), P(O["num_chunks"]),
+                                                P(O["lut"]), P(O["offsets"]), P(ws), ws.numel(), S)),
+            ("distribute", lambda: L.fp_distribute(P(src), n, P(O["cube"]), g, P(O["lut"]), P(O["offsets"]),
+                                                   P(O["num_chunks"]), P(O["dist"]), P(O["perm"]), P(ws),
+                                                   ws.numel(), S)),
+            ("octree", lambda: L.fp_build_chunk_octree(P(O["dist"]), P(O["perm"]), n, P(O["cube"]), P(O["chunks"]),
+                                                       P(O["num_chunks"]), P(O["offsets"]), P(O["counts"]), prm_ref,
+                                                       P(O["nodes"]), ncap, P(O["num_nodes"]), P(O["leaf"]),
+                                                       P(O["leaf_perm"]), P(O["owner"]), P(ws), ws.numel(), S)),
+            ("subsample", lambda: L.fp_subsample(P(O["nodes"]), P(O["num_nodes"]), ncap, P(O["dist"]), P(O["perm"]),
+                                                 P(O["owner"]), n, P(O["final"]), P(O["final_perm"]), P(ws),
+                                                 ws.numel(), S)),
+        ]
+
+    calls = stage_calls(pts)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
+
+    def step(record):
+        with torch.cuda.stream(st):
+            if record:
+                ev[0].record(st)
+            for k, (name, f) in enumerate(calls):
+                rc = f()
+                if rc != 0:
+                    raise RuntimeError("%s failed with status %d" % (name, rc))
+                if record:
+                    ev[k + 1].record(st)
+
+    for _ in range(max(3, args.warmup)):
+        step(False)
+    torch.cuda.synchronize()
+    assert fp.get_device_error(stream=st) == 0, "device error word set"
+
+    # kernels per step (CUPTI through the torch profiler, one step outside the timed region)
+    launches_per_step = None
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as pr:
+            step(False)
+            torch.cuda.synchronize()
+        launches_per_step = sum(1 for e in pr.events() if e.device_type.name == "CUDA" and
+                                not e.name.startswith("Memset") and not e.name.startswith("Memcpy"))
+    except Exception:
+        launches_per_step = None
+
+    clk = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    stage_ms = {k: [] for k in STAGES}
+    t0.record(st)
+    for _ in range(args.steps):
+        step(True)
+        st.synchronize()   # per-step stage events are read after each step
+        for k, name in enumerate(STAGES):
+            stage_ms[name].append(ev[k].elapsed_time(ev[k + 1]))
+    t1.record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = n * world / (ms * 1e-3) / 1e9
+
+    # end to end: pinned host input copied in, node table read back, every step
+    nodes_host = torch.empty_like(O["nodes"], device="cpu").pin_memory()
+    e2e_pts = torch.empty_like(pts)
+    calls_e2e = stage_calls(e2e_pts)
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    d2h = 0
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(st):
+            e2e_pts.copy_(host, non_blocking=True)
+            for name, f in calls_e2e:
+                if f() != 0:
+                    raise RuntimeError(name)
+            nn = O["num_nodes"].to("cpu", non_blocking=False)
+            M = int(nn.item())
+            nodes_host[:M].copy_(O["nodes"][:M], non_blocking=True)
+            st.synchronize()
+            d2h = M * 40 + 4
+    e2e_ms = (time.perf_counter() - te0) * 1e3 / e2e_steps
+    e2e_value = n * world / (e2e_ms * 1e-3) / 1e9
+
+    peak, peak_kind = measured_peaks()
+    med = {k: statistics.median(v) for k, v in stage_ms.items()}
+    dom = max(med, key=lambda k: med[k])
+    alg = ALG_BYTES[dom] * n + FIXED_BYTES.get(dom, 0)
+    achieved = alg / (med[dom] * 1e-3) / 1e9
+    total_alg = sum(ALG_BYTES[k] * n + FIXED_BYTES.get(k, 0) for k in STAGES)
+    M = int(O["num_nodes"].item())
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            r, ns, dt, cores = oracle_rate(kind, seed, wl, float(os.environ.get("FP_ORACLE_BUDGET_S", "12")))
+            cpu = {"value": r / 1e9, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+                   "sample": "first %d points of the %s workload, same parameters, %.1f s" % (ns, args.workload, dt)}
+        line = {
+            "metric": "octree build throughput (Gpts/s)", "value": value, "unit": "Gpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "points": n, "grid_log2": g, "sub_log2": s, "max_level": lmax,
+                       "chunk_threshold": T, "node_capacity": C, "nodes": M,
+                       "chunks": int(O["num_chunks"].item()), "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs (%.1f GB) larger than L2" % (16 * n / 1e9)},
+            "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "kernel": "stage " + dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "alg_bytes_per_launch": alg},
+            "step_roofline": {"alg_bytes": total_alg, "achieved_gbs": total_alg / (ms * 1e-3) / 1e9,
+                              "frac": total_alg / (ms * 1e-3) / 1e9 / peak},
+            "stage_ms": med,
+            "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps if launches_per_step else None,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
