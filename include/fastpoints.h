@@ -149,6 +149,23 @@ fp_status fp_bounds_decimate(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
                              fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
                              void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* fp_bounds_decimate without a workspace, for callers that cannot allocate
+ * device memory (a host application whose device memory belongs to another
+ * allocator or budget, or a real-time loop that must not wait on one).  The
+ * paper has no counterpart: this is a deployment convenience.
+ * Scratch: a 512 KiB array inside the library, held by every GPU that loads it
+ * until the process exits; n <= 2^27 (134,217,728) points, larger n returns
+ * FP_ERR_TOO_LARGE.  The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  Every call shares the one array (the scratch it needs is reset by
+ * each call), so calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race and must be serialised by the caller.  No
+ * device memory is allocated or freed.  Outputs as fp_bounds_decimate. */
+fp_status fp_bounds_decimate_static(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
+                                    uint64_t first_index, uint32_t modulus,
+                                    fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
+                                    cudaStream_t stream);
+
 /* Count grid (Sec. 4.4, the first step of sorting points into chunks):
  * d_counts[m] = number of points whose level-g cell has Morton key m, where the
  * cell of axis a is floor((p_a - o_a) * 2^g / S) in exact integer arithmetic and

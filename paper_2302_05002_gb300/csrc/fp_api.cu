@@ -70,6 +70,9 @@ fp_status check_params(const fp_params* p)
     return FP_OK;
 }
 
+// workspace view over a caller-provided (or library-held) buffer
+fp_status make_workspace(void* base, size_t bytes, size_t need, Workspace& ws) { return make_ws(base, bytes, need, ws); }
+
 size_t bounds_ws_bytes(uint64_t n, int num_sms)
 {
     uint64_t ntiles = (n + 4095) / 4096;

@@ -37,6 +37,9 @@ struct Workspace {
     }
 };
 
+// fp_api.cu
+fp_status make_workspace(void* base, size_t bytes, size_t need, Workspace& ws);
+
 // fp_core.cu
 cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cube, bool bounds, bool decim,
                                    uint64_t first, uint32_t modulus, fp_point* out, uint64_t out_cap,
