@@ -172,24 +172,35 @@ __global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __res
     }
 }
 
-__global__ void k_bounds_final(const int32_t* partial, int nblocks, uint64_t n, fp_cube* cube)
+__global__ void __launch_bounds__(256) k_bounds_final(const int32_t* partial, int nblocks, uint64_t n,
+                                                      fp_cube* cube)
 {
+    __shared__ int32_t s_red[6][8];
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], partial[b * 6 + a]);
+            hi[a] = max(hi[a], partial[b * 6 + 3 + a]);
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = __reduce_min_sync(0xFFFFFFFFu, lo[a]);
+        hi[a] = __reduce_max_sync(0xFFFFFFFFu, hi[a]);
+        if (lane == 0) { s_red[a][warp] = lo[a]; s_red[3 + a][warp] = hi[a]; }
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     fp_cube c;
     for (int a = 0; a < 3; ++a) { c.o[a] = 0; c.mx[a] = 0; }
     c.S = 0;
     if (n > 0) {
-        int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
-        for (int b = 0; b < nblocks; ++b)
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = min(lo[a], partial[b * 6 + a]);
-                hi[a] = max(hi[a], partial[b * 6 + 3 + a]);
-            }
         uint64_t ext = 0;
         for (int a = 0; a < 3; ++a) {
-            c.o[a] = lo[a];
-            c.mx[a] = hi[a];
-            uint64_t e = (uint64_t)((int64_t)hi[a] - (int64_t)lo[a]);
+            int32_t l = s_red[a][0], h = s_red[3 + a][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { l = min(l, s_red[a][w]); h = max(h, s_red[3 + a][w]); }
+            c.o[a] = l;
+            c.mx[a] = h;
+            uint64_t e = (uint64_t)((int64_t)h - (int64_t)l);
             ext = e > ext ? e : ext;
         }
         c.S = ext + 1;
@@ -324,7 +335,7 @@ cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cub
             k_bounds_decimate<false, true><<<grid, kBdNT, 0, st>>>(pts, n, first, modulus, out, out_cap,
                                                                     out_count, partial, status, counter, ntiles, ws.err);
     }
-    if (bounds) k_bounds_final<<<1, 32, 0, st>>>(partial, n ? grid : 0, n, cube);
+    if (bounds) k_bounds_final<<<1, 256, 0, st>>>(partial, n ? grid : 0, n, cube);
     return cudaGetLastError();
 }
 

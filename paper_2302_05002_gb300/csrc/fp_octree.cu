@@ -34,10 +34,10 @@
 
 namespace fp {
 
-constexpr int kPieceMax = 2048;                 // largest piece handled in shared memory
-constexpr int kWindow = 2048;                   // pieces starting in one window form a unit
+constexpr int kPieceMax = 1024;                 // largest piece handled in shared memory
+constexpr int kWindow = 1024;                   // pieces starting in one window form a unit
 constexpr int kUnitCap = kPieceMax + kWindow;   // records of one unit
-constexpr int kUnitNT = 512;
+constexpr int kUnitNT = 256;
 constexpr int kUnitWarps = kUnitNT / 32;
 constexpr uint8_t kInner = 0xFF;                // hierarchy still inner at this level
 constexpr uint8_t kEmpty = 0xFE;
@@ -185,43 +185,44 @@ __global__ void k_nodes_upper(OctCtx c)
 }
 
 // ------------------------------------------------------- big cells: gather
-// records of cells with more than kPieceMax points, key (big rank, sub-key)
-__global__ void k_big_gather(const OpenNode* open0, const uint32_t* nopen0, const uint32_t* bigstart,
-                             const uint64_t* gk, const uint32_t* gj, uint64_t* bk, uint32_t* bj, int g, int dl)
+// big cell of a position of the gathered array (bigstart: exclusive prefix of the big cells' counts)
+FP_DEV uint32_t big_of(const uint32_t* bigstart, uint32_t nb, uint32_t p)
 {
-    const uint32_t nb = *nopen0;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t a = 0, b = nb;
+    while (a < b) { uint32_t m = (a + b) >> 1; if (bigstart[m] <= p) a = m + 1; else b = m; }
+    return a - 1;
+}
+
+// records of cells with more than kPieceMax points, key (big rank, sub-key); one thread per record
+__global__ void k_big_gather(const OpenNode* open0, const uint32_t* nopen0, const uint32_t* bigstart,
+                             const uint32_t* total, const uint64_t* gk, const uint32_t* gj, uint64_t* bk, uint32_t* bj,
+                             int g, int dl)
+{
+    const uint32_t nb = *nopen0, T = *total;
     const int sub_bits = 3 * (dl - g);
     const uint64_t sub_mask = (1ull << sub_bits) - 1;
-    for (uint32_t b = warp; b < nb; b += nwarps) {
-        const OpenNode o = open0[b];
-        const uint32_t dst = bigstart[b];
-        for (uint32_t r = lane; r < o.count; r += 32) {
-            uint64_t k = gk[o.begin + r];
-            bk[dst + r] = ((uint64_t)b << sub_bits) | ((k >> (3 * (kKeyLevels - dl))) & sub_mask);
-            bj[dst + r] = gj[o.begin + r];
-        }
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
+        const uint32_t b = big_of(bigstart, nb, p);
+        const uint32_t src = open0[b].begin + (p - bigstart[b]);
+        bk[p] = ((uint64_t)b << sub_bits) | ((gk[src] >> (3 * (kKeyLevels - dl))) & sub_mask);
+        bj[p] = gj[src];
     }
 }
 
 // write the key-sorted big records back into their cells (keys truncated at level dl)
 __global__ void k_big_scatter(const OpenNode* open0, const uint32_t* nopen0, const uint32_t* bigstart,
-                              const uint64_t* bk, const uint32_t* bj, uint64_t* gk, uint32_t* gj, int g, int dl)
+                              const uint32_t* total, const uint64_t* bk, const uint32_t* bj, uint64_t* gk,
+                              uint32_t* gj, int g, int dl)
 {
-    const uint32_t nb = *nopen0;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nb = *nopen0, T = *total;
     const int sub_bits = 3 * (dl - g);
     const uint64_t sub_mask = (1ull << sub_bits) - 1;
-    for (uint32_t b = warp; b < nb; b += nwarps) {
-        const OpenNode o = open0[b];
-        const uint32_t src = bigstart[b];
-        for (uint32_t r = lane; r < o.count; r += 32) {
-            uint64_t k = bk[src + r];
-            gk[o.begin + r] = (o.key << (3 * (kKeyLevels - g))) | ((k & sub_mask) << (3 * (kKeyLevels - dl)));
-            gj[o.begin + r] = bj[src + r];
-        }
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
+        const uint32_t b = big_of(bigstart, nb, p);
+        const uint32_t dst = open0[b].begin + (p - bigstart[b]);
+        const uint64_t k = bk[p];
+        gk[dst] = (open0[b].key << (3 * (kKeyLevels - g))) | ((k & sub_mask) << (3 * (kKeyLevels - dl)));
+        gj[dst] = bj[p];
     }
 }
 
@@ -313,9 +314,11 @@ struct UnitSmem {
     uint32_t pbeg[kWindow + 1];
     uint16_t pcnt[kWindow + 1]; // 0 for an oversized piece (handled elsewhere)
     uint16_t psrt[kWindow + 1]; // start of each piece in the unit (load order = sorted order)
-    uint8_t pq[kWindow + 1], phier[kWindow + 1], pA[kWindow + 1];
+    uint8_t pq[kWindow + 1], phier[kWindow + 1], pA[kWindow + 1], pkind[kWindow + 1];
+    uint16_t pn[kWindow + 1];   // points of the piece (0 for an oversized one)
     uint16_t whist[kUnitWarps][256];
     uint32_t scan[64];
+    uint64_t wmin[kUnitWarps], wmax[kUnitWarps];
     unsigned long long kmin, kmax;
     uint32_t np, cnt, p0, dl;
 };
@@ -393,35 +396,43 @@ FP_DEV int piece_of(const UnitSmem& S, int np, int r)
 //   with the nearer of the two, plus one, is lambda unless the record is the
 //   minimum of its piece, whose lambda comes from the split tree;
 //   deep subtrees of inner pieces by binary search on the sorted keys.
-__global__ void __launch_bounds__(kUnitNT, 1) k_units(OctCtx c, const uint64_t* piece_begin_sorted,
+// first piece of every unit: lower bound of the unit's window start over the sorted piece begins
+__global__ void k_unit_ranges(const uint64_t* piece_begin_sorted, const uint32_t* npieces, uint32_t cap,
+                              uint64_t nunits, uint32_t* unit_p0)
+{
+    uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u > nunits) return;
+    const uint32_t np_all = *npieces < cap ? *npieces : cap;
+    const uint64_t w = u * kWindow;
+    uint32_t a = 0, b = np_all;
+    while (a < b) { uint32_t m = (a + b) >> 1; if (piece_begin_sorted[m] < w) a = m + 1; else b = m; }
+    unit_p0[u] = a;
+}
+
+__global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* unit_p0,
                                                       const uint32_t* piece_order, uint64_t n)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     UnitSmem& S = *reinterpret_cast<UnitSmem*>(smem_raw);
-    const uint32_t np_all = *c.npieces < c.piece_cap ? *c.npieces : c.piece_cap;
     const uint64_t nunits = (n + kWindow - 1) / kWindow;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-        const uint64_t wlo = u * kWindow, whi = wlo + kWindow;
         if (threadIdx.x == 0) {
-            uint32_t a = 0, b = np_all;
-            while (a < b) { uint32_t m = (a + b) >> 1; if (piece_begin_sorted[m] < wlo) a = m + 1; else b = m; }
-            uint32_t p0 = a;
-            b = np_all;
-            while (a < b) { uint32_t m = (a + b) >> 1; if (piece_begin_sorted[m] < whi) a = m + 1; else b = m; }
+            const uint32_t p0 = unit_p0[u];
             S.p0 = p0;
-            S.np = a - p0;
-            S.kmin = ~0ull;
-            S.kmax = 0;
+            S.np = unit_p0[u + 1] - p0;
             S.dl = 0;
         }
         __syncthreads();
         const int np = (int)S.np;
-        // piece descriptors; a block scan gives their starts in the unit
+        // piece descriptors.  Pieces of one point need nothing but their minimum
+        // rule; pieces of at most 32 points are handled by one warp with
+        // shuffles; larger pieces (and pieces whose node is still inner) go
+        // through the shared-memory sort.  A block scan places the large ones.
         {
             constexpr int per = (kWindow + kUnitNT - 1) / kUnitNT;   // 4
             uint32_t cn[per];
-            uint32_t sum = 0;
+            uint32_t sum = 0, dmax = 0;
             for (int q = 0; q < per; ++q) {
                 int pi = threadIdx.x * per + q;
                 cn[q] = 0;
@@ -431,16 +442,21 @@ __global__ void __launch_bounds__(kUnitNT, 1) k_units(OctCtx c, const uint64_t* 
                     S.pq[pi] = p.q;
                     S.phier[pi] = p.hier;
                     S.pA[pi] = p.A;
-                    cn[q] = p.dup ? 0u : p.count;
+                    const bool large = !p.dup && (p.count > 32 || p.hier == kInner);
+                    S.pkind[pi] = p.dup ? 3 : (large ? 2 : (p.count == 1 ? 0 : 1));
+                    S.pn[pi] = (uint16_t)(p.dup ? 0 : p.count);
+                    cn[q] = large ? p.count : 0u;
                     S.pcnt[pi] = (uint16_t)cn[q];
-                    if (cn[q]) {
+                    if (large) {
                         uint32_t d = p.hier == kInner ? (uint32_t)c.dl
                                                       : (uint32_t)min(kKeyLevels, c.s + (int)p.hier - 1);
-                        atomicMax(&S.dl, d);
+                        dmax = max(dmax, d);
                     }
                 }
                 sum += cn[q];
             }
+            dmax = __reduce_max_sync(0xFFFFFFFFu, dmax);
+            if (lane == 0 && dmax) atomicMax(&S.dl, dmax);
             uint32_t tot;
             uint32_t ex = block_exclusive_scan<kUnitNT, uint32_t>(sum, S.scan, tot);
             for (int q = 0; q < per; ++q) {
@@ -451,19 +467,69 @@ __global__ void __launch_bounds__(kUnitNT, 1) k_units(OctCtx c, const uint64_t* 
             if (threadIdx.x == 0) S.cnt = tot;
         }
         __syncthreads();
+        // ---- pieces of one point: the point is its piece's minimum
+        for (int pi = threadIdx.x; pi < np; pi += kUnitNT) {
+            if (S.pkind[pi] != 0) continue;
+            const uint32_t jj = c.gj[S.pbeg[pi]];
+            const int leafl = S.phier[pi];
+            int K = (int)S.pA[pi] - c.s;
+            K = K < 0 ? 0 : (K > leafl ? leafl : K);
+            c.own_code[jj] = (uint8_t)K;
+            c.leaf_code[jj] = (uint8_t)leafl;
+        }
+        // ---- pieces of 2..32 points: lambda from the deepest level shared with any
+        // point of smaller index in the piece (all pairs, by shuffles)
+        for (int pi = warp; pi < np; pi += kUnitWarps) {
+            if (S.pkind[pi] != 1) continue;
+            const int cnum = S.pn[pi];
+            const uint32_t b = S.pbeg[pi];
+            uint64_t k = 0;
+            uint32_t jj = 0xFFFFFFFFu;
+            if (lane < cnum) { k = c.gk[b + lane]; jj = c.gj[b + lane]; }
+            int lm = -1;
+            for (int t = 0; t < cnum; ++t) {
+                const uint64_t kt = __shfl_sync(0xFFFFFFFFu, k, t);
+                const uint32_t jt = __shfl_sync(0xFFFFFFFFu, jj, t);
+                if (jt < jj) lm = max(lm, common_level(k, kt));
+            }
+            if (lane < cnum) {
+                const int q = S.pq[pi];
+                const int lambda = lm < q ? (int)S.pA[pi] : lm + 1;
+                const int leafl = S.phier[pi];
+                int K = lambda - c.s;
+                K = K < 0 ? 0 : (K > leafl ? leafl : K);
+                c.own_code[jj] = (uint8_t)K;
+                c.leaf_code[jj] = (uint8_t)leafl;
+            }
+        }
         const int cnt = (int)S.cnt;
         if (cnt == 0) { __syncthreads(); continue; }
         // records; local index = position in load order
-        for (int r = threadIdx.x; r < cnt; r += kUnitNT) {
-            int pi = piece_of(S, np, r);
-            uint32_t g = S.pbeg[pi] + (uint32_t)(r - S.psrt[pi]);
-            uint64_t k = c.gk[g];
-            S.key[r] = k;
-            S.j[r] = c.gj[g];
-            S.v[r] = (uint16_t)r;
-            S.piece[r] = (uint16_t)pi;
-            atomicMin(&S.kmin, (unsigned long long)k);
-            atomicMax(&S.kmax, (unsigned long long)k);
+        {
+            uint64_t mn = ~0ull, mx = 0;
+            for (int r = threadIdx.x; r < cnt; r += kUnitNT) {
+                int pi = piece_of(S, np, r);
+                uint32_t g = S.pbeg[pi] + (uint32_t)(r - S.psrt[pi]);
+                uint64_t k = c.gk[g];
+                S.key[r] = k;
+                S.j[r] = c.gj[g];
+                S.v[r] = (uint16_t)r;
+                S.piece[r] = (uint16_t)pi;
+                mn = min(mn, k);
+                mx = max(mx, k);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = min(mn, (uint64_t)__shfl_xor_sync(0xFFFFFFFFu, (unsigned long long)mn, o));
+                mx = max(mx, (uint64_t)__shfl_xor_sync(0xFFFFFFFFu, (unsigned long long)mx, o));
+            }
+            if (lane == 0) { S.wmin[warp] = mn; S.wmax[warp] = mx; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < kUnitWarps; ++w) { mn = min(mn, S.wmin[w]); mx = max(mx, S.wmax[w]); }
+                mn = min(mn, S.wmin[0]); mx = max(mx, S.wmax[0]);
+                S.kmin = mn;
+                S.kmax = mx;
+            }
         }
         __syncthreads();
         {
@@ -483,7 +549,7 @@ __global__ void __launch_bounds__(kUnitNT, 1) k_units(OctCtx c, const uint64_t* 
         }
         __syncthreads();
         // ---- nearest smaller index along the key order, inside each thread's block first
-        const int per = (cnt + kUnitNT - 1) / kUnitNT;   // <= 8
+        const int per = (cnt + kUnitNT - 1) / kUnitNT;   // <= kUnitCap / kUnitNT
         const int b0 = min(cnt, (int)threadIdx.x * per), b1 = min(cnt, b0 + per);
         for (int r = b0; r < b1; ++r) {
             const uint32_t jr = S.j[S.v[r]];
@@ -804,6 +870,7 @@ struct OctBufs {
     uint32_t *idxtab, *leafw, *nown;
     uint8_t *own_code, *leaf_code;
     uint32_t* leafid;
+    uint32_t* unit_p0;
 };
 
 // one carve-up serves both the size query (base == nullptr) and the launch
@@ -844,6 +911,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.nown = ws.take<uint32_t>(Ly.node_cap);
     B.own_code = ws.take<uint8_t>(N); B.leaf_code = ws.take<uint8_t>(N);
     B.leafid = ws.take<uint32_t>(N);
+    B.unit_p0 = ws.take<uint32_t>((N + kWindow - 1) / kWindow + 2);
     return B;
 }
 
@@ -925,7 +993,9 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
                                                     (uint32_t*)nullptr, st)))
             return e;
         int gw = std::max(1, std::min(ws.num_sms * 16, (int)(((uint64_t)cap * 32 + 255) / 256)));
-        k_big_gather<<<gw, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.gk, B.gj, B.t_k2, B.t_j2, g, dl);
+        const int gr = std::max(1, std::min(ws.num_sms * 8, (int)((N + 255) / 256)));
+        k_big_gather<<<gr, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.ocount + 3, B.gk, B.gj, B.t_k2, B.t_j2,
+                                         g, dl);
         int rank_bits = 1;
         while ((1ull << rank_bits) < std::min<uint64_t>(Ly.open_cap, Ly.cells)) ++rank_bits;
         const uint32_t total_bits = (uint32_t)(3 * (dl - g) + rank_bits);
@@ -935,7 +1005,8 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         a.b.val_src = B.t_j2; a.b.val_tmp = B.t_j1; a.b.val_dst = B.t_j3;
         a.n = N; a.d_n = B.ocount + 3; a.err = ws.err;
         if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
-        k_big_scatter<<<gw, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.t_k3, B.t_j3, B.gk, B.gj, g, dl);
+        k_big_scatter<<<gr, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.ocount + 3, B.t_k3, B.t_j3, B.gk, B.gj,
+                                          g, dl);
         int cur = 0;
         for (int q = g; q < dl; ++q) {
             k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
@@ -963,9 +1034,10 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
         const size_t smem = sizeof(UnitSmem);
         if ((e = cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-        uint64_t nunits = (N + kWindow - 1) / kWindow;
+        const uint64_t nunits = (N + kWindow - 1) / kWindow;
+        k_unit_ranges<<<(unsigned)((nunits + 1 + 255) / 256), 256, 0, st>>>(B.pk3, npieces, pcap, nunits, B.unit_p0);
         int grid = (int)std::min<uint64_t>(nunits, (uint64_t)ws.num_sms * 2);
-        k_units<<<grid, kUnitNT, smem, st>>>(c, B.pk3, B.pv, N);
+        k_units<<<grid, kUnitNT, smem, st>>>(c, B.unit_p0, B.pv, N);
         k_dup_pieces<<<ws.num_sms, 256, 0, st>>>(c);
     }
     // 7. node table in preorder: stable sort by level, then by start at max_level resolution
@@ -1056,22 +1128,20 @@ __global__ void k_stitch_list(const uint32_t* mark, const uint32_t* mrank, const
     }
 }
 
-// keys (rank << 32 | original index) of the points of marked nodes, value = final position
+// keys (rank << 32 | original index) of the points of marked nodes, value = final position;
+// one thread per stitch record, its node found by binary search over the segment offsets
 __global__ void k_stitch_keys(const uint32_t* mlist, const uint32_t* nmarked, const uint32_t* soff,
-                              const uint32_t* nown, const uint64_t* first, const uint32_t* fperm, uint64_t* key,
+                              const uint32_t* nstitch, const uint64_t* first, const uint32_t* fperm, uint64_t* key,
                               uint32_t* val)
 {
-    const uint32_t nm = *nmarked;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t r = warp; r < nm; r += nwarps) {
-        const uint32_t node = mlist[r];
-        const uint32_t cnt = nown[node];
-        const uint64_t f0 = first[node];
-        for (uint32_t t = lane; t < cnt; t += 32) {
-            key[soff[r] + t] = ((uint64_t)r << 32) | fperm[f0 + t];
-            val[soff[r] + t] = (uint32_t)(f0 + t);
-        }
+    const uint32_t nm = *nmarked, S = *nstitch;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < S; t += gridDim.x * blockDim.x) {
+        uint32_t a = 0, b = nm;
+        while (a < b) { uint32_t m = (a + b) >> 1; if (soff[m] <= t) a = m + 1; else b = m; }
+        const uint32_t r = a - 1;
+        const uint64_t f = first[mlist[r]] + (t - soff[r]);
+        key[t] = ((uint64_t)r << 32) | fperm[f];
+        val[t] = (uint32_t)f;
     }
 }
 
@@ -1186,8 +1256,7 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     k_stitch_list<<<gM, 256, 0, st>>>(mark, mrank, num_nodes, node_cap, mlist, nown, mown);
     if ((e = scan_exclusive<uint32_t, uint32_t>(mown, soff, M, cnt, tiles32, cnt + 1, (uint32_t*)nullptr, st)))
         return e;
-    int gw = std::max(1, std::min(ws.num_sms * 16, (int)((M * 32ull + 255) / 256)));
-    k_stitch_keys<<<gw, 256, 0, st>>>(mlist, cnt, soff, nown, first, final_perm, s_key, s_val);
+    k_stitch_keys<<<ws.num_sms * 8, 256, 0, st>>>(mlist, cnt, soff, cnt + 1, first, final_perm, s_key, s_val);
     int rank_bits = 1;
     while ((1ull << rank_bits) < M) ++rank_bits;
     if ((e = sort_plan_keys(sc, s_key, N, cnt + 1, 0, (uint32_t)(32 + rank_bits), st))) return e;

@@ -16,6 +16,7 @@
 // host: surplus pass slots return at once, and slot k reads from the source,
 // or the temporaries, and writes to the destination when it is the last pass.
 #pragma once
+#include <type_traits>
 #include "fp_internal.cuh"
 
 namespace fp {
@@ -72,27 +73,35 @@ FP_DEV const T* pick_src(int slot, int npass, const T* src, T* dst, T* tmp)
     return slot == 0 ? src : pick_dst(slot - 1, npass, dst, tmp);
 }
 
-template <int DIG, bool CPT, bool CK64, bool CK32>
+// Two widths of every pass kernel: MAXB = 8 (small shared memory, two or three
+// CTAs per SM) runs the passes whose digit has at most 8 bits, MAXB = 11 the
+// others; the plan decides on the device and the other variant returns at once.
+constexpr int kSortSmallBits = 8;
+
+template <int DIG, bool CPT, bool CK64, bool CK32, int MAXB>
 struct SortSmem {
+    using dig_t = typename std::conditional<(MAXB <= 8), uint8_t, uint16_t>::type;
     static constexpr size_t pt = CPT ? sizeof(int4) * kSortTile : 0;
     static constexpr size_t k64 = CK64 ? sizeof(uint64_t) * kSortTile : 0;
     static constexpr size_t val = sizeof(uint32_t) * kSortTile;
     static constexpr size_t k32 = CK32 ? sizeof(uint32_t) * kSortTile : 0;
-    static constexpr size_t dig = sizeof(uint16_t) * kSortTile;
-    static constexpr size_t whist = sizeof(uint16_t) * kSortWarps * (1 << kSortMaxBits);
-    static constexpr size_t gbase = sizeof(uint64_t) * (1 << kSortMaxBits);
-    static constexpr size_t cnt = sizeof(uint32_t) * (1 << kSortMaxBits);
-    static constexpr size_t off = sizeof(uint32_t) * (1 << kSortMaxBits);
+    static constexpr size_t dig = sizeof(dig_t) * kSortTile;
+    static constexpr size_t whist = sizeof(uint16_t) * kSortWarps * (1 << MAXB);
+    static constexpr size_t gbase = sizeof(uint64_t) * (1 << MAXB);
+    static constexpr size_t cnt = sizeof(uint32_t) * (1 << MAXB);
+    static constexpr size_t off = sizeof(uint32_t) * (1 << MAXB);
     static constexpr size_t misc = 4 * (1 + kSortWarps + 15);   // tile id + block-scan scratch
     static constexpr size_t total = pt + k64 + val + k32 + dig + whist + gbase + cnt + off + misc;
 };
 
-template <int DIG, bool CPT, bool CK64, bool CK32>
-__global__ void __launch_bounds__(kSortNT, 1) k_sort_pass(SortArgs a, int slot)
+template <int DIG, bool CPT, bool CK64, bool CK32, int MAXB>
+__global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_sort_pass(SortArgs a, int slot)
 {
     const SortPlan plan = *a.plan;
     if (slot >= (int)plan.npass) return;
-    using SM = SortSmem<DIG, CPT, CK64, CK32>;
+    if ((int)plan.bits > MAXB || (MAXB > kSortSmallBits && (int)plan.bits <= kSortSmallBits)) return;
+    using SM = SortSmem<DIG, CPT, CK64, CK32, MAXB>;
+    using dig_t = typename SM::dig_t;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* sp = smem;
     int4* s_pt = reinterpret_cast<int4*>(sp); sp += SM::pt;
@@ -102,7 +111,7 @@ __global__ void __launch_bounds__(kSortNT, 1) k_sort_pass(SortArgs a, int slot)
     uint32_t* s_k32 = reinterpret_cast<uint32_t*>(sp); sp += SM::k32;
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(sp); sp += SM::cnt;
     uint32_t* s_off = reinterpret_cast<uint32_t*>(sp); sp += SM::off;
-    uint16_t* s_dig = reinterpret_cast<uint16_t*>(sp); sp += SM::dig;
+    dig_t* s_dig = reinterpret_cast<dig_t*>(sp); sp += SM::dig;
     uint16_t* s_whist = reinterpret_cast<uint16_t*>(sp); sp += SM::whist;
     uint32_t* s_misc = reinterpret_cast<uint32_t*>(sp);   // [0] tile id, [1..] scan scratch
 
@@ -216,7 +225,7 @@ __global__ void __launch_bounds__(kSortNT, 1) k_sort_pass(SortArgs a, int slot)
                 if (CK64 && DIG != DIG_CELL) s_k64[lp] = in_k64[i];
                 if (CK32) s_k32[lp] = in_k32[i];
                 s_val[lp] = in_val ? in_val[i] : (uint32_t)i;
-                s_dig[lp] = (uint16_t)d;
+                s_dig[lp] = (dig_t)d;
             }
         }
 
@@ -286,24 +295,37 @@ cudaError_t sort_plan_weights(const SortScratch& sc, const uint32_t* weights, co
 cudaError_t sort_plan_keys(const SortScratch& sc, const uint64_t* keys, uint64_t n, const uint32_t* d_n,
                            uint32_t shift0, uint32_t total_bits, cudaStream_t st);
 
+template <int DIG, bool CPT, bool CK64, bool CK32, int MAXB>
+cudaError_t sort_launch_variant(const SortArgs& a, int slot, int num_sms, cudaStream_t st)
+{
+    using SM = SortSmem<DIG, CPT, CK64, CK32, MAXB>;
+    auto kern = k_sort_pass<DIG, CPT, CK64, CK32, MAXB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::total);
+    if (e) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSortNT, SM::total);
+    if (e) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t ntiles = (a.n + kSortTile - 1) / kSortTile;
+    int grid = (int)std::min<uint64_t>(ntiles ? ntiles : 1, (uint64_t)num_sms * per_sm);
+    kern<<<grid, kSortNT, SM::total, st>>>(a, slot);
+    return cudaGetLastError();
+}
+
 template <int DIG, bool CPT, bool CK64, bool CK32>
 cudaError_t sort_run_pass(const SortScratch& sc, const SortArgs& a0, int slot, int num_sms, cudaStream_t st)
 {
-    using SM = SortSmem<DIG, CPT, CK64, CK32>;
-    cudaError_t e = cudaFuncSetAttribute(k_sort_pass<DIG, CPT, CK64, CK32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::total);
-    if (e) return e;
+    cudaError_t e;
     SortArgs a = a0;
     a.plan = sc.plan;
     a.bases = sc.bases;
     a.status = sc.status;
     a.counter = sc.counter + slot;
     uint64_t ntiles = (a.n + kSortTile - 1) / kSortTile;
-    int grid = (int)std::min<uint64_t>(ntiles ? ntiles : 1, (uint64_t)num_sms);
     k_sort_zero<<<std::max(1, std::min(num_sms * 4, (int)((ntiles * (1 << kSortMaxBits) + 1023) / 1024))), 256, 0,
                   st>>>(sc.status, sc.counter + slot, a.n, sc.plan, slot);
-    k_sort_pass<DIG, CPT, CK64, CK32><<<grid, kSortNT, SM::total, st>>>(a, slot);
-    return cudaGetLastError();
+    if ((e = sort_launch_variant<DIG, CPT, CK64, CK32, kSortSmallBits>(a, slot, num_sms, st))) return e;
+    return sort_launch_variant<DIG, CPT, CK64, CK32, kSortMaxBits>(a, slot, num_sms, st);
 }
 
 }  // namespace fp
