@@ -308,8 +308,10 @@ struct UnitSmem {
     uint16_t v[kUnitCap];       // local index by sorted position
     uint16_t v2[kUnitCap];
     uint16_t piece[kUnitCap];   // piece of a local index
-    uint8_t cl[kUnitCap];       // common level with the nearest smaller index on the left (255: none)
+    uint8_t cl[kUnitCap];       // by run: common level with the nearest smaller index on the left (255: none)
     uint8_t cr[kUnitCap];       // ... on the right
+    uint32_t hj[kUnitCap];      // by run: smallest index of the run
+    uint16_t hid[kUnitCap];     // by sorted position: run number
     uint8_t leaf[kUnitCap];     // leaf level by sorted position (pieces with a deep subtree)
     uint32_t pbeg[kWindow + 1];
     uint16_t pcnt[kWindow + 1]; // 0 for an oversized piece (handled elsewhere)
@@ -320,7 +322,7 @@ struct UnitSmem {
     uint32_t scan[64];
     uint64_t wmin[kUnitWarps], wmax[kUnitWarps];
     unsigned long long kmin, kmax;
-    uint32_t np, cnt, p0, dl;
+    uint32_t np, cnt, p0, dl, nh;
 };
 
 // stable LSD pass over the unit's records by 8 key bits at `shift`
@@ -548,31 +550,77 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
             }
         }
         __syncthreads();
-        // ---- nearest smaller index along the key order, inside each thread's block first
-        const int per = (cnt + kUnitNT - 1) / kUnitNT;   // <= kUnitCap / kUnitNT
-        const int b0 = min(cnt, (int)threadIdx.x * per), b1 = min(cnt, b0 + per);
+        // ---- runs: records equal down to the sorted depth share every cell down
+        // to that depth, so only the smallest index of a run can be the minimum of
+        // any of those cells and the others inherit "never" (lambda beyond the
+        // depth).  The search below runs over one representative per run: the
+        // run's smallest index, with the run's key.
+        int lo_bit_u = 0;
+        {
+            const int dl_unit = (int)S.dl;
+            const int clev = common_level(S.kmin, S.kmax);
+            lo_bit_u = 3 * (kKeyLevels - max(dl_unit, clev));
+        }
+        {
+            constexpr int per_h = kUnitCap / kUnitNT;   // records per thread, contiguous
+            const int h0 = threadIdx.x * per_h;
+            uint32_t flags = 0, cntf = 0;
+            for (int q = 0; q < per_h; ++q) {
+                const int r = h0 + q;
+                bool head = false;
+                if (r < cnt) head = r == 0 || ((S.key[r] ^ S.key[r - 1]) >> lo_bit_u) != 0;
+                flags |= (uint32_t)head << q;
+                cntf += head;
+            }
+            uint32_t tot;
+            const uint32_t ex0 = block_exclusive_scan<kUnitNT, uint32_t>(cntf, S.scan, tot);
+            for (uint32_t x = threadIdx.x; x < tot; x += kUnitNT) S.hj[x] = 0xFFFFFFFFu;
+            __syncthreads();
+            int run = (int)ex0 - 1;   // run of the record before this thread's block
+            uint32_t mn = 0xFFFFFFFFu;
+            for (int q = 0; q < per_h; ++q) {
+                const int r = h0 + q;
+                if (r >= cnt) break;
+                if ((flags >> q) & 1u) {
+                    if (run >= 0 && mn != 0xFFFFFFFFu) atomicMin(&S.hj[run], mn);
+                    ++run;
+                    mn = 0xFFFFFFFFu;
+                    S.key2[run] = S.key[r];
+                }
+                S.hid[r] = (uint16_t)run;
+                mn = min(mn, S.j[S.v[r]]);
+            }
+            if (run >= 0 && mn != 0xFFFFFFFFu) atomicMin(&S.hj[run], mn);
+            if (threadIdx.x == 0) S.nh = tot;
+        }
+        __syncthreads();
+        const int nh = (int)S.nh;
+        // ---- nearest smaller index among the heads (chain jumping; every skipped
+        // position holds a larger index), inside each thread's block first
+        const int per = (nh + kUnitNT - 1) / kUnitNT;   // <= kUnitCap / kUnitNT
+        const int b0 = min(nh, (int)threadIdx.x * per), b1 = min(nh, b0 + per);
         for (int r = b0; r < b1; ++r) {
-            const uint32_t jr = S.j[S.v[r]];
+            const uint32_t jr = S.hj[r];
             int x = r - 1;
-            while (x >= b0 && S.j[S.v[x]] > jr) x = S.ps[x];
+            while (x >= b0 && S.hj[x] > jr) x = S.ps[x];
             S.ps[r] = (int16_t)x;   // x < b0: continue from x later (every index in (x, r) is larger)
         }
         for (int r = b1 - 1; r >= b0; --r) {
-            const uint32_t jr = S.j[S.v[r]];
+            const uint32_t jr = S.hj[r];
             int x = r + 1;
-            while (x < b1 && S.j[S.v[x]] > jr) x = S.ns[x];
+            while (x < b1 && S.hj[x] > jr) x = S.ns[x];
             S.ns[r] = (int16_t)x;
         }
         __syncthreads();
         for (int r = b0; r < b1; ++r) {
-            const uint32_t jr = S.j[S.v[r]];
-            const uint64_t kr = S.key[r];
+            const uint32_t jr = S.hj[r];
+            const uint64_t kr = S.key2[r];
             int x = S.ps[r];
-            while (x >= 0 && S.j[S.v[x]] > jr) x = S.ps[x];
-            S.cl[r] = x >= 0 ? (uint8_t)common_level(kr, S.key[x]) : (uint8_t)255;
+            while (x >= 0 && S.hj[x] > jr) x = S.ps[x];
+            S.cl[r] = x >= 0 ? (uint8_t)common_level(kr, S.key2[x]) : (uint8_t)255;
             x = S.ns[r];
-            while (x < cnt && S.j[S.v[x]] > jr) x = S.ns[x];
-            S.cr[r] = x < cnt ? (uint8_t)common_level(kr, S.key[x]) : (uint8_t)255;
+            while (x < nh && S.hj[x] > jr) x = S.ns[x];
+            S.cr[r] = x < nh ? (uint8_t)common_level(kr, S.key2[x]) : (uint8_t)255;
         }
         __syncthreads();
         // ---- deep subtrees inside pieces whose node is still inner: one warp per piece
@@ -622,9 +670,13 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         for (int r = threadIdx.x; r < cnt; r += kUnitNT) {
             const int vv = S.v[r];
             const int pi = S.piece[vv];
-            const int ql = S.cl[r] == 255 ? -1 : (int)S.cl[r];
-            const int qr = S.cr[r] == 255 ? -1 : (int)S.cr[r];
-            const int lm = max(ql, qr);
+            const int h = S.hid[r];
+            int lm = kKeyLevels;   // not its run's minimum: shares the sorted depth with a smaller index
+            if (S.j[vv] == S.hj[h]) {
+                const int ql = S.cl[h] == 255 ? -1 : (int)S.cl[h];
+                const int qr = S.cr[h] == 255 ? -1 : (int)S.cr[h];
+                lm = max(ql, qr);
+            }
             const int q = S.pq[pi];
             const int lambda = lm < q ? (int)S.pA[pi] : lm + 1;   // the piece minimum: from the split tree
             const int leafl = S.phier[pi] == kInner ? (int)S.leaf[r] : (int)S.phier[pi];
