@@ -44,6 +44,31 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def count_kernels(run, torch):
+    """Kernels one call of run() launches, from the profiler's device activity."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as pr:
+            run()
+            torch.cuda.synchronize()
+        names = []
+        for e in pr.events():
+            dt = getattr(e, "device_type", None)
+            if dt is None or "CUDA" not in str(dt):
+                continue
+            if e.name.startswith(("Memset", "Memcpy", "cuda", "Activity")):
+                continue
+            names.append(e.name)
+        if not names:
+            print("gpu_launches: profiler saw no kernels", file=sys.stderr)
+            return None
+        return len(names)
+    except Exception as ex:  # reported, not fatal: the count is informational
+        print("gpu_launches: profiler failed: %r" % (ex,), file=sys.stderr)
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -251,16 +276,7 @@ def main():
     assert fp.get_device_error(stream=st) == 0, "device error word set"
 
     # kernels per step (CUPTI through the torch profiler, one step outside the timed region)
-    launches_per_step = None
-    try:
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as pr:
-            step(False)
-            torch.cuda.synchronize()
-        launches_per_step = sum(1 for e in pr.events() if e.device_type.name == "CUDA" and
-                                not e.name.startswith("Memset") and not e.name.startswith("Memcpy"))
-    except Exception:
-        launches_per_step = None
+    launches_per_step = count_kernels(lambda: step(False), torch)
 
     clk = ClockSampler(local)
     if world > 1:

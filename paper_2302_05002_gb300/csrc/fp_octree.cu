@@ -193,35 +193,39 @@ FP_DEV uint32_t big_of(const uint32_t* bigstart, uint32_t nb, uint32_t p)
     return a - 1;
 }
 
-// records of cells with more than kPieceMax points, key (big rank, sub-key); one thread per record
-__global__ void k_big_gather(const OpenNode* open0, const uint32_t* nopen0, const uint32_t* bigstart,
+// Records of the open nodes at level q (more than kPieceMax points each), one
+// thread per record.  Key = (rank of the open node << 3 (21 - q)) | the key
+// bits below level q: sorting by the rank and the next levels' digits groups
+// the records by node and orders them by those levels, and the key stays
+// whole (the rank needs at most 21 bits, the rest 3 (21 - q) <= 42).
+__global__ void k_big_gather(const OpenNode* open, const uint32_t* nopen, const uint32_t* bigstart,
                              const uint32_t* total, const uint64_t* gk, const uint32_t* gj, uint64_t* bk, uint32_t* bj,
-                             int g, int dl)
+                             int q)
 {
-    const uint32_t nb = *nopen0, T = *total;
-    const int sub_bits = 3 * (dl - g);
-    const uint64_t sub_mask = (1ull << sub_bits) - 1;
+    const uint32_t nb = *nopen, T = *total;
+    const int low = 3 * (kKeyLevels - q);
+    const uint64_t low_mask = (1ull << low) - 1;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
         const uint32_t b = big_of(bigstart, nb, p);
-        const uint32_t src = open0[b].begin + (p - bigstart[b]);
-        bk[p] = ((uint64_t)b << sub_bits) | ((gk[src] >> (3 * (kKeyLevels - dl))) & sub_mask);
+        const uint32_t src = open[b].begin + (p - bigstart[b]);
+        bk[p] = ((uint64_t)b << low) | (gk[src] & low_mask);
         bj[p] = gj[src];
     }
 }
 
-// write the key-sorted big records back into their cells (keys truncated at level dl)
-__global__ void k_big_scatter(const OpenNode* open0, const uint32_t* nopen0, const uint32_t* bigstart,
+// write the sorted records back into their nodes' ranges, with their full keys
+__global__ void k_big_scatter(const OpenNode* open, const uint32_t* nopen, const uint32_t* bigstart,
                               const uint32_t* total, const uint64_t* bk, const uint32_t* bj, uint64_t* gk,
-                              uint32_t* gj, int g, int dl)
+                              uint32_t* gj, int q)
 {
-    const uint32_t nb = *nopen0, T = *total;
-    const int sub_bits = 3 * (dl - g);
-    const uint64_t sub_mask = (1ull << sub_bits) - 1;
+    const uint32_t nb = *nopen, T = *total;
+    const int low = 3 * (kKeyLevels - q);
+    const uint64_t low_mask = (1ull << low) - 1;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
         const uint32_t b = big_of(bigstart, nb, p);
-        const uint32_t dst = open0[b].begin + (p - bigstart[b]);
+        const uint32_t dst = open[b].begin + (p - bigstart[b]);
         const uint64_t k = bk[p];
-        gk[dst] = (open0[b].key << (3 * (kKeyLevels - g))) | ((k & sub_mask) << (3 * (kKeyLevels - dl)));
+        gk[dst] = (open[b].key << low) | (k & low_mask);
         gj[dst] = bj[p];
     }
 }
@@ -1037,33 +1041,44 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
     }
     // 3. cells: pieces, leaf levels, open big cells
     k_cell_setup<<<(unsigned)((Ly.cells + 255) / 256), 256, 0, st>>>(c, B.open[0], B.ocount);
-    // 4. big cells: key-sort their records (key = big rank, sub-key to level dl), write back, split
+    // 4. big cells: split tree.  The records of the open nodes are key-sorted
+    // (stable: records equal down to the sorted depth stay in index order) in
+    // two rounds, the first down to level g + R, the second down to dl for the
+    // nodes still open there; each round is followed by the splits it allows.
     {
         const uint32_t cap = (uint32_t)Ly.open_cap;
-        k_open_counts<<<(cap + 255) / 256, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, cap);
-        if ((e = scan_exclusive<uint32_t, uint32_t>(B.bigstart, B.bigstart, cap, nullptr, B.leafw, B.ocount + 3,
-                                                    (uint32_t*)nullptr, st)))
-            return e;
         int gw = std::max(1, std::min(ws.num_sms * 16, (int)(((uint64_t)cap * 32 + 255) / 256)));
         const int gr = std::max(1, std::min(ws.num_sms * 8, (int)((N + 255) / 256)));
-        k_big_gather<<<gr, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.ocount + 3, B.gk, B.gj, B.t_k2, B.t_j2,
-                                         g, dl);
         int rank_bits = 1;
         while ((1ull << rank_bits) < std::min<uint64_t>(Ly.open_cap, Ly.cells)) ++rank_bits;
-        const uint32_t total_bits = (uint32_t)(3 * (dl - g) + rank_bits);
-        if ((e = sort_plan_keys(sc, B.t_k2, N, B.ocount + 3, 0, total_bits, st))) return e;
-        SortArgs a{};
-        a.b.k64_src = B.t_k2; a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.t_k3;
-        a.b.val_src = B.t_j2; a.b.val_tmp = B.t_j1; a.b.val_dst = B.t_j3;
-        a.n = N; a.d_n = B.ocount + 3; a.err = ws.err;
-        if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
-        k_big_scatter<<<gr, 256, 0, st>>>(B.open[0], B.ocount, B.bigstart, B.ocount + 3, B.t_k3, B.t_j3, B.gk, B.gj,
-                                          g, dl);
+        // first round: digits plus rank within 32 bits (four passes at most)
+        const int R = std::max(1, (32 - rank_bits) / 3);
         int cur = 0;
-        for (int q = g; q < dl; ++q) {
-            k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
-            k_split<<<gw, 256, 0, st>>>(c, B.open[cur], B.ocount + cur, B.open[1 - cur], B.ocount + (1 - cur), cap);
-            cur = 1 - cur;
+        for (int q = g; q < dl;) {
+            const int r = q == g ? std::min(R, dl - q) : dl - q;
+            k_open_counts<<<(cap + 255) / 256, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, cap);
+            if ((e = scan_exclusive<uint32_t, uint32_t>(B.bigstart, B.bigstart, cap, nullptr, B.leafw, B.ocount + 3,
+                                                        (uint32_t*)nullptr, st)))
+                return e;
+            k_big_gather<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, B.ocount + 3, B.gk, B.gj,
+                                             B.t_k2, B.t_j2, q);
+            if ((e = sort_plan_keys(sc, B.t_k2, N, B.ocount + 3, (uint32_t)(3 * (kKeyLevels - q - r)),
+                                    (uint32_t)(3 * r), st, B.ocount + cur)))
+                return e;
+            SortArgs a{};
+            a.b.k64_src = B.t_k2; a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.t_k3;
+            a.b.val_src = B.t_j2; a.b.val_tmp = B.t_j1; a.b.val_dst = B.t_j3;
+            a.n = N; a.d_n = B.ocount + 3; a.err = ws.err;
+            if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
+            k_big_scatter<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, B.ocount + 3, B.t_k3,
+                                              B.t_j3, B.gk, B.gj, q);
+            for (int l = q; l < q + r; ++l) {
+                k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
+                k_split<<<gw, 256, 0, st>>>(c, B.open[cur], B.ocount + cur, B.open[1 - cur], B.ocount + (1 - cur),
+                                            cap);
+                cur = 1 - cur;
+            }
+            q += r;
         }
     }
     // 5. nodes at levels <= g

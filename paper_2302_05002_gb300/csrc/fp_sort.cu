@@ -10,6 +10,8 @@
 
 namespace fp {
 
+// Passes and digit width for a key of `need` bits (at most 64): the fewest
+// passes of at most 8 bits, the bits spread evenly over them.
 FP_DEV void plan_shape(uint64_t nw, uint32_t fixed_bits, uint32_t& npass, uint32_t& bits)
 {
     uint32_t need = fixed_bits;
@@ -18,10 +20,19 @@ FP_DEV void plan_shape(uint64_t nw, uint32_t fixed_bits, uint32_t& npass, uint32
         while (need < 64 && (nw - 1) >> need) ++need;
         if (nw <= 1) need = 1;
     }
+    if (need > 64) need = 64;
     npass = (need + kSortMaxBits - 1) / kSortMaxBits;
     if (npass < 1) npass = 1;
     bits = (need + npass - 1) / npass;
     if (bits < 1) bits = 1;
+}
+
+// bits of the largest value below *d (at least 1)
+FP_DEV uint32_t bits_of_count(uint32_t v)
+{
+    uint32_t b = 1;
+    while (b < 32 && ((v ? v - 1 : 0) >> b)) ++b;
+    return b;
 }
 
 __global__ void k_sort_zero(uint32_t* status, uint32_t* counter, uint64_t n, const SortPlan* plan, int slot)
@@ -61,9 +72,10 @@ __global__ void k_plan_hist_weights(const uint32_t* weights, const uint64_t* off
 }
 
 __global__ void k_plan_hist_keys(const uint64_t* keys, uint64_t n, const uint32_t* d_n, uint32_t shift0,
-                                 uint32_t total_bits, uint32_t* hist)
+                                 uint32_t total_bits, uint32_t* hist, const uint32_t* d_rank_n)
 {
     if (d_n && *d_n < n) n = *d_n;
+    if (d_rank_n) total_bits += bits_of_count(*d_rank_n);
     __shared__ uint32_t sh[kSortMaxPass << kSortMaxBits];
     uint32_t npass, bits;
     plan_shape(0, total_bits, npass, bits);
@@ -82,15 +94,16 @@ __global__ void k_plan_hist_keys(const uint64_t* keys, uint64_t n, const uint32_
 
 __global__ void __launch_bounds__(1024) k_plan_finalize(const uint32_t* d_nw, uint64_t nw_max, uint32_t fixed_bits,
                                                         uint32_t shift0, const uint32_t* hist, SortPlan* plan,
-                                                        uint64_t* bases)
+                                                        uint64_t* bases, const uint32_t* d_rank_n)
 {
     __shared__ uint64_t warp_s[32];
+    if (d_rank_n) fixed_bits += bits_of_count(*d_rank_n);
     uint64_t nw = d_nw ? *d_nw : nw_max;
     uint32_t npass, bits;
     plan_shape(nw, fixed_bits, npass, bits);
     const int nb = 1 << bits;
     for (uint32_t k = 0; k < npass; ++k) {
-        const int d = 2 * threadIdx.x;   // two digits per thread (nb <= 2048)
+        const int d = 2 * threadIdx.x;   // two digits per thread
         uint64_t v0 = d < nb ? hist[(k << kSortMaxBits) + d] : 0;
         uint64_t v1 = d + 1 < nb ? hist[(k << kSortMaxBits) + d + 1] : 0;
         uint64_t tot;
@@ -136,18 +149,18 @@ cudaError_t sort_plan_weights(const SortScratch& sc, const uint32_t* weights, co
     if (e) return e;
     int grid = (int)std::min<uint64_t>((nw_max + 1023) / 1024 ? (nw_max + 1023) / 1024 : 1, 512);
     k_plan_hist_weights<<<grid, 1024, 0, st>>>(weights, offsets, d_nw, nw_max, sc.hist);
-    k_plan_finalize<<<1, 1024, 0, st>>>(d_nw, nw_max, 0, shift0, sc.hist, sc.plan, sc.bases);
+    k_plan_finalize<<<1, 1024, 0, st>>>(d_nw, nw_max, 0, shift0, sc.hist, sc.plan, sc.bases, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t sort_plan_keys(const SortScratch& sc, const uint64_t* keys, uint64_t n, const uint32_t* d_n,
-                           uint32_t shift0, uint32_t total_bits, cudaStream_t st)
+                           uint32_t shift0, uint32_t total_bits, cudaStream_t st, const uint32_t* d_rank_n)
 {
     cudaError_t e = cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * (kSortMaxPass << kSortMaxBits), st);
     if (e) return e;
     int grid = (int)std::min<uint64_t>((n + 4095) / 4096 ? (n + 4095) / 4096 : 1, 1024);
-    k_plan_hist_keys<<<grid, 1024, 0, st>>>(keys, n, d_n, shift0, total_bits, sc.hist);
-    k_plan_finalize<<<1, 1024, 0, st>>>(nullptr, 0, total_bits, shift0, sc.hist, sc.plan, sc.bases);
+    k_plan_hist_keys<<<grid, 1024, 0, st>>>(keys, n, d_n, shift0, total_bits, sc.hist, d_rank_n);
+    k_plan_finalize<<<1, 1024, 0, st>>>(nullptr, 0, total_bits, shift0, sc.hist, sc.plan, sc.bases, d_rank_n);
     return cudaGetLastError();
 }
 

@@ -16,7 +16,6 @@
 // host: surplus pass slots return at once, and slot k reads from the source,
 // or the temporaries, and writes to the destination when it is the last pass.
 #pragma once
-#include <type_traits>
 #include "fp_internal.cuh"
 
 namespace fp {
@@ -25,8 +24,8 @@ constexpr int kSortNT = 512;
 constexpr int kSortIPT = 8;
 constexpr int kSortWarps = kSortNT / 32;
 constexpr int kSortTile = kSortNT * kSortIPT;   // 4096
-constexpr int kSortMaxBits = 11;                // at most 2048 buckets per pass
-constexpr int kSortMaxPass = 6;
+constexpr int kSortMaxBits = 8;                 // at most 256 buckets per pass
+constexpr int kSortMaxPass = 8;                 // keys of up to 64 bits
 constexpr uint32_t kStFlagAgg = 1u << 30;
 constexpr uint32_t kStFlagInc = 2u << 30;
 constexpr uint32_t kStMask = (1u << 30) - 1;
@@ -73,34 +72,31 @@ FP_DEV const T* pick_src(int slot, int npass, const T* src, T* dst, T* tmp)
     return slot == 0 ? src : pick_dst(slot - 1, npass, dst, tmp);
 }
 
-// Two widths of every pass kernel: MAXB = 8 (small shared memory, two or three
-// CTAs per SM) runs the passes whose digit has at most 8 bits, MAXB = 11 the
-// others; the plan decides on the device and the other variant returns at once.
-constexpr int kSortSmallBits = 8;
-
-template <int DIG, bool CPT, bool CK64, bool CK32, int MAXB>
+// Digits of at most 8 bits keep the per-warp histograms, the digit scan and the
+// look-back small enough for two CTAs per SM; wider digits measured several
+// times slower per pass than two 8-bit passes.
+template <int DIG, bool CPT, bool CK64, bool CK32>
 struct SortSmem {
-    using dig_t = typename std::conditional<(MAXB <= 8), uint8_t, uint16_t>::type;
+    using dig_t = uint8_t;
     static constexpr size_t pt = CPT ? sizeof(int4) * kSortTile : 0;
     static constexpr size_t k64 = CK64 ? sizeof(uint64_t) * kSortTile : 0;
     static constexpr size_t val = sizeof(uint32_t) * kSortTile;
     static constexpr size_t k32 = CK32 ? sizeof(uint32_t) * kSortTile : 0;
     static constexpr size_t dig = sizeof(dig_t) * kSortTile;
-    static constexpr size_t whist = sizeof(uint16_t) * kSortWarps * (1 << MAXB);
-    static constexpr size_t gbase = sizeof(uint64_t) * (1 << MAXB);
-    static constexpr size_t cnt = sizeof(uint32_t) * (1 << MAXB);
-    static constexpr size_t off = sizeof(uint32_t) * (1 << MAXB);
+    static constexpr size_t whist = sizeof(uint16_t) * kSortWarps * (1 << kSortMaxBits);
+    static constexpr size_t gbase = sizeof(uint64_t) * (1 << kSortMaxBits);
+    static constexpr size_t cnt = sizeof(uint32_t) * (1 << kSortMaxBits);
+    static constexpr size_t off = sizeof(uint32_t) * (1 << kSortMaxBits);
     static constexpr size_t misc = 4 * (1 + kSortWarps + 15);   // tile id + block-scan scratch
     static constexpr size_t total = pt + k64 + val + k32 + dig + whist + gbase + cnt + off + misc;
 };
 
-template <int DIG, bool CPT, bool CK64, bool CK32, int MAXB>
-__global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_sort_pass(SortArgs a, int slot)
+template <int DIG, bool CPT, bool CK64, bool CK32>
+__global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
 {
     const SortPlan plan = *a.plan;
     if (slot >= (int)plan.npass) return;
-    if ((int)plan.bits > MAXB || (MAXB > kSortSmallBits && (int)plan.bits <= kSortSmallBits)) return;
-    using SM = SortSmem<DIG, CPT, CK64, CK32, MAXB>;
+    using SM = SortSmem<DIG, CPT, CK64, CK32>;
     using dig_t = typename SM::dig_t;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* sp = smem;
@@ -273,10 +269,10 @@ __global__ void k_sort_zero(uint32_t* status, uint32_t* counter, uint64_t n, con
 __global__ void k_plan_hist_weights(const uint32_t* weights, const uint64_t* offsets, const uint32_t* d_nw,
                                     uint64_t nw_max, uint32_t* hist);
 __global__ void k_plan_finalize(const uint32_t* d_nw, uint64_t nw_max, uint32_t fixed_bits, uint32_t shift0,
-                                const uint32_t* hist, SortPlan* plan, uint64_t* bases);
+                                const uint32_t* hist, SortPlan* plan, uint64_t* bases, const uint32_t* d_rank_n);
 // Plan of a fixed-width key sort: digits of bits [shift0, shift0 + total_bits) of k64 keys.
 __global__ void k_plan_hist_keys(const uint64_t* keys, uint64_t n, const uint32_t* d_n, uint32_t shift0,
-                                 uint32_t total_bits, uint32_t* hist);
+                                 uint32_t total_bits, uint32_t* hist, const uint32_t* d_rank_n);
 
 // host helpers
 struct SortScratch {
@@ -292,14 +288,16 @@ SortScratch take_sort_scratch(const Workspace& ws, uint64_t n);
 // plan from weights of ids; then run the passes of the given kind
 cudaError_t sort_plan_weights(const SortScratch& sc, const uint32_t* weights, const uint64_t* offsets,
                               const uint32_t* d_nw, uint64_t nw_max, uint32_t shift0, cudaStream_t st);
+// total_bits of key above shift0, plus the bit width of *d_rank_n when given
 cudaError_t sort_plan_keys(const SortScratch& sc, const uint64_t* keys, uint64_t n, const uint32_t* d_n,
-                           uint32_t shift0, uint32_t total_bits, cudaStream_t st);
+                           uint32_t shift0, uint32_t total_bits, cudaStream_t st,
+                           const uint32_t* d_rank_n = nullptr);
 
-template <int DIG, bool CPT, bool CK64, bool CK32, int MAXB>
-cudaError_t sort_launch_variant(const SortArgs& a, int slot, int num_sms, cudaStream_t st)
+template <int DIG, bool CPT, bool CK64, bool CK32>
+cudaError_t sort_launch(const SortArgs& a, int slot, int num_sms, cudaStream_t st)
 {
-    using SM = SortSmem<DIG, CPT, CK64, CK32, MAXB>;
-    auto kern = k_sort_pass<DIG, CPT, CK64, CK32, MAXB>;
+    using SM = SortSmem<DIG, CPT, CK64, CK32>;
+    auto kern = k_sort_pass<DIG, CPT, CK64, CK32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::total);
     if (e) return e;
     int per_sm = 0;
@@ -324,8 +322,8 @@ cudaError_t sort_run_pass(const SortScratch& sc, const SortArgs& a0, int slot, i
     uint64_t ntiles = (a.n + kSortTile - 1) / kSortTile;
     k_sort_zero<<<std::max(1, std::min(num_sms * 4, (int)((ntiles * (1 << kSortMaxBits) + 1023) / 1024))), 256, 0,
                   st>>>(sc.status, sc.counter + slot, a.n, sc.plan, slot);
-    if ((e = sort_launch_variant<DIG, CPT, CK64, CK32, kSortSmallBits>(a, slot, num_sms, st))) return e;
-    return sort_launch_variant<DIG, CPT, CK64, CK32, kSortMaxBits>(a, slot, num_sms, st);
+    if ((e = cudaGetLastError())) return e;
+    return sort_launch<DIG, CPT, CK64, CK32>(a, slot, num_sms, st);
 }
 
 }  // namespace fp
