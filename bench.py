@@ -44,8 +44,51 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def count_kernels(run, torch):
-    """Kernels one call of run() launches, from the profiler's device activity."""
+def count_kernels_captured(run, stream):
+    """Kernels one call of run() enqueues: the call is captured into a CUDA graph
+    (relaxed mode; nothing executes) and the graph's kernel nodes are counted."""
+    import ctypes
+    rt = ctypes.CDLL("libcudart.so.13")
+    h = ctypes.c_void_p(stream.cuda_stream)
+    if rt.cudaStreamBeginCapture(h, ctypes.c_int(2)) != 0:   # cudaStreamCaptureModeRelaxed
+        raise RuntimeError("begin capture failed")
+    graph = ctypes.c_void_p()
+    try:
+        run()
+    finally:
+        rc = rt.cudaStreamEndCapture(h, ctypes.byref(graph))
+    if rc != 0 or not graph.value:
+        rt.cudaGetLastError()
+        raise RuntimeError("capture failed (%d)" % rc)
+    try:
+        num = ctypes.c_size_t(0)
+        if rt.cudaGraphGetNodes(graph, None, ctypes.byref(num)) != 0:
+            raise RuntimeError("graph nodes query failed")
+        nodes = (ctypes.c_void_p * max(1, num.value))()
+        if rt.cudaGraphGetNodes(graph, nodes, ctypes.byref(num)) != 0:
+            raise RuntimeError("graph nodes query failed")
+        kernels = 0
+        for i in range(num.value):
+            t = ctypes.c_int(-1)
+            if rt.cudaGraphNodeGetType(ctypes.c_void_p(nodes[i]), ctypes.byref(t)) == 0 and t.value == 0:
+                kernels += 1   # cudaGraphNodeTypeKernel
+        return kernels
+    finally:
+        rt.cudaGraphDestroy(graph)
+
+
+def count_kernels(run, torch, stream=None):
+    """Kernels one call of run() launches: counted from a captured graph when
+    possible, else from the profiler's device activity."""
+    if stream is not None:
+        try:
+            k = count_kernels_captured(run, stream)
+            torch.cuda.synchronize()
+            if k:
+                return k
+        except Exception as ex:
+            print("gpu_launches: capture count failed: %r" % (ex,), file=sys.stderr)
+            torch.cuda.synchronize()
     try:
         from torch.profiler import ProfilerActivity, profile
         torch.cuda.synchronize()
@@ -252,7 +295,8 @@ def main():
                                                        P(O["nodes"]), ncap, P(O["num_nodes"]), P(O["leaf"]),
                                                        P(O["leaf_perm"]), P(O["owner"]), P(ws), ws.numel(), S)),
             ("subsample", lambda: L.fp_subsample(P(O["nodes"]), P(O["num_nodes"]), ncap, P(O["dist"]), P(O["perm"]),
-                                                 P(O["owner"]), n, P(O["final"]), P(O["final_perm"]), P(ws),
+                                                 P(O["owner"]), n, P(O["chunks"]), P(O["num_chunks"]),
+                                                 P(O["offsets"]), P(O["final"]), P(O["final_perm"]), P(ws),
                                                  ws.numel(), S)),
         ]
 
@@ -276,7 +320,7 @@ def main():
     assert fp.get_device_error(stream=st) == 0, "device error word set"
 
     # kernels per step (CUPTI through the torch profiler, one step outside the timed region)
-    launches_per_step = count_kernels(lambda: step(False), torch)
+    launches_per_step = count_kernels(lambda: step(False), torch, st)
 
     clk = ClockSampler(local)
     if world > 1:

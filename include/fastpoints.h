@@ -222,10 +222,13 @@ fp_status fp_build_chunk_octree(const fp_point* d_sorted, const uint32_t* d_perm
 /* Final level-of-detail layout: nodes in preorder, each node's kept points in
  * ascending original index (points kept by nodes above the chunks are merged
  * across chunks: the stitch).  Fills d_nodes[*].first and writes d_final /
- * d_final_perm (n each).  node_cap <= 2^23; the workspace is sized for this
+ * d_final_perm (n each, required).  d_chunks / d_num_chunks / d_offsets are the
+ * chunks the points were distributed into (fp_merge_chunks); the layout is
+ * computed chunk by chunk.  node_cap <= 2^23; the workspace is sized for this
  * node_cap (fp_workspace_size(FP_STAGE_SUBSAMPLE) assumes the bound above). */
 fp_status fp_subsample(fp_node* d_nodes, const uint32_t* d_num_nodes, uint32_t node_cap,
                        const fp_point* d_sorted, const uint32_t* d_perm, const uint32_t* d_owner, uint64_t n,
+                       const fp_chunk* d_chunks, const uint32_t* d_num_chunks, const uint64_t* d_offsets,
                        fp_point* d_final, uint32_t* d_final_perm,
                        void* d_ws, size_t ws_bytes, cudaStream_t stream);
 

@@ -262,10 +262,13 @@ fp_status fp_build_chunk_octree(const fp_point* d_sorted, const uint32_t* d_perm
 
 // Sec. 4.4: final layout, points of nodes above the chunks merged across chunks
 fp_status fp_subsample(fp_node* d_nodes, const uint32_t* d_num_nodes, uint32_t node_cap, const fp_point* d_sorted,
-                       const uint32_t* d_perm, const uint32_t* d_owner, uint64_t n, fp_point* d_final,
+                       const uint32_t* d_perm, const uint32_t* d_owner, uint64_t n, const fp_chunk* d_chunks,
+                       const uint32_t* d_num_chunks, const uint64_t* d_offsets, fp_point* d_final,
                        uint32_t* d_final_perm, void* d_ws, size_t ws_bytes, cudaStream_t stream)
 {
-    if (!d_num_nodes || (node_cap && !d_nodes) || (n && (!d_sorted || !d_perm || !d_owner || !d_final)))
+    if (!d_num_nodes || (node_cap && !d_nodes) ||
+        (n && (!d_sorted || !d_perm || !d_owner || !d_chunks || !d_num_chunks || !d_offsets || !d_final ||
+               !d_final_perm)))
         return FP_ERR_INVALID;
     if (n >= kMaxPoints) return FP_ERR_TOO_LARGE;
     if (n && (!aligned16(d_sorted) || !aligned16(d_final))) return FP_ERR_ALIGN;
@@ -273,8 +276,8 @@ fp_status fp_subsample(fp_node* d_nodes, const uint32_t* d_num_nodes, uint32_t n
     Workspace ws;
     fp_status s = make_ws(d_ws, ws_bytes, subsample_ws_bytes(n, node_cap), ws);
     if (s != FP_OK) return s;
-    return cuda_status(launch_subsample(d_nodes, d_num_nodes, node_cap, d_sorted, d_perm, d_owner, n, d_final,
-                                        d_final_perm, ws, stream));
+    return cuda_status(launch_subsample(d_nodes, d_num_nodes, node_cap, d_sorted, d_perm, d_owner, n, d_chunks,
+                                        d_num_chunks, d_offsets, d_final, d_final_perm, ws, stream));
 }
 
 }  // extern "C"

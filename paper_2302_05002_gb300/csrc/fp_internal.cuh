@@ -67,7 +67,8 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
                           uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
                           const Workspace& ws, cudaStream_t st);
 cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const fp_point* sorted,
-                             const uint32_t* perm, const uint32_t* owner, uint64_t n, fp_point* final_pts,
+                             const uint32_t* perm, const uint32_t* owner, uint64_t n, const fp_chunk* chunks,
+                             const uint32_t* num_chunks, const uint64_t* offsets, fp_point* final_pts,
                              uint32_t* final_perm, const Workspace& ws, cudaStream_t st);
 
 }  // namespace fp

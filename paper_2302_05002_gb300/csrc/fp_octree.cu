@@ -30,7 +30,7 @@
 //   5. the points are scattered stably by leaf id (leaf-grouped output) and,
 //      in fp_subsample, by owner id (final output); owner segments of nodes
 //      above the chunks (the stitch) are re-sorted by original index.
-#include "fp_sort.cuh"
+#include "fp_seg.cuh"
 
 namespace fp {
 
@@ -307,8 +307,7 @@ struct UnitSmem {
     uint64_t key[kUnitCap];
     uint64_t key2[kUnitCap];
     uint32_t j[kUnitCap];       // by local index
-    int16_t ps[kUnitCap];       // by sorted position: left chain pointer (see k_units)
-    int16_t ns[kUnitCap];       // right chain pointer
+    uint32_t mt[kUnitCap];      // min-tree over hj: internal nodes 1..P-1 (leaves are hj itself)
     uint16_t v[kUnitCap];       // local index by sorted position
     uint16_t v2[kUnitCap];
     uint16_t piece[kUnitCap];   // piece of a local index
@@ -396,11 +395,10 @@ FP_DEV int piece_of(const UnitSmem& S, int np, int r)
 // One CTA per window of kWindow record positions: the pieces starting in it.
 // Per unit:
 //   sort the records by key (stable, 8-bit LSD passes in shared memory);
-//   nearest smaller index on each side along the key order (chain jumping:
-//   while the candidate's index is larger, jump to the candidate's own
-//   pointer; every skipped position holds a larger index).  The level shared
-//   with the nearer of the two, plus one, is lambda unless the record is the
-//   minimum of its piece, whose lambda comes from the split tree;
+//   nearest smaller index on each side along the key order (min-tree walks
+//   over one representative per run of equal keys).  The deeper of the levels
+//   shared with those two neighbours, plus one, is lambda unless the record is
+//   the minimum of its piece, whose lambda comes from the split tree;
 //   deep subtrees of inner pieces by binary search on the sorted keys.
 // first piece of every unit: lower bound of the unit's window start over the sorted piece begins
 __global__ void k_unit_ranges(const uint64_t* piece_begin_sorted, const uint32_t* npieces, uint32_t cap,
@@ -599,32 +597,46 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         }
         __syncthreads();
         const int nh = (int)S.nh;
-        // ---- nearest smaller index among the heads (chain jumping; every skipped
-        // position holds a larger index), inside each thread's block first
-        const int per = (nh + kUnitNT - 1) / kUnitNT;   // <= kUnitCap / kUnitNT
-        const int b0 = min(nh, (int)threadIdx.x * per), b1 = min(nh, b0 + per);
-        for (int r = b0; r < b1; ++r) {
-            const uint32_t jr = S.hj[r];
-            int x = r - 1;
-            while (x >= b0 && S.hj[x] > jr) x = S.ps[x];
-            S.ps[r] = (int16_t)x;   // x < b0: continue from x later (every index in (x, r) is larger)
-        }
-        for (int r = b1 - 1; r >= b0; --r) {
-            const uint32_t jr = S.hj[r];
-            int x = r + 1;
-            while (x < b1 && S.hj[x] > jr) x = S.ns[x];
-            S.ns[r] = (int16_t)x;
-        }
+        // ---- nearest smaller index on each side of every representative, by a
+        // min-tree over hj (the leaves are hj itself, padded to a power of two):
+        // climb to the first sibling subtree that holds a smaller index, then
+        // descend into it towards the near side.  The level shared with that
+        // neighbour is the deepest level at which the representative is not
+        // its cell's minimum on that side (keys are sorted, so nearer records
+        // share at least as many levels).
+        int P = 1;
+        while (P < nh) P <<= 1;
+        auto tv = [&](int k) -> uint32_t {
+            return k >= P ? (k - P < nh ? S.hj[k - P] : 0xFFFFFFFFu) : S.mt[k];
+        };
+        for (int k = max(1, P / 2) + (int)threadIdx.x; k < P; k += kUnitNT) S.mt[k] = min(tv(2 * k), tv(2 * k + 1));
         __syncthreads();
-        for (int r = b0; r < b1; ++r) {
+        for (int m = P / 4; m >= 1; m >>= 1) {
+            for (int k = m + (int)threadIdx.x; k < 2 * m; k += kUnitNT) S.mt[k] = min(S.mt[2 * k], S.mt[2 * k + 1]);
+            __syncthreads();
+        }
+        for (int r = threadIdx.x; r < nh; r += kUnitNT) {
             const uint32_t jr = S.hj[r];
             const uint64_t kr = S.key2[r];
-            int x = S.ps[r];
-            while (x >= 0 && S.hj[x] > jr) x = S.ps[x];
-            S.cl[r] = x >= 0 ? (uint8_t)common_level(kr, S.key2[x]) : (uint8_t)255;
-            x = S.ns[r];
-            while (x < nh && S.hj[x] > jr) x = S.ns[x];
-            S.cr[r] = x < nh ? (uint8_t)common_level(kr, S.key2[x]) : (uint8_t)255;
+            int left = -1, right = -1;
+            for (int k = P + r; k > 1; k >>= 1) {
+                if ((k & 1) && tv(k - 1) < jr) {
+                    k = k - 1;
+                    while (k < P) k = tv(2 * k + 1) < jr ? 2 * k + 1 : 2 * k;
+                    left = k - P;
+                    break;
+                }
+            }
+            for (int k = P + r; k > 1; k >>= 1) {
+                if (!(k & 1) && tv(k + 1) < jr) {
+                    k = k + 1;
+                    while (k < P) k = tv(2 * k) < jr ? 2 * k : 2 * k + 1;
+                    right = k - P;
+                    break;
+                }
+            }
+            S.cl[r] = left >= 0 ? (uint8_t)common_level(kr, S.key2[left]) : (uint8_t)255;
+            S.cr[r] = right >= 0 ? (uint8_t)common_level(kr, S.key2[right]) : (uint8_t)255;
         }
         __syncthreads();
         // ---- deep subtrees inside pieces whose node is still inner: one warp per piece
@@ -927,6 +939,7 @@ struct OctBufs {
     uint8_t *own_code, *leaf_code;
     uint32_t* leafid;
     uint32_t* unit_p0;
+    SegScratch seg;
 };
 
 // one carve-up serves both the size query (base == nullptr) and the launch
@@ -968,6 +981,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.own_code = ws.take<uint8_t>(N); B.leaf_code = ws.take<uint8_t>(N);
     B.leafid = ws.take<uint32_t>(N);
     B.unit_p0 = ws.take<uint32_t>((N + kWindow - 1) / kWindow + 2);
+    B.seg = take_seg_scratch(ws, N, Ly.cells, 1);
     return B;
 }
 
@@ -994,7 +1008,6 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
                           uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
                           const Workspace& ws, cudaStream_t st)
 {
-    (void)chunks; (void)num_chunks; (void)offsets;   // chunk ranges are implied by the cell grouping
     cudaError_t e;
     if (n == 0) {
         k_set_u32<<<1, 1, 0, st>>>(num_nodes, 0);
@@ -1140,8 +1153,22 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
                                         owner, B.leafid, B.nown, g, lmax, ws.err);
         k_write_nown<<<(unsigned)((Ly.node_cap + 255) / 256), 256, 0, st>>>(nodes, nnode, node_cap, B.nown);
     }
-    // 9. leaf-grouped points: stable scatter by leaf id
+    // 9. leaf-grouped points: stable scatter by leaf id, chunk by chunk (every
+    // leaf lies in the subtree of its points' chunk); the whole-array sort by
+    // leaf id runs instead, gated on the device, when a chunk does not fit
     if (leaf_pts || leaf_perm) {
+        SegCall sg{};
+        sg.mode = SEG_LEAF;
+        sg.nodes = nodes; sg.num_nodes = num_nodes; sg.node_cap = node_cap;
+        sg.chunks = chunks; sg.num_chunks = num_chunks; sg.offsets = offsets;
+        sg.pt_in = leaf_pts ? reinterpret_cast<const int4*>(sorted) : nullptr;
+        sg.pt_out = reinterpret_cast<int4*>(leaf_pts);
+        sg.val_in = perm; sg.val_out = leaf_perm;
+        sg.id_in = B.leafid;
+        sg.n = N;
+        sg.first = reinterpret_cast<const uint64_t*>(nodes) + offsetof(fp_node, leaf_first) / sizeof(uint64_t);
+        sg.first_stride = sizeof(fp_node) / sizeof(uint64_t);
+        if ((e = seg_scatter(B.seg, sg, ws, st))) return e;
         if ((e = sort_plan_weights(sc, B.leafw, nullptr, nnode, Ly.node_cap, 0, st))) return e;
         SortArgs a{};
         a.b.pt_src = reinterpret_cast<const int4*>(sorted);
@@ -1149,7 +1176,7 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         a.b.pt_dst = reinterpret_cast<int4*>(leaf_pts);
         a.b.val_src = perm; a.b.val_tmp = B.lt_val; a.b.val_dst = leaf_perm;
         a.b.k32_src = B.leafid; a.b.k32_tmp = B.lt_k32; a.b.k32_dst = nullptr;
-        a.n = N; a.err = ws.err;
+        a.n = N; a.d_n = B.seg.cnt + 5; a.err = ws.err;
         if (leaf_pts) e = run_sort<DIG_K32, true, false, true>(sc, a, ws, st);
         else e = run_sort<DIG_K32, false, false, true>(sc, a, ws, st);
         if (e) return e;
@@ -1173,10 +1200,11 @@ __global__ void k_first_out(fp_node* nodes, const uint32_t* num_nodes, uint32_t 
 }
 
 // owner segments whose original indices are not ascending (owners above the chunks)
-__global__ void k_mark_unsorted(const uint32_t* fown, const uint32_t* fperm, uint64_t n, uint32_t* mark,
-                                const uint32_t* nm)
+__global__ void k_mark_unsorted(const uint32_t* fown, const uint32_t* fperm, uint64_t n, const uint32_t* d_n,
+                                uint32_t* mark, const uint32_t* nm)
 {
     const uint32_t M = *nm;
+    if (*d_n < n) n = *d_n;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f + 1 < n; f += stride)
         if (fown[f] == fown[f + 1] && fperm[f] > fperm[f + 1] && fown[f] < M) mark[fown[f]] = 1;
@@ -1232,6 +1260,32 @@ __global__ void k_stitch_put(const uint32_t* nstitch, const uint64_t* key, const
     fperm[f] = tperm[t];
 }
 
+// stitch records staged by the segmented scatter: a node above the chunks keeps
+// all of its points through the staging area, the others none of theirs
+__global__ void k_stitch_counts(const uint8_t* inside, const uint32_t* nown, const uint32_t* nm, uint32_t* scnt,
+                                uint32_t cap)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap) return;
+    scnt[i] = i < *nm && !inside[i] ? nown[i] : 0u;
+}
+
+// sorted staging record t = (node X, original index): final position first[X] + rank inside X
+__global__ void k_stitch_place(const uint32_t* nstaged, const uint64_t* key, const uint32_t* src, int shift,
+                               const uint32_t* nm, const uint32_t* soff, const uint64_t* first, const int4* pts,
+                               const uint32_t* perm, uint64_t n, int4* fin, uint32_t* fperm, uint32_t* err)
+{
+    const uint32_t S = *nstaged, M = *nm;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < S; t += gridDim.x * blockDim.x) {
+        const uint32_t X = (uint32_t)(key[t] >> shift);
+        const uint32_t j = src[t];
+        const uint64_t f = X < M ? first[X] + (t - soff[X]) : n;
+        if (f >= n || j >= n) { raise(err, FP_ERR_CAPACITY); continue; }
+        fin[f] = __ldg(pts + j);
+        fperm[f] = perm[j];
+    }
+}
+
 static const uint64_t kMaxScanNodes = (uint64_t)kScanTile * kScanMaxTiles;
 
 struct SubBufs {
@@ -1246,7 +1300,12 @@ struct SubBufs {
     uint32_t* s_perm;
     uint64_t* tiles64;
     uint32_t* tiles32;
+    uint32_t* scnt;
+    SegScratch seg;
 };
+
+// chunks of a cloud of n points: at most n, and at most 8^7 count-grid cells
+static uint64_t chunk_bound(uint64_t n) { return std::min<uint64_t>(n ? n : 1, 1ull << 21); }
 
 static SubBufs sub_carve(const Workspace& ws, uint64_t n, uint64_t M)
 {
@@ -1263,6 +1322,8 @@ static SubBufs sub_carve(const Workspace& ws, uint64_t n, uint64_t M)
     B.s_key3 = ws.take<uint64_t>(N); B.s_val3 = ws.take<uint32_t>(N);
     B.s_pt = ws.take<int4>(N); B.s_perm = ws.take<uint32_t>(N);
     B.tiles64 = ws.take<uint64_t>(kScanMaxTiles); B.tiles32 = ws.take<uint32_t>(kScanMaxTiles);
+    B.scnt = ws.take<uint32_t>(M + 1);
+    B.seg = take_seg_scratch(ws, N, chunk_bound(n), M);
     return B;
 }
 
@@ -1274,7 +1335,8 @@ size_t subsample_ws_bytes(uint64_t n, uint64_t node_cap)
 }
 
 cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const fp_point* sorted,
-                             const uint32_t* perm, const uint32_t* owner, uint64_t n, fp_point* final_pts,
+                             const uint32_t* perm, const uint32_t* owner, uint64_t n, const fp_chunk* chunks,
+                             const uint32_t* num_chunks, const uint64_t* offsets, fp_point* final_pts,
                              uint32_t* final_perm, const Workspace& ws, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
@@ -1287,60 +1349,87 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     uint32_t *nown = B.nown, *mark = B.mark, *mrank = B.mrank, *mlist = B.mlist, *mown = B.mown, *soff = B.soff;
     uint32_t* cnt = B.cnt;
     uint64_t* first = B.first;
-    int4* t_pt = B.t_pt;
-    uint32_t *t_val = B.t_val, *t_k32 = B.t_k32, *fown = B.fown;
-    uint64_t *s_key = B.s_key, *s_key2 = B.s_key2, *s_key3 = B.s_key3;
-    uint32_t *s_val = B.s_val, *s_val2 = B.s_val2, *s_val3 = B.s_val3;
-    int4* s_pt = B.s_pt;
-    uint32_t* s_perm = B.s_perm;
-    uint64_t* tiles64 = B.tiles64;
-    uint32_t* tiles32 = B.tiles32;
     const unsigned gM = (M + 255) / 256;
+    const unsigned gN = (unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
 
     uint32_t* nm = cnt + 2;   // node count clamped to the capacity
+    uint32_t* nstaged = cnt + 3;
     k_clamp_copy<<<1, 1, 0, st>>>(num_nodes, node_cap, nm);
     k_nown_in<<<gM, 256, 0, st>>>(nodes, num_nodes, node_cap, nown);
-    if ((e = scan_exclusive<uint32_t, uint64_t>(nown, first, M, nm, tiles64, (uint64_t*)nullptr,
+    if ((e = scan_exclusive<uint32_t, uint64_t>(nown, first, M, nm, B.tiles64, (uint64_t*)nullptr,
                                                 (uint64_t*)nullptr, st)))
         return e;
     k_first_out<<<gM, 256, 0, st>>>(nodes, num_nodes, node_cap, first);
-    // stable scatter by owner id (index order inside every chunk)
+
+    // 1. stable scatter by owner id, chunk by chunk; owners above the chunk are staged
+    int pbits = 1;
+    while ((1ull << pbits) < N) ++pbits;   // original indices are below 2^pbits
+    SegCall sg{};
+    sg.mode = SEG_OWNER;
+    sg.nodes = nodes; sg.num_nodes = num_nodes; sg.node_cap = node_cap;
+    sg.chunks = chunks; sg.num_chunks = num_chunks; sg.offsets = offsets;
+    sg.pt_in = reinterpret_cast<const int4*>(sorted); sg.pt_out = reinterpret_cast<int4*>(final_pts);
+    sg.val_in = perm; sg.val_out = final_perm;
+    sg.id_in = owner;
+    sg.n = N;
+    sg.first = first; sg.first_stride = 1;
+    sg.st_key = B.s_key; sg.st_src = B.s_val; sg.st_count = nstaged; sg.st_shift = pbits;
+    if ((e = seg_scatter(B.seg, sg, ws, st))) return e;
+    // 2. the stitch: staged records sorted by (node, original index), then placed
+    k_stitch_counts<<<gM, 256, 0, st>>>(B.seg.inside, nown, nm, B.scnt, M);
+    if ((e = scan_exclusive<uint32_t, uint32_t>(B.scnt, soff, M, nm, B.tiles32, (uint32_t*)nullptr,
+                                                (uint32_t*)nullptr, st)))
+        return e;
+    if ((e = sort_plan_keys(sc, B.s_key, N, nstaged, 0, (uint32_t)pbits, st, nm))) return e;
+    {
+        SortArgs b{};
+        b.b.k64_src = B.s_key; b.b.k64_tmp = B.s_key2; b.b.k64_dst = B.s_key3;
+        b.b.val_src = B.s_val; b.b.val_tmp = B.s_val2; b.b.val_dst = B.s_val3;
+        b.n = N; b.d_n = nstaged; b.err = ws.err;
+        for (int slot = 0; slot < kSortMaxPass; ++slot)
+            if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, b, slot, ws.num_sms, st))) return e;
+    }
+    k_stitch_place<<<gN, 256, 0, st>>>(nstaged, B.s_key3, B.s_val3, pbits, nm, soff, first,
+                                       reinterpret_cast<const int4*>(sorted), perm, N,
+                                       reinterpret_cast<int4*>(final_pts), final_perm, ws.err);
+
+    // whole-array path (runs with seg cnt[5] = n records when a chunk did not fit, else on none):
+    // stable scatter by owner id, then the owner segments spanning several chunks re-sorted
+    const uint32_t* gate = B.seg.cnt + 5;
     if ((e = sort_plan_weights(sc, nown, nullptr, nm, M, 0, st))) return e;
     SortArgs a{};
-    a.b.pt_src = reinterpret_cast<const int4*>(sorted); a.b.pt_tmp = t_pt;
+    a.b.pt_src = reinterpret_cast<const int4*>(sorted); a.b.pt_tmp = B.t_pt;
     a.b.pt_dst = reinterpret_cast<int4*>(final_pts);
-    a.b.val_src = perm; a.b.val_tmp = t_val; a.b.val_dst = final_perm;
-    a.b.k32_src = owner; a.b.k32_tmp = t_k32; a.b.k32_dst = fown;
-    a.n = N; a.err = ws.err;
+    a.b.val_src = perm; a.b.val_tmp = B.t_val; a.b.val_dst = final_perm;
+    a.b.k32_src = owner; a.b.k32_tmp = B.t_k32; a.b.k32_dst = B.fown;
+    a.n = N; a.d_n = gate; a.err = ws.err;
     for (int slot = 0; slot < kSortMaxPass; ++slot)
         if ((e = sort_run_pass<DIG_K32, true, false, true>(sc, a, slot, ws.num_sms, st))) return e;
-    // stitch: owner segments spanning several chunks, re-sorted by original index
     if ((e = cudaMemsetAsync(mark, 0, (size_t)M * 4, st))) return e;
-    int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
-    k_mark_unsorted<<<grid, 256, 0, st>>>(fown, final_perm, N, mark, nm);
-    if ((e = scan_exclusive<uint32_t, uint32_t>(mark, mrank, M, nm, tiles32, cnt, (uint32_t*)nullptr, st)))
+    if ((e = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), st))) return e;
+    k_mark_unsorted<<<gN, 256, 0, st>>>(B.fown, final_perm, N, gate, mark, nm);
+    if ((e = scan_exclusive<uint32_t, uint32_t>(mark, mrank, M, nm, B.tiles32, cnt, (uint32_t*)nullptr, st)))
         return e;
     k_stitch_list<<<gM, 256, 0, st>>>(mark, mrank, num_nodes, node_cap, mlist, nown, mown);
-    if ((e = scan_exclusive<uint32_t, uint32_t>(mown, soff, M, cnt, tiles32, cnt + 1, (uint32_t*)nullptr, st)))
+    if ((e = scan_exclusive<uint32_t, uint32_t>(mown, soff, M, cnt, B.tiles32, cnt + 1, (uint32_t*)nullptr, st)))
         return e;
-    k_stitch_keys<<<ws.num_sms * 8, 256, 0, st>>>(mlist, cnt, soff, cnt + 1, first, final_perm, s_key, s_val);
+    k_stitch_keys<<<ws.num_sms * 8, 256, 0, st>>>(mlist, cnt, soff, cnt + 1, first, final_perm, B.s_key, B.s_val);
     int rank_bits = 1;
     while ((1ull << rank_bits) < M) ++rank_bits;
-    if ((e = sort_plan_keys(sc, s_key, N, cnt + 1, 0, (uint32_t)(32 + rank_bits), st))) return e;
+    if ((e = sort_plan_keys(sc, B.s_key, N, cnt + 1, 0, (uint32_t)(32 + rank_bits), st))) return e;
     SortArgs b{};
-    b.b.k64_src = s_key; b.b.k64_tmp = s_key2; b.b.k64_dst = s_key3;
-    b.b.val_src = s_val; b.b.val_tmp = s_val2; b.b.val_dst = s_val3;
+    b.b.k64_src = B.s_key; b.b.k64_tmp = B.s_key2; b.b.k64_dst = B.s_key3;
+    b.b.val_src = B.s_val; b.b.val_tmp = B.s_val2; b.b.val_dst = B.s_val3;
     b.n = N; b.d_n = cnt + 1; b.err = ws.err;
     for (int slot = 0; slot < kSortMaxPass; ++slot)
         if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, b, slot, ws.num_sms, st))) return e;
-    unsigned gN = (unsigned)((N + 255) / 256);
-    k_stitch_gather<<<gN, 256, 0, st>>>(cnt + 1, s_val3, reinterpret_cast<const int4*>(final_pts), final_perm, s_pt,
-                                        s_perm);
-    k_stitch_put<<<gN, 256, 0, st>>>(cnt + 1, s_key3, mlist, soff, first, s_pt, s_perm,
-                                     reinterpret_cast<int4*>(final_pts), final_perm);
+    k_stitch_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(cnt + 1, B.s_val3,
+                                                                  reinterpret_cast<const int4*>(final_pts),
+                                                                  final_perm, B.s_pt, B.s_perm);
+    k_stitch_put<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(cnt + 1, B.s_key3, mlist, soff, first, B.s_pt,
+                                                               B.s_perm, reinterpret_cast<int4*>(final_pts),
+                                                               final_perm);
     return cudaGetLastError();
 }
-
-
 
 }  // namespace fp

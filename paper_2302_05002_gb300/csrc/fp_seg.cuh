@@ -1,0 +1,258 @@
+// fp_seg.cuh -- single-pass stable scatter of the chunk array by node id, chunk
+// by chunk: the leaf grouping of fp_build_chunk_octree and the owner layout of
+// fp_subsample (Sec. 4.4: every chunk's local octree is a subtree of the global
+// one).
+//
+// Inside a chunk the distributed order is index order, and every leaf of a
+// chunk's points, and every owner below the chunk, lies in the subtree of the
+// chunk's node, whose ids are consecutive in preorder.  So the scatter runs
+// chunk by chunk with digit = node id - id of the chunk's node: tiles never
+// straddle chunks, the decoupled look-back stops at the chunk's first tile, and
+// the bucket bases come from the node table -- no histogram or plan passes.
+// Points owned by a node above their chunk (the stitch, owner layout only) take
+// the last digit and go to a staging area, merged across chunks afterwards.
+//
+// Two widths: chunks of at most 256 digits run on the 8-bit variant (two CTAs
+// per SM), chunks of up to 2048 on the 11-bit one; a chunk with more sets the
+// fail word and the caller's whole-array sort runs instead.
+#pragma once
+#include <cstddef>
+#include "fp_sort.cuh"
+
+namespace fp {
+
+static_assert(sizeof(fp_node) == 40 && offsetof(fp_node, leaf_first) % 8 == 0, "fp_node layout");
+
+constexpr int kSegSmallBits = 8;
+constexpr int kSegMaxBits = 11;
+
+struct SegTile {
+    uint32_t chunk, index;   // chunk, and tile number inside the chunk
+};
+
+struct SegArgs {
+    const int4* pt_in;                    // nullable: points not carried
+    int4* pt_out;
+    const uint32_t* val_in;               // original index of every record
+    uint32_t* val_out;                    // nullable
+    const uint32_t* id_in;                // node id of every record
+    const uint64_t* offsets;              // chunk c = records [offsets[c], offsets[c + 1])
+    const uint32_t* seg_lo;               // id of the chunk's node
+    const uint32_t* seg_nb;               // digits of the chunk
+    const SegTile* tiles;                 // this variant's tiles, each chunk's in order
+    const uint32_t* d_ntiles;
+    uint64_t ntiles_max;
+    const uint64_t* first;                // output start of node id: first[id * first_stride]
+    uint32_t first_stride;
+    uint32_t* status;                     // [row][1 << MAXB], row = tile start / kSortTile
+    uint32_t* counter;
+    int stitch;                           // nonzero: the chunk's last digit is the staging digit
+    uint64_t* st_key;                     // (node id << st_shift) | original index
+    uint32_t* st_src;                     // position in the chunk array
+    uint32_t* st_count;
+    uint64_t st_cap;
+    int st_shift;
+    uint64_t n;                           // records, and output positions
+
+    const uint32_t* d_fail;
+    uint32_t* err;
+};
+
+template <bool CPT, int MAXB>
+struct SegSmem {
+    using dig_t = typename std::conditional<(MAXB <= 8), uint8_t, uint16_t>::type;
+    static constexpr size_t pt = CPT ? sizeof(int4) * kSortTile : 0;
+    static constexpr size_t gbase = sizeof(uint64_t) * (1 << MAXB);
+    static constexpr size_t val = sizeof(uint32_t) * kSortTile;
+    static constexpr size_t cnt = sizeof(uint32_t) * (1 << MAXB);
+    static constexpr size_t off = sizeof(uint32_t) * (1 << MAXB);
+    static constexpr size_t pos = sizeof(uint16_t) * kSortTile;   // tile position of a staged record
+    static constexpr size_t dig = sizeof(dig_t) * kSortTile;
+    static constexpr size_t whist = sizeof(uint16_t) * kSortWarps * (1 << MAXB);
+    static constexpr size_t misc = 4 * (1 + kSortWarps + 15);
+    static constexpr size_t total = pt + gbase + val + cnt + off + pos + dig + whist + misc;
+};
+
+template <bool CPT, int MAXB>
+__global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegArgs a)
+{
+    if (*a.d_fail) return;
+    using SM = SegSmem<CPT, MAXB>;
+    using dig_t = typename SM::dig_t;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* sp = smem;
+    int4* s_pt = reinterpret_cast<int4*>(sp); sp += SM::pt;
+    uint64_t* s_gbase = reinterpret_cast<uint64_t*>(sp); sp += SM::gbase;
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(sp); sp += SM::val;
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(sp); sp += SM::cnt;
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(sp); sp += SM::off;
+    uint16_t* s_pos = reinterpret_cast<uint16_t*>(sp); sp += SM::pos;
+    dig_t* s_dig = reinterpret_cast<dig_t*>(sp); sp += SM::dig;
+    uint16_t* s_whist = reinterpret_cast<uint16_t*>(sp); sp += SM::whist;
+    uint32_t* s_misc = reinterpret_cast<uint32_t*>(sp);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
+    constexpr int kStride = 1 << MAXB;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_misc[0] = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const uint64_t tile = s_misc[0];
+        if (tile >= ntiles) break;
+        const SegTile td = a.tiles[tile];
+        const uint32_t lo = a.seg_lo[td.chunk];
+        const int nb = (int)a.seg_nb[td.chunk];   // 1 .. 1 << MAXB (checked by the setup)
+        const uint64_t cend = a.offsets[td.chunk + 1];
+        const uint64_t base = a.offsets[td.chunk] + (uint64_t)td.index * kSortTile;
+        const int tn = (int)(cend - base < (uint64_t)kSortTile ? cend - base : (uint64_t)kSortTile);
+        const bool last = base + (uint64_t)tn >= cend;   // no later tile of the chunk reads this one
+        const uint64_t row = base / kSortTile;            // tiles that are not last are full: rows are distinct
+        const int sdig = a.stitch ? nb - 1 : nb;          // staging digit (nb: none)
+        for (int q = threadIdx.x; q < kSortWarps * nb; q += kSortNT) s_whist[q] = 0;
+        __syncthreads();
+        uint16_t* wh = s_whist + warp * nb;
+
+        // ---- digits and in-warp stable ranks
+        uint32_t pack[kSortIPT];
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const int p = warp * (kSortIPT * 32) + r * 32 + lane;
+            uint32_t d = 0xFFFFu;
+            if (p < tn) {
+                d = a.id_in[base + p] - lo;
+                if (d >= (uint32_t)sdig) {
+                    if (!a.stitch) raise(a.err, FP_ERR_CAPACITY);   // a leaf outside the chunk's subtree
+                    d = (uint32_t)(nb - 1);
+                }
+            }
+            uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader && d != 0xFFFFu) {
+                old = wh[d];
+                wh[d] = (uint16_t)(old + __popc(peers));
+            }
+            old = __shfl_sync(0xFFFFFFFFu, old, leader);
+            pack[r] = d | ((old + __popc(peers & lanemask_lt())) << 16);
+            __syncwarp();
+        }
+        __syncthreads();
+        // ---- per-digit totals, per-warp exclusive prefixes; publish aggregates
+        for (int d = threadIdx.x; d < nb; d += kSortNT) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                uint32_t v = s_whist[w * nb + d];
+                s_whist[w * nb + d] = (uint16_t)s;
+                s += v;
+            }
+            s_cnt[d] = s;
+            if (!last && d != sdig) a.status[row * kStride + d] = (td.index == 0 ? kStFlagInc : kStFlagAgg) | s;
+        }
+        __syncthreads();
+        {
+            const int per = (nb + kSortNT - 1) / kSortNT;
+            const int d0 = threadIdx.x * per;
+            uint32_t s = 0;
+            for (int q = 0; q < per; ++q)
+                if (d0 + q < nb) s += s_cnt[d0 + q];
+            uint32_t tot;
+            uint32_t ex = block_exclusive_scan<kSortNT, uint32_t>(s, s_misc + 1, tot);
+            for (int q = 0; q < per; ++q)
+                if (d0 + q < nb) { s_off[d0 + q] = ex; ex += s_cnt[d0 + q]; }
+        }
+        __syncthreads();
+        // ---- stage the records in digit order
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const int p = warp * (kSortIPT * 32) + r * 32 + lane;
+            if (p < tn) {
+                const uint32_t d = pack[r] & 0xFFFFu;
+                const uint32_t lp = s_off[d] + s_whist[warp * nb + d] + (pack[r] >> 16);
+                const uint64_t i = base + p;
+                if (CPT) s_pt[lp] = __ldg(a.pt_in + i);
+                s_val[lp] = a.val_in[i];
+                s_pos[lp] = (uint16_t)p;
+                s_dig[lp] = (dig_t)d;
+            }
+        }
+        // ---- look-back over the chunk's earlier tiles; staging slots for the stitch digit
+        for (int d = threadIdx.x; d < nb; d += kSortNT) {
+            if (d == sdig) {
+                const uint32_t k = s_cnt[d];
+                const uint32_t at = k ? atomicAdd(a.st_count, k) : 0u;
+                s_gbase[d] = (uint64_t)at - s_off[d];
+                continue;
+            }
+            uint32_t excl = 0;
+            if (td.index > 0) {
+                uint64_t t = row - 1;
+                uint32_t spins = 0;
+                for (;;) {
+                    const uint32_t sv = ld_volatile(&a.status[t * kStride + d]);
+                    if ((sv & ~kStMask) == 0) {
+                        if (++spins > kSpinLimit) { raise(a.err, FP_ERR_TIMEOUT); break; }
+                        continue;
+                    }
+                    excl += sv & kStMask;
+                    if ((sv & ~kStMask) == kStFlagInc) break;
+                    --t;
+                }
+                if (!last) atomicExch(&a.status[row * kStride + d], kStFlagInc | (excl + s_cnt[d]));
+            }
+            s_gbase[d] = a.first[(uint64_t)(lo + d) * a.first_stride] + excl - s_off[d];
+        }
+        __syncthreads();
+        // ---- coalesced writes of each digit run
+        for (int q = threadIdx.x; q < tn; q += kSortNT) {
+            const int d = s_dig[q];
+            const uint64_t o = s_gbase[d] + q;
+            if (d == sdig) {
+                if (o >= a.st_cap) { raise(a.err, FP_ERR_CAPACITY); continue; }
+                const uint64_t src = base + s_pos[q];
+                a.st_key[o] = ((uint64_t)a.id_in[src] << a.st_shift) | s_val[q];
+                a.st_src[o] = (uint32_t)src;
+            } else {
+                if (o >= a.n) { raise(a.err, FP_ERR_CAPACITY); continue; }   // inconsistent node table
+                if (CPT) a.pt_out[o] = s_pt[q];
+                if (a.val_out) a.val_out[o] = s_val[q];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- host side
+struct SegScratch {
+    uint32_t* lo;          // [kmax]
+    uint32_t* nb;          // [kmax]
+    SegTile* tiles[2];     // [tiles_max] per variant
+    uint32_t* status[2];   // [rows][256] and [rows][2048]
+    uint32_t* cnt;         // [0..1] tiles per variant, [2] fail, [3..4] tile counters, [5] gated record count
+    uint8_t* inside;       // [node_cap] owner layout: node lies in a chunk's subtree
+    uint64_t kmax, tiles_max, rows, node_cap;
+};
+SegScratch take_seg_scratch(const Workspace& ws, uint64_t n, uint64_t kmax, uint64_t node_cap);
+
+enum SegMode { SEG_LEAF = 0, SEG_OWNER = 1 };
+
+struct SegCall {
+    SegMode mode;
+    const fp_node* nodes; const uint32_t* num_nodes; uint32_t node_cap;
+    const fp_chunk* chunks; const uint32_t* num_chunks; const uint64_t* offsets;
+    const int4* pt_in; int4* pt_out;
+    const uint32_t* val_in; uint32_t* val_out;
+    const uint32_t* id_in;
+    uint64_t n;
+    const uint64_t* first; uint32_t first_stride;
+    // owner layout: staging
+    uint64_t* st_key; uint32_t* st_src; uint32_t* st_count; int st_shift;
+};
+
+// Setup (chunk node ids, digits, tiles), status reset, both pass variants.
+// Afterwards cnt[2] != 0 means a chunk did not fit (the caller's whole-array
+// path must run; it is gated on cnt[5] = n in that case, 0 otherwise).
+cudaError_t seg_scatter(const SegScratch& sc, const SegCall& call, const Workspace& ws, cudaStream_t st);
+
+}  // namespace fp

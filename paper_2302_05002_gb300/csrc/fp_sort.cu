@@ -35,10 +35,12 @@ FP_DEV uint32_t bits_of_count(uint32_t v)
     return b;
 }
 
-__global__ void k_sort_zero(uint32_t* status, uint32_t* counter, uint64_t n, const SortPlan* plan, int slot)
+__global__ void k_sort_zero(uint32_t* status, uint32_t* counter, uint64_t n, const uint32_t* d_n, const SortPlan* plan,
+                            int slot)
 {   // n is the record bound of the pass: zeroing every tile it may use is a superset
     if (slot >= (int)plan->npass) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    if (d_n && *d_n < n) n = *d_n;
     uint64_t ntiles = (n + kSortTile - 1) / kSortTile;
     uint64_t words = ntiles << plan->bits;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;

@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
 }
 
 // zero the status words and the tile counter of one pass slot
-__global__ void k_sort_zero(uint32_t* status, uint32_t* counter, uint64_t n, const SortPlan* plan, int slot);
+__global__ void k_sort_zero(uint32_t* status, uint32_t* counter, uint64_t n, const uint32_t* d_n, const SortPlan* plan,
+                            int slot);
 
 // Plan from per-id weights (ids 0..*d_nw-1, or nw_max when d_nw is null; the id
 // is the key above bit shift0):
@@ -321,7 +322,7 @@ cudaError_t sort_run_pass(const SortScratch& sc, const SortArgs& a0, int slot, i
     a.counter = sc.counter + slot;
     uint64_t ntiles = (a.n + kSortTile - 1) / kSortTile;
     k_sort_zero<<<std::max(1, std::min(num_sms * 4, (int)((ntiles * (1 << kSortMaxBits) + 1023) / 1024))), 256, 0,
-                  st>>>(sc.status, sc.counter + slot, a.n, sc.plan, slot);
+                  st>>>(sc.status, sc.counter + slot, a.n, a.d_n, sc.plan, slot);
     if ((e = cudaGetLastError())) return e;
     return sort_launch<DIG, CPT, CK64, CK32>(a, slot, num_sms, st);
 }

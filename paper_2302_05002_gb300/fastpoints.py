@@ -57,7 +57,7 @@ def load():
         "fp_merge_chunks": (st, [p, u32, u64, p, p, p, p, p, sz, p]),
         "fp_distribute": (st, [p, u64, p, u32, p, p, p, p, p, p, sz, p]),
         "fp_build_chunk_octree": (st, [p, p, u64, p, p, p, p, p, p, p, u32, p, p, p, p, p, sz, p]),
-        "fp_subsample": (st, [p, p, u32, p, p, p, u64, p, p, p, sz, p]),
+        "fp_subsample": (st, [p, p, u32, p, p, p, u64, p, p, p, p, p, p, sz, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -226,9 +226,11 @@ def fp_build_chunk_octree(sorted_pts, perm, cube, chunks, num_chunks, offsets, c
     return nodes, num_nodes, leaf_pts, leaf_perm, owner
 
 
-def fp_subsample(nodes, num_nodes, sorted_pts, perm, owner, prm, stream=None, ws=None, final=None, final_perm=None):
+def fp_subsample(nodes, num_nodes, sorted_pts, perm, owner, chunks, num_chunks, offsets, prm, stream=None, ws=None,
+                 final=None, final_perm=None):
     """nodes must have been allocated with node_capacity_bound(n, prm) rows (the
-    workspace size assumes that node_cap)."""
+    workspace size assumes that node_cap); chunks / num_chunks / offsets are
+    fp_merge_chunks' outputs the points were distributed with."""
     n = sorted_pts.shape[0]
     dev = _dev(sorted_pts)
     if final is None:
@@ -237,7 +239,8 @@ def fp_subsample(nodes, num_nodes, sorted_pts, perm, owner, prm, stream=None, ws
         final_perm = torch.empty(n, dtype=torch.int32, device=dev)
     w, need = _ws("subsample", n, prm, dev, ws)
     _check(load().fp_subsample(_ptr(nodes), _ptr(num_nodes), nodes.shape[0], _ptr(sorted_pts), _ptr(perm),
-                               _ptr(owner), n, _ptr(final), _ptr(final_perm), _ptr(w), w.numel(), _stream(stream)),
+                               _ptr(owner), n, _ptr(chunks), _ptr(num_chunks), _ptr(offsets), _ptr(final),
+                               _ptr(final_perm), _ptr(w), w.numel(), _stream(stream)),
            "fp_subsample")
     return final, final_perm
 
@@ -281,7 +284,8 @@ def build_octree(pts, prm, stream=None):
     dist, perm = fp_distribute(pts, cube, prm.grid_log2, lut, offsets, num_chunks, stream=stream)
     nodes, num_nodes, leaf_pts, leaf_perm, owner = fp_build_chunk_octree(dist, perm, cube, chunks, num_chunks, offsets,
                                                                          counts, prm, stream=stream)
-    final, final_perm = fp_subsample(nodes, num_nodes, dist, perm, owner, prm, stream=stream)
+    final, final_perm = fp_subsample(nodes, num_nodes, dist, perm, owner, chunks, num_chunks, offsets, prm,
+                                     stream=stream)
     return dict(cube=cube, preview=prev, preview_count=prev_n, counts=counts, chunks=chunks, num_chunks=num_chunks,
                 lut=lut, offsets=offsets, dist=dist, perm=perm, nodes=nodes, num_nodes=num_nodes, leaf_pts=leaf_pts,
                 leaf_perm=leaf_perm, owner=owner, final=final, final_perm=final_perm)

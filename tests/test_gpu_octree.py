@@ -60,6 +60,19 @@ def run_case(fp, pts_np, g, s, lmax, T, C):
     assert np.array_equal(got_owner, own_of_index[perm])
     assert np.array_equal(r["final_perm"].cpu().numpy().view(np.uint32), want["final_perm"])
     assert_points_equal(r["final"], want["final_pts"])
+    return want
+
+
+def chunk_subtree_sizes(want):
+    """Nodes in the subtree of every chunk's node (the digits of the chunk in the
+    chunk-by-chunk scatter of the leaf grouping; one more in the owner layout)."""
+    nodes = want["nodes"]
+    sizes = []
+    for c in want["chunks"]:
+        idx = np.flatnonzero((nodes["key"] == c["key"]) & (nodes["level"] == c["level"]))
+        assert len(idx) == 1, "every chunk is a node of the tree"
+        sizes.append(int(nodes["n_desc"][idx[0]]) + 1)
+    return np.array(sizes)
 
 
 CASES = [
@@ -74,6 +87,24 @@ CASES = [
     ("uniform", 1, 8, 7, 7, 15, 100, 10),
     ("uniform", 3, 9, 1, 1, 21, 1, 1),
 ]
+
+# Chunk subtrees of every width the chunk-by-chunk scatter handles: up to 256
+# digits, up to 2048 (with a chunk of many tiles and owners above the chunks),
+# and beyond 2048, where the whole-array sort runs instead.
+WIDTH_CASES = [
+    # kind, n, seed, g, s, lmax, T, C, widest chunk subtree: (lower, upper]
+    ("lidar", 300_000, 12, 5, 5, 14, 60_000, 300, (256, 2047)),
+    ("uniform", 200_000, 11, 4, 4, 9, 200_000, 2_000, (256, 2047)),
+    ("clustered", 200_000, 13, 5, 6, 16, 50_000, 150, (2047, 10 ** 9)),
+    ("uniform", 300_000, 10, 3, 3, 10, 300_000, 200, (2047, 10 ** 9)),
+]
+
+
+@pytest.mark.parametrize("kind,n,seed,g,s,lmax,T,C,widest", WIDTH_CASES)
+def test_octree_chunk_widths(gpu_lib, kind, n, seed, g, s, lmax, T, C, widest):
+    want = run_case(gpu_lib, cloud(kind, n, seed), g, s, lmax, T, C)
+    sizes = chunk_subtree_sizes(want)
+    assert widest[0] < sizes.max() + 1 <= widest[1], sizes.max()
 
 
 @pytest.mark.parametrize("kind,n,seed,g,s,lmax,T,C", CASES)
