@@ -58,7 +58,7 @@ static_assert(sizeof(Piece) == 16, "Piece layout");
 
 struct OpenNode {
     uint64_t key;
-    uint32_t begin, count, minj;
+    uint32_t begin, count;
     uint8_t q, hier, A, pad;
 };
 static_assert(sizeof(OpenNode) == 24, "OpenNode layout");
@@ -156,7 +156,6 @@ __global__ void k_cell_setup(OctCtx c, OpenNode* open0, uint32_t* nopen0)
         o.key = m;
         o.begin = c.cstart[m];
         o.count = cnt;
-        o.minj = c.gj[c.cstart[m]];   // the cell's records are still in index order here
         o.q = (uint8_t)c.g;
         o.hier = hier;
         o.A = (uint8_t)c.g;
@@ -230,11 +229,25 @@ __global__ void k_big_scatter(const OpenNode* open, const uint32_t* nopen, const
     }
 }
 
-__global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uint32_t* cnt_out, uint32_t cap)
+// records of each open node to gather for a sort round; none when *d_skip > skip_min
+// (the records are already sorted deep enough)
+__global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uint32_t* cnt_out, uint32_t cap,
+                              const uint64_t* d_skip, uint64_t skip_min)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
-    cnt_out[i] = i < *nopen0 ? open0[i].count : 0;
+    const bool skip = d_skip && *d_skip > skip_min;
+    cnt_out[i] = i < *nopen0 && !skip ? open0[i].count : 0;
+}
+
+// points in cells of more than kPieceMax points (the records the split tree sorts)
+__global__ void k_big_sum(const uint32_t* counts, uint64_t cells, uint64_t* sum)
+{
+    uint64_t s = 0;
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x)
+        if (counts[m] > (uint32_t)kPieceMax) s += counts[m];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd((unsigned long long*)sum, (unsigned long long)s);
 }
 
 // --------------------------------------------------- big cells: split tree
@@ -262,21 +275,38 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
             }
             lo = a;
         }
+        // smallest index of every child, and of the node (the smallest of those)
+        uint32_t mjd[8];
+        uint32_t pmin = 0xFFFFFFFFu;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const uint32_t cb = __shfl_sync(0xFFFFFFFFu, lo, d);
+            const uint32_t ce = __shfl_sync(0xFFFFFFFFu, lo, d + 1);
+            uint32_t mj = 0xFFFFFFFFu;
+            uint32_t r = cb + lane;
+            for (; r + 96 < ce; r += 128) {   // four independent loads in flight per lane
+                const uint32_t v0 = c.gj[r], v1 = c.gj[r + 32], v2 = c.gj[r + 64], v3 = c.gj[r + 96];
+                mj = min(mj, min(min(v0, v1), min(v2, v3)));
+            }
+            for (; r < ce; r += 32) mj = min(mj, c.gj[r]);
+            for (int off = 16; off > 0; off >>= 1) mj = min(mj, __shfl_xor_sync(0xFFFFFFFFu, mj, off));
+            mjd[d] = mj;
+            pmin = min(pmin, mj);
+        }
+#pragma unroll
         for (int d = 0; d < 8; ++d) {
             uint32_t cb = __shfl_sync(0xFFFFFFFFu, lo, d);
             uint32_t ce = __shfl_sync(0xFFFFFFFFu, lo, d + 1);
             uint32_t cn = ce - cb;
             if (cn == 0) continue;
-            uint32_t mj = 0xFFFFFFFFu;
-            for (uint32_t r = cb + lane; r < ce; r += 32) mj = min(mj, c.gj[r]);
-            for (int off = 16; off > 0; off >>= 1) mj = min(mj, __shfl_xor_sync(0xFFFFFFFFu, mj, off));
+            const uint32_t mj = mjd[d];
             if (lane == 0) {
                 uint64_t key = (o.key << 3) | (uint64_t)d;
                 uint8_t hier;
                 if (o.hier != kInner) hier = o.hier;
                 else hier = (cn <= c.C || q1 == c.lmax) ? (uint8_t)q1 : kInner;
                 // the child's minimum is the parent's minimum: it keeps the parent's first-min level
-                uint8_t A = mj == o.minj ? o.A : (uint8_t)q1;
+                uint8_t A = mj == pmin ? o.A : (uint8_t)q1;
                 if (o.hier == kInner) emit_node(c, key, q1, cn, cb, hier != kInner);
                 uint32_t id = 0;
                 const bool open_child = cn > (uint32_t)kPieceMax && q1 < c.dl;
@@ -288,7 +318,6 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
                     ch.key = key;
                     ch.begin = cb;
                     ch.count = cn;
-                    ch.minj = mj;
                     ch.q = (uint8_t)q1;
                     ch.hier = hier;
                     ch.A = A;
@@ -917,6 +946,8 @@ uint64_t node_capacity_bound(uint64_t n, const fp_params& p) { return oct_layout
 
 struct OctBufs {
     SortScratch sc;
+    SortScratch sc_deep;   // plan, bases and histograms of the deeper cell grouping
+    uint64_t* bigsum;
     uint64_t *t_k1, *t_k2, *t_k3;
     uint32_t *t_j1, *t_j2, *t_j3;
     int4* lt_pt;
@@ -948,6 +979,8 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     OctBufs B;
     const uint64_t N = n ? n : 1;
     B.sc = take_sort_scratch(ws, std::max<uint64_t>(N, std::max(Ly.node_cap, Ly.piece_cap)));
+    B.sc_deep = take_sort_scratch(ws, 1);
+    B.bigsum = ws.take<uint64_t>(1);
     // aliased phase region: grouping temporaries, later the leaf scatter temporaries
     const size_t phase_base = ws.used;
     B.t_k1 = ws.take<uint64_t>(N); B.t_j1 = ws.take<uint32_t>(N);
@@ -1040,9 +1073,27 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
     c.own_code = B.own_code; c.leaf_code = B.leaf_code; c.open_cap = (uint32_t)Ly.open_cap;
     c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
 
-    // 2. group by level-g cell: stable scatter of (key21, j) by cell id
+    // depth of the first split round: the rank of an open node and the digits of
+    // R levels within 32 bits (four sort passes at most)
+    int rank_bits = 1;
+    while ((1ull << rank_bits) < std::min<uint64_t>(Ly.open_cap, Ly.cells)) ++rank_bits;
+    const int R = std::max(1, (32 - rank_bits) / 3);
+    const int r1 = std::min(R, dl - g);
+    // 2. group by level-g cell: stable scatter of (key21, j) by cell id.  When
+    // more than a third of the points lie in cells of more than kPieceMax points,
+    // sorting all records down to level g + r1 instead (two more passes over n)
+    // is cheaper than the first split round's gather, sort and scatter of them,
+    // and that round then has nothing to do.
     {
+        if ((e = cudaMemsetAsync(B.bigsum, 0, sizeof(uint64_t), st))) return e;
+        k_big_sum<<<std::max(1, std::min(ws.num_sms * 4, (int)((Ly.cells + 255) / 256))), 256, 0, st>>>(
+            counts, Ly.cells, B.bigsum);
         if ((e = sort_plan_weights(sc, counts, nullptr, nullptr, Ly.cells, 3 * (kKeyLevels - g), st))) return e;
+        if (r1 > 0 &&
+            (e = sort_plan_points_gated(sc, B.sc_deep, reinterpret_cast<const int4*>(sorted), N, cube,
+                                        (uint32_t)(3 * (kKeyLevels - g - r1)), (uint32_t)(3 * (g + r1)), B.bigsum,
+                                        N / 3, st)))
+            return e;
         SortArgs a{};
         a.b.pt_src = reinterpret_cast<const int4*>(sorted);
         a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.gk;
@@ -1062,14 +1113,11 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         const uint32_t cap = (uint32_t)Ly.open_cap;
         int gw = std::max(1, std::min(ws.num_sms * 16, (int)(((uint64_t)cap * 32 + 255) / 256)));
         const int gr = std::max(1, std::min(ws.num_sms * 8, (int)((N + 255) / 256)));
-        int rank_bits = 1;
-        while ((1ull << rank_bits) < std::min<uint64_t>(Ly.open_cap, Ly.cells)) ++rank_bits;
-        // first round: digits plus rank within 32 bits (four passes at most)
-        const int R = std::max(1, (32 - rank_bits) / 3);
         int cur = 0;
         for (int q = g; q < dl;) {
-            const int r = q == g ? std::min(R, dl - q) : dl - q;
-            k_open_counts<<<(cap + 255) / 256, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, cap);
+            const int r = q == g ? r1 : dl - q;
+            k_open_counts<<<(cap + 255) / 256, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, cap,
+                                                             q == g ? B.bigsum : nullptr, N / 3);
             if ((e = scan_exclusive<uint32_t, uint32_t>(B.bigstart, B.bigstart, cap, nullptr, B.leafw, B.ocount + 3,
                                                         (uint32_t*)nullptr, st)))
                 return e;
@@ -1243,21 +1291,23 @@ __global__ void k_stitch_keys(const uint32_t* mlist, const uint32_t* nmarked, co
 __global__ void k_stitch_gather(const uint32_t* nstitch, const uint32_t* val, const int4* fin, const uint32_t* fperm,
                                 int4* tpt, uint32_t* tperm)
 {
-    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *nstitch) return;
-    tpt[t] = fin[val[t]];
-    tperm[t] = fperm[val[t]];
+    const uint32_t S = *nstitch;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < S; t += gridDim.x * blockDim.x) {
+        tpt[t] = fin[val[t]];
+        tperm[t] = fperm[val[t]];
+    }
 }
 
 __global__ void k_stitch_put(const uint32_t* nstitch, const uint64_t* key, const uint32_t* mlist, const uint32_t* soff,
                              const uint64_t* first, const int4* tpt, const uint32_t* tperm, int4* fin, uint32_t* fperm)
 {
-    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *nstitch) return;
-    uint32_t r = (uint32_t)(key[t] >> 32);
-    uint64_t f = first[mlist[r]] + (t - soff[r]);
-    fin[f] = tpt[t];
-    fperm[f] = tperm[t];
+    const uint32_t S = *nstitch;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < S; t += gridDim.x * blockDim.x) {
+        uint32_t r = (uint32_t)(key[t] >> 32);
+        uint64_t f = first[mlist[r]] + (t - soff[r]);
+        fin[f] = tpt[t];
+        fperm[f] = tperm[t];
+    }
 }
 
 // stitch records staged by the segmented scatter: a node above the chunks keeps
@@ -1423,10 +1473,10 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     b.n = N; b.d_n = cnt + 1; b.err = ws.err;
     for (int slot = 0; slot < kSortMaxPass; ++slot)
         if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, b, slot, ws.num_sms, st))) return e;
-    k_stitch_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(cnt + 1, B.s_val3,
+    k_stitch_gather<<<gN, 256, 0, st>>>(cnt + 1, B.s_val3,
                                                                   reinterpret_cast<const int4*>(final_pts),
                                                                   final_perm, B.s_pt, B.s_perm);
-    k_stitch_put<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(cnt + 1, B.s_key3, mlist, soff, first, B.s_pt,
+    k_stitch_put<<<gN, 256, 0, st>>>(cnt + 1, B.s_key3, mlist, soff, first, B.s_pt,
                                                                B.s_perm, reinterpret_cast<int4*>(final_pts),
                                                                final_perm);
     return cudaGetLastError();

@@ -70,7 +70,8 @@ struct SegSmem {
     static constexpr size_t dig = sizeof(dig_t) * kSortTile;
     static constexpr size_t whist = sizeof(uint16_t) * kSortWarps * (1 << MAXB);
     static constexpr size_t misc = 4 * (1 + kSortWarps + 15);
-    static constexpr size_t total = pt + gbase + val + cnt + off + pos + dig + whist + misc;
+    static constexpr size_t tiles = 4 * 2;   // current and next tile id
+    static constexpr size_t total = pt + gbase + val + cnt + off + pos + dig + whist + misc + tiles;
 };
 
 template <bool CPT, int MAXB>
@@ -89,17 +90,21 @@ __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegAr
     uint16_t* s_pos = reinterpret_cast<uint16_t*>(sp); sp += SM::pos;
     dig_t* s_dig = reinterpret_cast<dig_t*>(sp); sp += SM::dig;
     uint16_t* s_whist = reinterpret_cast<uint16_t*>(sp); sp += SM::whist;
-    uint32_t* s_misc = reinterpret_cast<uint32_t*>(sp);
+    uint32_t* s_misc = reinterpret_cast<uint32_t*>(sp); sp += SM::misc;
+    uint32_t* s_tile = reinterpret_cast<uint32_t*>(sp);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
     constexpr int kStride = 1 << MAXB;
 
-    for (;;) {
-        if (threadIdx.x == 0) s_misc[0] = atomicAdd(a.counter, 1u);
+    // the next tile is claimed while the current one is worked on (tiles only
+    // wait on earlier tiles of their chunk, so a reserved tile cannot deadlock)
+    if (threadIdx.x == 0) s_tile[0] = atomicAdd(a.counter, 1u);
+    for (int it = 0;; ++it) {
         __syncthreads();
-        const uint64_t tile = s_misc[0];
+        const uint64_t tile = s_tile[it & 1];
         if (tile >= ntiles) break;
+        if (threadIdx.x == 0) s_tile[(it + 1) & 1] = atomicAdd(a.counter, 1u);
         const SegTile td = a.tiles[tile];
         const uint32_t lo = a.seg_lo[td.chunk];
         const int nb = (int)a.seg_nb[td.chunk];   // 1 .. 1 << MAXB (checked by the setup)
@@ -113,14 +118,20 @@ __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegAr
         __syncthreads();
         uint16_t* wh = s_whist + warp * nb;
 
-        // ---- digits and in-warp stable ranks
+        // ---- digits (all loads issued first), then in-warp stable ranks
+        uint32_t dg[kSortIPT];
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const int p = warp * (kSortIPT * 32) + r * 32 + lane;
+            dg[r] = p < tn ? a.id_in[base + p] - lo : 0xFFFFFFFFu;
+        }
         uint32_t pack[kSortIPT];
 #pragma unroll
         for (int r = 0; r < kSortIPT; ++r) {
             const int p = warp * (kSortIPT * 32) + r * 32 + lane;
             uint32_t d = 0xFFFFu;
             if (p < tn) {
-                d = a.id_in[base + p] - lo;
+                d = dg[r];
                 if (d >= (uint32_t)sdig) {
                     if (!a.stitch) raise(a.err, FP_ERR_CAPACITY);   // a leaf outside the chunk's subtree
                     d = (uint32_t)(nb - 1);

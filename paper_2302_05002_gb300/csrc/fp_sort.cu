@@ -123,6 +123,49 @@ __global__ void __launch_bounds__(1024) k_plan_finalize(const uint32_t* d_nw, ui
     }
 }
 
+__global__ void k_plan_hist_points(const int4* pts, uint64_t n, const fp_cube* cube, uint32_t shift0,
+                                   uint32_t total_bits, uint32_t* hist, const uint64_t* d_gate, uint64_t gate_min)
+{
+    if (*d_gate <= gate_min) return;
+    const CubeDev cb = load_cube(cube);
+    __shared__ uint32_t sh[kSortMaxPass << kSortMaxBits];
+    uint32_t npass, bits;
+    plan_shape(0, total_bits, npass, bits);
+    const uint32_t mask = (1u << bits) - 1;
+    for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x) sh[q] = 0;
+    __syncthreads();
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int4 q = __ldg(pts + i);
+        const uint64_t k = key21(q.x, q.y, q.z, cb) >> shift0;
+        for (uint32_t p = 0; p < npass; ++p) atomicAdd(&sh[(p << kSortMaxBits) + ((k >> (p * bits)) & mask)], 1u);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x)
+        if (sh[q]) atomicAdd(&hist[q], sh[q]);
+}
+
+__global__ void k_plan_select(const uint64_t* d_gate, uint64_t gate_min, const SortPlan* p2, const uint64_t* b2,
+                              SortPlan* p, uint64_t* b)
+{
+    if (*d_gate <= gate_min) return;
+    for (int i = threadIdx.x; i < (kSortMaxPass << kSortMaxBits); i += blockDim.x) b[i] = b2[i];
+    if (threadIdx.x == 0) *p = *p2;
+}
+
+cudaError_t sort_plan_points_gated(const SortScratch& target, const SortScratch& alt, const int4* pts, uint64_t n,
+                                   const fp_cube* cube, uint32_t shift0, uint32_t total_bits, const uint64_t* d_gate,
+                                   uint64_t gate_min, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(alt.hist, 0, sizeof(uint32_t) * (kSortMaxPass << kSortMaxBits), st);
+    if (e) return e;
+    int grid = (int)std::min<uint64_t>((n + 4095) / 4096 ? (n + 4095) / 4096 : 1, 1024);
+    k_plan_hist_points<<<grid, 1024, 0, st>>>(pts, n, cube, shift0, total_bits, alt.hist, d_gate, gate_min);
+    k_plan_finalize<<<1, 1024, 0, st>>>(nullptr, 0, total_bits, shift0, alt.hist, alt.plan, alt.bases, nullptr);
+    k_plan_select<<<1, 256, 0, st>>>(d_gate, gate_min, alt.plan, alt.bases, target.plan, target.bases);
+    return cudaGetLastError();
+}
+
 size_t sort_scratch_bytes(uint64_t n)
 {
     uint64_t ntiles = (n + kSortTile - 1) / kSortTile;

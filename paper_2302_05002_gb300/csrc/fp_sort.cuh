@@ -87,8 +87,9 @@ struct SortSmem {
     static constexpr size_t gbase = sizeof(uint64_t) * (1 << kSortMaxBits);
     static constexpr size_t cnt = sizeof(uint32_t) * (1 << kSortMaxBits);
     static constexpr size_t off = sizeof(uint32_t) * (1 << kSortMaxBits);
-    static constexpr size_t misc = 4 * (1 + kSortWarps + 15);   // tile id + block-scan scratch
-    static constexpr size_t total = pt + k64 + val + k32 + dig + whist + gbase + cnt + off + misc;
+    static constexpr size_t misc = 4 * (1 + kSortWarps + 15);   // block-scan scratch
+    static constexpr size_t tiles = 4 * 2;                       // current and next tile id
+    static constexpr size_t total = pt + k64 + val + k32 + dig + whist + gbase + cnt + off + misc + tiles;
 };
 
 template <int DIG, bool CPT, bool CK64, bool CK32>
@@ -109,7 +110,8 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
     uint32_t* s_off = reinterpret_cast<uint32_t*>(sp); sp += SM::off;
     dig_t* s_dig = reinterpret_cast<dig_t*>(sp); sp += SM::dig;
     uint16_t* s_whist = reinterpret_cast<uint16_t*>(sp); sp += SM::whist;
-    uint32_t* s_misc = reinterpret_cast<uint32_t*>(sp);   // [0] tile id, [1..] scan scratch
+    uint32_t* s_misc = reinterpret_cast<uint32_t*>(sp); sp += SM::misc;   // [1..] scan scratch
+    uint32_t* s_tile = reinterpret_cast<uint32_t*>(sp);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int bits = (int)plan.bits;
@@ -134,20 +136,24 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
     if (DIG == DIG_CHUNK || DIG == DIG_CELL) cube = load_cube(a.cube);
     const int cell_shift = 3 * (kKeyLevels - a.g);
 
-    for (;;) {
-        if (threadIdx.x == 0) s_misc[0] = atomicAdd(a.counter, 1u);
+    // Tiles are claimed in order through the counter; each CTA claims its next
+    // tile while it works on the current one (a claimed tile only waits on
+    // smaller ones, so holding one in reserve cannot deadlock the look-back).
+    if (threadIdx.x == 0) s_tile[0] = atomicAdd(a.counter, 1u);
+    for (int it = 0;; ++it) {
         // zero the per-warp histograms of this tile
         for (int q = threadIdx.x; q < kSortWarps * nb / 8; q += kSortNT)
             reinterpret_cast<uint4*>(s_whist)[q] = make_uint4(0, 0, 0, 0);
         __syncthreads();
-        const uint64_t tile = s_misc[0];
+        const uint64_t tile = s_tile[it & 1];
         if (tile >= ntiles) break;
+        if (threadIdx.x == 0) s_tile[(it + 1) & 1] = atomicAdd(a.counter, 1u);
         const uint64_t base = tile * kSortTile;
         const int tn = (int)(n - base < (uint64_t)kSortTile ? n - base : (uint64_t)kSortTile);
         uint16_t* wh = s_whist + warp * nb;
 
-        // ---- phase 1: digits and in-warp stable ranks
-        uint32_t pack[kSortIPT];
+        // ---- phase 1: digits (all loads issued first), then in-warp stable ranks
+        uint32_t dg[kSortIPT];
 #pragma unroll
         for (int r = 0; r < kSortIPT; ++r) {
             const int p = warp * (kSortIPT * 32) + r * 32 + lane;
@@ -161,10 +167,20 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
                     d = (uint32_t)(key21(q.x, q.y, q.z, cube) >> shift) & dmask;
                 } else {
                     int4 q = __ldg(in_pt + i);
-                    uint32_t cell = (uint32_t)(key21(q.x, q.y, q.z, cube) >> cell_shift);
-                    d = (__ldg(a.lut + cell) >> shift) & dmask;
+                    d = (uint32_t)(key21(q.x, q.y, q.z, cube) >> cell_shift);   // cell; its chunk below
                 }
             }
+            dg[r] = d;
+        }
+        if (DIG == DIG_CHUNK) {
+#pragma unroll
+            for (int r = 0; r < kSortIPT; ++r)
+                if (warp * (kSortIPT * 32) + r * 32 + lane < tn) dg[r] = (__ldg(a.lut + dg[r]) >> shift) & dmask;
+        }
+        uint32_t pack[kSortIPT];
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const uint32_t d = dg[r];
             uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
             int leader = __ffs(peers) - 1;
             uint32_t old = 0;
@@ -285,6 +301,12 @@ struct SortScratch {
 };
 size_t sort_scratch_bytes(uint64_t n);
 SortScratch take_sort_scratch(const Workspace& ws, uint64_t n);
+
+// When *d_gate > gate_min: replace target's plan by that of a key sort of
+// key21(point) over bits [shift0, shift0 + total_bits) (alt: plan, bases, hist scratch).
+cudaError_t sort_plan_points_gated(const SortScratch& target, const SortScratch& alt, const int4* pts, uint64_t n,
+                                   const fp_cube* cube, uint32_t shift0, uint32_t total_bits, const uint64_t* d_gate,
+                                   uint64_t gate_min, cudaStream_t st);
 
 // plan from weights of ids; then run the passes of the given kind
 cudaError_t sort_plan_weights(const SortScratch& sc, const uint32_t* weights, const uint64_t* offsets,
