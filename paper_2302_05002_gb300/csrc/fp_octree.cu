@@ -37,7 +37,7 @@ namespace fp {
 constexpr int kPieceMax = 1024;                 // largest piece handled in shared memory
 constexpr int kWindow = 1024;                   // pieces starting in one window form a unit
 constexpr int kUnitCap = kPieceMax + kWindow;   // records of one unit
-constexpr int kUnitNT = 256;
+constexpr int kUnitNT = 512;
 constexpr int kUnitWarps = kUnitNT / 32;
 constexpr uint8_t kInner = 0xFF;                // hierarchy still inner at this level
 constexpr uint8_t kEmpty = 0xFE;
@@ -73,6 +73,8 @@ struct OctCtx {   // device pointers of one fp_build_chunk_octree call
     Piece* pieces;
     uint32_t* npieces;
     uint32_t piece_cap;
+    uint32_t* dups;       // pieces of more than kPieceMax points (equal keys to the deepest level)
+    uint32_t* ndups;
     NodeRec* nrec;
     uint32_t* nnode;
     uint32_t node_cap_ws;
@@ -128,6 +130,10 @@ FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, u
     p.dup = count > (uint32_t)kPieceMax ? 1 : 0;
     p.pad = 0;
     c.pieces[id] = p;
+    if (p.dup) {
+        const uint32_t k = atomicAdd(c.ndups, 1u);
+        if (k < c.piece_cap) c.dups[k] = id;
+    }
 }
 
 // ---------------------------------------------------------------- cells
@@ -357,12 +363,15 @@ struct UnitSmem {
     uint32_t np, cnt, p0, dl, nh;
 };
 
+// two units per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
+static_assert(sizeof(UnitSmem) <= 113 * 1024, "UnitSmem must leave room for two CTAs per SM");
+
 // stable LSD pass over the unit's records by 8 key bits at `shift`
 FP_DEV void unit_sort_pass(UnitSmem& S, const uint64_t* kin, const uint16_t* vin, uint64_t* kout, uint16_t* vout,
                            int cnt, int shift)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int per_warp = kUnitCap / kUnitWarps;   // 256 records per warp, 8 rounds
+    constexpr int per_warp = kUnitCap / kUnitWarps;   // records per warp
     for (int q = threadIdx.x; q < kUnitWarps * 256; q += kUnitNT) (&S.whist[0][0])[q] = 0;
     __syncthreads();
     uint32_t pack[per_warp / 32];
@@ -463,14 +472,24 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         // shuffles; larger pieces (and pieces whose node is still inner) go
         // through the shared-memory sort.  A block scan places the large ones.
         {
-            constexpr int per = (kWindow + kUnitNT - 1) / kUnitNT;   // 4
-            uint32_t cn[per];
+            constexpr int per = (kWindow + kUnitNT - 1) / kUnitNT;
+            uint32_t cn[per], po[per];
             uint32_t sum = 0, dmax = 0;
+#pragma unroll
+            for (int q = 0; q < per; ++q) {   // both levels of loads issued before use
+                const int pi = threadIdx.x * per + q;
+                po[q] = pi < np ? piece_order[S.p0 + pi] : 0u;
+            }
+            Piece pr[per];
+#pragma unroll
+            for (int q = 0; q < per; ++q)
+                if ((int)threadIdx.x * per + q < np) pr[q] = c.pieces[po[q]];
+#pragma unroll
             for (int q = 0; q < per; ++q) {
                 int pi = threadIdx.x * per + q;
                 cn[q] = 0;
                 if (pi < np) {
-                    Piece p = c.pieces[piece_order[S.p0 + pi]];
+                    const Piece p = pr[q];
                     S.pbeg[pi] = p.begin;
                     S.pq[pi] = p.q;
                     S.phier[pi] = p.hier;
@@ -540,16 +559,33 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         // records; local index = position in load order
         {
             uint64_t mn = ~0ull, mx = 0;
-            for (int r = threadIdx.x; r < cnt; r += kUnitNT) {
-                int pi = piece_of(S, np, r);
-                uint32_t g = S.pbeg[pi] + (uint32_t)(r - S.psrt[pi]);
-                uint64_t k = c.gk[g];
-                S.key[r] = k;
-                S.j[r] = c.gj[g];
-                S.v[r] = (uint16_t)r;
-                S.piece[r] = (uint16_t)pi;
-                mn = min(mn, k);
-                mx = max(mx, k);
+            constexpr int kPer = kUnitCap / kUnitNT;   // records per thread
+            uint32_t gi[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int r = threadIdx.x + q * kUnitNT;
+                gi[q] = 0;
+                if (r < cnt) {
+                    const int pi = piece_of(S, np, r);
+                    gi[q] = S.pbeg[pi] + (uint32_t)(r - S.psrt[pi]);
+                    S.v[r] = (uint16_t)r;
+                    S.piece[r] = (uint16_t)pi;
+                }
+            }
+            uint64_t kq[kPer];
+            uint32_t jq[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q)   // all loads in flight together
+                if ((int)threadIdx.x + q * kUnitNT < cnt) { kq[q] = c.gk[gi[q]]; jq[q] = c.gj[gi[q]]; }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int r = threadIdx.x + q * kUnitNT;
+                if (r < cnt) {
+                    S.key[r] = kq[q];
+                    S.j[r] = jq[q];
+                    mn = min(mn, kq[q]);
+                    mx = max(mx, kq[q]);
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
                 mn = min(mn, (uint64_t)__shfl_xor_sync(0xFFFFFFFFu, (unsigned long long)mn, o));
@@ -740,10 +776,9 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
 // needed level): only their first record, the smallest index, can be a minimum
 __global__ void k_dup_pieces(OctCtx c)
 {
-    const uint32_t np_all = *c.npieces < c.piece_cap ? *c.npieces : c.piece_cap;
-    for (uint32_t pi = blockIdx.x; pi < np_all; pi += gridDim.x) {
-        const Piece p = c.pieces[pi];
-        if (!p.dup) continue;
+    const uint32_t nd = *c.ndups < c.piece_cap ? *c.ndups : c.piece_cap;
+    for (uint32_t k = blockIdx.x; k < nd; k += gridDim.x) {
+        const Piece p = c.pieces[c.dups[k]];
         const int leafl = p.hier == kInner ? c.lmax : (int)p.hier;
         for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) {
             uint32_t jj = c.gj[p.begin + r];
@@ -817,11 +852,11 @@ __global__ void k_node_write(const NodeRec* nrec, const uint32_t* nnode, const u
 
 __global__ void k_node_fill(const NodeRec* nrec, const uint32_t* nnode, const uint32_t* order,
                             const uint64_t* sorted_start, const uint8_t* sorted_level, fp_node* nodes,
-                            uint32_t node_cap, int lmax)
+                            uint32_t node_cap, uint32_t* ndesc, int lmax)
 {
     const uint32_t M = *nnode;
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M || i >= node_cap) return;
+    if (i >= M) return;
     NodeRec r = nrec[order[i]];
     fp_node o;
     o.key = r.key;
@@ -841,7 +876,8 @@ __global__ void k_node_fill(const NodeRec* nrec, const uint32_t* nnode, const ui
     o.child_mask = 0;
     o.is_leaf = r.is_leaf;
     o.pad = 0;
-    nodes[i] = o;
+    ndesc[i] = o.n_desc;
+    if (i < node_cap) nodes[i] = o;
 }
 
 __global__ void k_node_children(const uint32_t* nnode, const uint64_t* sorted_start, const uint8_t* sorted_level,
@@ -862,10 +898,13 @@ __global__ void k_node_children(const uint32_t* nnode, const uint64_t* sorted_st
 }
 
 // owner and leaf ids of every distributed point; owned counts per node
+// A node deeper than g lies in the subtree of its level-g ancestor, whose ids
+// are consecutive in preorder: the search runs over that subtree only.
 __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp_cube* cube,
                           const uint8_t* own_code, const uint8_t* leaf_code, const uint32_t* idxtab,
-                          const uint64_t* sorted_start, const uint8_t* sorted_level, const uint32_t* nnode,
-                          uint32_t* owner, uint32_t* leafid, uint32_t* n_own, int g, int lmax, uint32_t* err)
+                          const uint64_t* sorted_start, const uint8_t* sorted_level, const uint32_t* ndesc,
+                          const uint32_t* nnode, uint32_t* owner, uint32_t* leafid, uint32_t* n_own, int g, int lmax,
+                          uint32_t* err)
 {
     const CubeDev cb = load_cube(cube);
     const uint32_t M = *nnode;
@@ -879,11 +918,20 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
             uint64_t k21 = key21(p.x, p.y, p.z, cb);
             int ks[2] = {own_code[j], leaf_code[j]};
             uint32_t ids[2];
+            const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + (k21 >> (3 * (kKeyLevels - g)))];
             for (int t = 0; t < 2; ++t) {
                 int L = ks[t];
                 uint64_t k = k21 >> (3 * (kKeyLevels - L));
-                ids[t] = L <= g ? idxtab[((1ull << (3 * L)) - 1) / 7 + k]
-                                : node_lookup(sorted_start, sorted_level, M, k << (3 * (lmax - L)), L);
+                if (L <= g) {
+                    ids[t] = idxtab[((1ull << (3 * L)) - 1) / 7 + k];
+                } else {
+                    ids[t] = kNone;
+                    if (c0 < M) {
+                        const uint32_t r = node_lookup(sorted_start + c0, sorted_level + c0,
+                                                       min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
+                        if (r != kNone) ids[t] = c0 + r;
+                    }
+                }
                 if (L > lmax) ids[t] = kNone;
             }
             if (ids[0] >= M || ids[1] >= M) {   // never for a consistent tree
@@ -957,7 +1005,8 @@ struct OctBufs {
     uint64_t* gk;
     uint32_t* gj;
     Piece* pieces;
-    uint32_t* counters;
+    uint32_t* counters;   // [0] pieces, [1] pieces of equal keys, [3] node records
+    uint32_t* dups;
     uint64_t *pk, *pk2, *pk3;
     uint32_t *pv, *pv2;
     OpenNode* open[2];
@@ -970,6 +1019,7 @@ struct OctBufs {
     uint8_t *own_code, *leaf_code;
     uint32_t* leafid;
     uint32_t* unit_p0;
+    uint32_t* ndesc;
     SegScratch seg;
 };
 
@@ -996,6 +1046,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.gk = ws.take<uint64_t>(N); B.gj = ws.take<uint32_t>(N);
     B.pieces = ws.take<Piece>(Ly.piece_cap);
     B.counters = ws.take<uint32_t>(4);
+    B.dups = ws.take<uint32_t>(Ly.piece_cap);
     B.pk = ws.take<uint64_t>(Ly.piece_cap); B.pk2 = ws.take<uint64_t>(Ly.piece_cap);
     B.pk3 = ws.take<uint64_t>(Ly.piece_cap);
     B.pv = ws.take<uint32_t>(Ly.piece_cap); B.pv2 = ws.take<uint32_t>(Ly.piece_cap);
@@ -1014,6 +1065,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.own_code = ws.take<uint8_t>(N); B.leaf_code = ws.take<uint8_t>(N);
     B.leafid = ws.take<uint32_t>(N);
     B.unit_p0 = ws.take<uint32_t>((N + kWindow - 1) / kWindow + 2);
+    B.ndesc = ws.take<uint32_t>(Ly.node_cap);
     B.seg = take_seg_scratch(ws, N, Ly.cells, 1);
     return B;
 }
@@ -1069,6 +1121,7 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
     OctCtx c;
     c.counts = counts; c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
     c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
+    c.dups = B.dups; c.ndups = B.counters + 1;
     c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
     c.own_code = B.own_code; c.leaf_code = B.leaf_code; c.open_cap = (uint32_t)Ly.open_cap;
     c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
@@ -1190,15 +1243,15 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         if ((e = run_sort<DIG_K64, false, true, false>(sc, b2, ws, st))) return e;
         k_node_write<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, num_nodes, B.idxtab,
                                          B.leafw, g, lmax, ws.err);
-        k_node_fill<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, lmax);
+        k_node_fill<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, B.ndesc, lmax);
         k_node_children<<<gn, 256, 0, st>>>(nnode, B.nk, B.slevel, nodes, node_cap, lmax);
         if ((e = cudaMemsetAsync(B.nown, 0, (size_t)ncap * sizeof(uint32_t), st))) return e;
     }
     // 8. owner and leaf ids per distributed point, owned counts
     {
         int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
-        k_resolve<<<grid, 256, 0, st>>>(sorted, N, cube, B.own_code, B.leaf_code, B.idxtab, B.nk, B.slevel, nnode,
-                                        owner, B.leafid, B.nown, g, lmax, ws.err);
+        k_resolve<<<grid, 256, 0, st>>>(sorted, N, cube, B.own_code, B.leaf_code, B.idxtab, B.nk, B.slevel, B.ndesc,
+                                        nnode, owner, B.leafid, B.nown, g, lmax, ws.err);
         k_write_nown<<<(unsigned)((Ly.node_cap + 255) / 256), 256, 0, st>>>(nodes, nnode, node_cap, B.nown);
     }
     // 9. leaf-grouped points: stable scatter by leaf id, chunk by chunk (every

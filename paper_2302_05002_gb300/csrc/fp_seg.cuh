@@ -198,18 +198,8 @@ __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegAr
             }
             uint32_t excl = 0;
             if (td.index > 0) {
-                uint64_t t = row - 1;
-                uint32_t spins = 0;
-                for (;;) {
-                    const uint32_t sv = ld_volatile(&a.status[t * kStride + d]);
-                    if ((sv & ~kStMask) == 0) {
-                        if (++spins > kSpinLimit) { raise(a.err, FP_ERR_TIMEOUT); break; }
-                        continue;
-                    }
-                    excl += sv & kStMask;
-                    if ((sv & ~kStMask) == kStFlagInc) break;
-                    --t;
-                }
+                excl = look_back([&](int64_t t) { return &a.status[(uint64_t)t * kStride + d]; }, (int64_t)row - 1,
+                                 (int64_t)row - (int64_t)td.index, a.err);
                 if (!last) atomicExch(&a.status[row * kStride + d], kStFlagInc | (excl + s_cnt[d]));
             }
             s_gbase[d] = a.first[(uint64_t)(lo + d) * a.first_stride] + excl - s_off[d];

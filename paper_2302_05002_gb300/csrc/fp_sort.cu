@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(1024) k_plan_finalize(const uint32_t* d_nw, ui
     }
 }
 
+// Digit histograms of every pass, one warp-aggregated shared-memory add per
+// distinct digit of the warp (neighbouring records often share their high
+// digits).  The whole warp runs every round; lanes past n add nothing.
 __global__ void k_plan_hist_points(const int4* pts, uint64_t n, const fp_cube* cube, uint32_t shift0,
                                    uint32_t total_bits, uint32_t* hist, const uint64_t* d_gate, uint64_t gate_min)
 {
@@ -134,11 +137,21 @@ __global__ void k_plan_hist_points(const int4* pts, uint64_t n, const fp_cube* c
     const uint32_t mask = (1u << bits) - 1;
     for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x) sh[q] = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int4 q = __ldg(pts + i);
-        const uint64_t k = key21(q.x, q.y, q.z, cb) >> shift0;
-        for (uint32_t p = 0; p < npass; ++p) atomicAdd(&sh[(p << kSortMaxBits) + ((k >> (p * bits)) & mask)], 1u);
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        uint64_t k = 0;
+        if (i < n) {
+            const int4 q = __ldg(pts + i);
+            k = key21(q.x, q.y, q.z, cb) >> shift0;
+        }
+        for (uint32_t p = 0; p < npass; ++p) {
+            const uint32_t d = i < n ? (uint32_t)((k >> (p * bits)) & mask) : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            if (d != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+                atomicAdd(&sh[(p << kSortMaxBits) + d], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x)

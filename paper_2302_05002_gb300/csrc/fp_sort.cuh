@@ -32,6 +32,41 @@ constexpr uint32_t kStMask = (1u << 30) - 1;
 
 enum DigitSource { DIG_K64 = 0, DIG_K32 = 1, DIG_CHUNK = 2, DIG_CELL = 3 };
 
+// Decoupled look-back of one digit: the sum of the counts of tiles t, t-1, ...
+// down to the nearest one that published an inclusive prefix (tile t_first
+// always does).  The status words of kLookBatch earlier tiles are read at once,
+// so a walk over many tiles that published only their own counts costs one
+// round trip per kLookBatch of them; reading stops at the first word not yet
+// published and resumes there (bounded: FP_ERR_TIMEOUT after kSpinLimit rounds).
+constexpr int kLookBatch = 8;
+template <typename Word>
+FP_DEV uint32_t look_back(Word word, int64_t t, int64_t t_first, uint32_t* err)
+{
+    uint32_t excl = 0, spins = 0;
+    while (t >= t_first) {
+        uint32_t sv[kLookBatch];
+#pragma unroll
+        for (int k = 0; k < kLookBatch; ++k) sv[k] = t - k >= t_first ? ld_volatile(word(t - k)) : 0u;
+        int adv = 0;
+        bool stop = false;
+#pragma unroll
+        for (int k = 0; k < kLookBatch; ++k) {
+            if (stop || t - k < t_first) { stop = true; continue; }
+            const uint32_t f = sv[k] & ~kStMask;
+            if (f == 0) { stop = true; continue; }   // not published yet: read again from here
+            excl += sv[k] & kStMask;
+            if (f == kStFlagInc) return excl;
+            ++adv;
+        }
+        if (adv == 0 && ++spins > kSpinLimit) {
+            raise(err, FP_ERR_TIMEOUT);
+            return excl;
+        }
+        t -= adv;
+    }
+    return excl;
+}
+
 struct SortPlan {
     uint32_t npass;    // passes to run (1..kSortMaxPass)
     uint32_t bits;     // digit width of every pass
@@ -245,18 +280,8 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
         for (int d = threadIdx.x; d < nb; d += kSortNT) {
             uint32_t excl = 0;
             if (tile > 0) {
-                int64_t t = (int64_t)tile - 1;
-                uint32_t spins = 0;
-                while (t >= 0) {
-                    uint32_t s = ld_volatile(&a.status[(uint64_t)t * nb + d]);
-                    if ((s & ~kStMask) == 0) {
-                        if (++spins > kSpinLimit) { raise(a.err, FP_ERR_TIMEOUT); break; }
-                        continue;
-                    }
-                    excl += s & kStMask;
-                    if ((s & ~kStMask) == kStFlagInc) break;
-                    --t;
-                }
+                excl = look_back([&](int64_t t) { return &a.status[(uint64_t)t * nb + d]; }, (int64_t)tile - 1, 0,
+                                 a.err);
                 atomicExch(&a.status[tile * nb + d], kStFlagInc | (excl + s_cnt[d]));
             }
             s_gbase[d] = bases[d] + excl - s_off[d];
