@@ -40,27 +40,36 @@ FP_DEV CubeDev load_cube(const fp_cube* c)
     return d;
 }
 
-// floor(d * 2^21 / S) for 0 <= d < S <= 2^32
-FP_DEV uint32_t cell21(int32_t p, int32_t o, uint64_t S, float scale21)
+// floor(d * 2^l / S) for d = p - o, 0 <= d < S <= 2^32, l <= 21; scale = 2^l / S
+// in fp32.  d fits 32 bits, q * S is a 32 x 32 -> 64-bit product (S = 2^32 is
+// the one value with a high word).
+FP_DEV uint32_t cell_at(int32_t p, int32_t o, uint64_t S, float scale, int l)
 {
-    uint64_t d = (uint64_t)((int64_t)p - (int64_t)o);
-    int32_t q = (int32_t)((float)d * scale21);
+    const uint32_t d = (uint32_t)((int64_t)p - (int64_t)o);
+    int32_t q = (int32_t)((float)d * scale);
     if (q < 0) q = 0;
-    int64_t r = (int64_t)(d << 21) - (int64_t)q * (int64_t)S;
-    if (r < 0) --q;
-    else if (r >= (int64_t)S) ++q;
+    const uint64_t num = (uint64_t)d << l;
+    const uint64_t qs = (uint64_t)(uint32_t)q * (uint32_t)S + ((uint64_t)((uint32_t)q * (uint32_t)(S >> 32)) << 32);
+    if (num < qs) --q;
+    else if (num - qs >= S) ++q;
     return (uint32_t)q;
 }
 
-FP_DEV uint64_t spread3(uint32_t v)   // 21 bits -> bits 0, 3, 6, ...
+FP_DEV uint32_t cell21(int32_t p, int32_t o, uint64_t S, float scale21) { return cell_at(p, o, S, scale21, 21); }
+
+FP_DEV uint32_t spread3_10(uint32_t x)   // 10 bits -> bits 0, 3, ..., 27
 {
-    uint64_t x = v & 0x1FFFFFu;
-    x = (x | (x << 32)) & 0x001F00000000FFFFull;
-    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
-    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
-    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
     return x;
+}
+
+FP_DEV uint64_t spread3(uint32_t v)   // 21 bits -> bits 0, 3, ..., 60
+{
+    return (uint64_t)spread3_10(v) | ((uint64_t)spread3_10(v >> 10) << 30) | ((uint64_t)((v >> 20) & 1u) << 60);
 }
 
 // 63-bit Morton key of the level-21 cell of a point
@@ -70,6 +79,16 @@ FP_DEV uint64_t key21(int32_t x, int32_t y, int32_t z, const CubeDev& c)
     uint32_t cy = cell21(y, c.o[1], c.S, c.scale21);
     uint32_t cz = cell21(z, c.o[2], c.S, c.scale21);
     return (spread3(cx) << 2) | (spread3(cy) << 1) | spread3(cz);
+}
+
+// fp32 2^l / S from the cube's 2^21 / S (scaling by a power of two is exact)
+FP_DEV float scale_at(const CubeDev& c, int l) { return c.scale21 * __int_as_float((127 + l - 21) << 23); }
+
+// Morton key of the level-l cell of a point, l <= 10 (equal to key21 >> 3 (21 - l))
+FP_DEV uint32_t key_small(int32_t x, int32_t y, int32_t z, const CubeDev& c, float scale, int l)
+{
+    return (spread3_10(cell_at(x, c.o[0], c.S, scale, l)) << 2) | (spread3_10(cell_at(y, c.o[1], c.S, scale, l)) << 1) |
+           spread3_10(cell_at(z, c.o[2], c.S, scale, l));
 }
 
 FP_DEV uint64_t key_at(uint64_t k21, int level) { return k21 >> (3 * (kKeyLevels - level)); }

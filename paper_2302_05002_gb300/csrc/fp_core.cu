@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts,
                                                const fp_cube* __restrict__ cube, int g, uint32_t* __restrict__ counts)
 {
     const CubeDev c = load_cube(cube);
-    const int sh = 3 * (kKeyLevels - g);
+    const float sg = scale_at(c, g);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride * 4) {
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts,
             key[u] = kNone;
             if (i < n) {
                 int4 p = ld_point_cs(pts, i);
-                key[u] = (uint32_t)(fp::key21(p.x, p.y, p.z, c) >> sh);
+                key[u] = key_small(p.x, p.y, p.z, c, sg, g);
             }
         }
 #pragma unroll

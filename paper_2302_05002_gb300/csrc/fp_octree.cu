@@ -246,6 +246,12 @@ __global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uin
     cnt_out[i] = i < *nopen0 && !skip ? open0[i].count : 0;
 }
 
+__global__ void k_deep_flag(const uint64_t* bigsum, uint64_t min_sum, uint32_t* flag)
+{
+    flag[0] = *bigsum > min_sum ? 1u : 0u;
+    flag[1] = 1u - flag[0];
+}
+
 // points in cells of more than kPieceMax points (the records the split tree sorts)
 __global__ void k_big_sum(const uint32_t* counts, uint64_t cells, uint64_t* sum)
 {
@@ -996,6 +1002,7 @@ struct OctBufs {
     SortScratch sc;
     SortScratch sc_deep;   // plan, bases and histograms of the deeper cell grouping
     uint64_t* bigsum;
+    uint32_t* deep;        // [0]: the deeper grouping runs, [1]: it does not
     uint64_t *t_k1, *t_k2, *t_k3;
     uint32_t *t_j1, *t_j2, *t_j3;
     int4* lt_pt;
@@ -1031,6 +1038,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.sc = take_sort_scratch(ws, std::max<uint64_t>(N, std::max(Ly.node_cap, Ly.piece_cap)));
     B.sc_deep = take_sort_scratch(ws, 1);
     B.bigsum = ws.take<uint64_t>(1);
+    B.deep = ws.take<uint32_t>(2);
     // aliased phase region: grouping temporaries, later the leaf scatter temporaries
     const size_t phase_base = ws.used;
     B.t_k1 = ws.take<uint64_t>(N); B.t_j1 = ws.take<uint32_t>(N);
@@ -1141,18 +1149,23 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         if ((e = cudaMemsetAsync(B.bigsum, 0, sizeof(uint64_t), st))) return e;
         k_big_sum<<<std::max(1, std::min(ws.num_sms * 4, (int)((Ly.cells + 255) / 256))), 256, 0, st>>>(
             counts, Ly.cells, B.bigsum);
+        k_deep_flag<<<1, 1, 0, st>>>(B.bigsum, r1 > 0 ? N / 3 : ~0ull, B.deep);
         if ((e = sort_plan_weights(sc, counts, nullptr, nullptr, Ly.cells, 3 * (kKeyLevels - g), st))) return e;
-        if (r1 > 0 &&
-            (e = sort_plan_points_gated(sc, B.sc_deep, reinterpret_cast<const int4*>(sorted), N, cube,
-                                        (uint32_t)(3 * (kKeyLevels - g - r1)), (uint32_t)(3 * (g + r1)), B.bigsum,
-                                        N / 3, st)))
+        // deeper grouping: every key computed once into t_k2, read by the first pass
+        if ((e = sort_plan_cells_deep(sc, B.sc_deep, reinterpret_cast<const int4*>(sorted), N, cube, counts, Ly.cells,
+                                      (uint32_t)(3 * (kKeyLevels - g - r1)), (uint32_t)(3 * (g + r1)),
+                                      (uint32_t)(3 * r1), B.t_k2, B.deep, st)))
             return e;
         SortArgs a{};
         a.b.pt_src = reinterpret_cast<const int4*>(sorted);
-        a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.gk;
+        a.b.k64_src = B.t_k2; a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.gk;
         a.b.val_src = nullptr; a.b.val_tmp = B.t_j1; a.b.val_dst = B.gj;
         a.n = N; a.cube = cube; a.g = g; a.err = ws.err;
-        if ((e = sort_run_pass<DIG_CELL, false, true, false>(sc, a, 0, ws.num_sms, st))) return e;
+        SortArgs a_cell = a, a_key = a;
+        a_cell.run_if = B.deep + 1;   // keys from the points in the first pass
+        a_key.run_if = B.deep;        // keys from t_k2
+        if ((e = sort_run_pass<DIG_CELL, false, true, false>(sc, a_cell, 0, ws.num_sms, st))) return e;
+        if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a_key, 0, ws.num_sms, st))) return e;
         for (int slot = 1; slot < kSortMaxPass; ++slot)
             if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a, slot, ws.num_sms, st))) return e;
     }

@@ -96,6 +96,7 @@ struct SortArgs {
     const fp_cube* cube;
     const uint32_t* lut;      // DIG_CHUNK: cell -> chunk
     int g;
+    const uint32_t* run_if;   // nullable: the pass runs only when *run_if != 0
     uint32_t* err;
 };
 
@@ -131,7 +132,7 @@ template <int DIG, bool CPT, bool CK64, bool CK32>
 __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
 {
     const SortPlan plan = *a.plan;
-    if (slot >= (int)plan.npass) return;
+    if (slot >= (int)plan.npass || (a.run_if && !*a.run_if)) return;
     using SM = SortSmem<DIG, CPT, CK64, CK32>;
     using dig_t = typename SM::dig_t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
 
     CubeDev cube;
     if (DIG == DIG_CHUNK || DIG == DIG_CELL) cube = load_cube(a.cube);
-    const int cell_shift = 3 * (kKeyLevels - a.g);
+    const float scale_g = DIG == DIG_CHUNK ? scale_at(cube, a.g) : 0.f;
 
     // Tiles are claimed in order through the counter; each CTA claims its next
     // tile while it works on the current one (a claimed tile only waits on
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
                     d = (uint32_t)(key21(q.x, q.y, q.z, cube) >> shift) & dmask;
                 } else {
                     int4 q = __ldg(in_pt + i);
-                    d = (uint32_t)(key21(q.x, q.y, q.z, cube) >> cell_shift);   // cell; its chunk below
+                    d = key_small(q.x, q.y, q.z, cube, scale_g, a.g);   // cell; its chunk below
                 }
             }
             dg[r] = d;
@@ -327,11 +328,14 @@ struct SortScratch {
 size_t sort_scratch_bytes(uint64_t n);
 SortScratch take_sort_scratch(const Workspace& ws, uint64_t n);
 
-// When *d_gate > gate_min: replace target's plan by that of a key sort of
-// key21(point) over bits [shift0, shift0 + total_bits) (alt: plan, bases, hist scratch).
-cudaError_t sort_plan_points_gated(const SortScratch& target, const SortScratch& alt, const int4* pts, uint64_t n,
-                                   const fp_cube* cube, uint32_t shift0, uint32_t total_bits, const uint64_t* d_gate,
-                                   uint64_t gate_min, cudaStream_t st);
+// When *flag != 0: replace target's plan by that of a key sort of key21(point)
+// over bits [shift0, shift0 + total_bits), whose bits from shift0 + lsh up are
+// the cell bits of the count grid `counts`, and write every point's key21 to
+// keys_out (alt: plan, bases and histogram scratch).
+cudaError_t sort_plan_cells_deep(const SortScratch& target, const SortScratch& alt, const int4* pts, uint64_t n,
+                                 const fp_cube* cube, const uint32_t* counts, uint64_t cells, uint32_t shift0,
+                                 uint32_t total_bits, uint32_t lsh, uint64_t* keys_out, const uint32_t* flag,
+                                 cudaStream_t st);
 
 // plan from weights of ids; then run the passes of the given kind
 cudaError_t sort_plan_weights(const SortScratch& sc, const uint32_t* weights, const uint64_t* offsets,
