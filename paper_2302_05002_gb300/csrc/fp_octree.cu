@@ -52,7 +52,8 @@ static_assert(sizeof(NodeRec) == 24, "NodeRec layout");
 struct Piece {
     uint32_t begin, count;   // record range in the cell-grouped arrays
     uint8_t q, hier, A, dup; // level, leaf level or kInner, first-min level of its minimum, oversized
-    uint32_t pad;
+    uint8_t srt;             // its records are in key order down to this level
+    uint8_t pad[3];
 };
 static_assert(sizeof(Piece) == 16, "Piece layout");
 
@@ -75,6 +76,8 @@ struct OctCtx {   // device pointers of one fp_build_chunk_octree call
     uint32_t piece_cap;
     uint32_t* dups;       // pieces of more than kPieceMax points (equal keys to the deepest level)
     uint32_t* ndups;
+    const uint32_t* deep; // nonzero: the cell grouping sorted every record down to level g + r1
+    int r1;
     NodeRec* nrec;
     uint32_t* nnode;
     uint32_t node_cap_ws;
@@ -117,7 +120,7 @@ FP_DEV void emit_node(const OctCtx& c, uint64_t key, int level, uint32_t count, 
     c.nrec[id] = r;
 }
 
-FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, uint8_t hier, uint8_t A)
+FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, uint8_t hier, uint8_t A, int srt)
 {
     uint32_t id = atomicAdd(c.npieces, 1u);
     if (id >= c.piece_cap) { raise(c.err, FP_ERR_CAPACITY); return; }
@@ -128,7 +131,8 @@ FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, u
     p.hier = hier;
     p.A = A;
     p.dup = count > (uint32_t)kPieceMax ? 1 : 0;
-    p.pad = 0;
+    p.srt = (uint8_t)srt;
+    p.pad[0] = p.pad[1] = p.pad[2] = 0;
     c.pieces[id] = p;
     if (p.dup) {
         const uint32_t k = atomicAdd(c.ndups, 1u);
@@ -154,7 +158,7 @@ __global__ void k_cell_setup(OctCtx c, OpenNode* open0, uint32_t* nopen0)
     }
     c.cell_leaf[m] = hier;
     if (cnt <= (uint32_t)kPieceMax) {
-        emit_piece(c, c.cstart[m], cnt, c.g, hier, (uint8_t)c.g);
+        emit_piece(c, c.cstart[m], cnt, c.g, hier, (uint8_t)c.g, *c.deep ? c.g + c.r1 : c.g);
     } else {
         uint32_t id = atomicAdd(nopen0, 1u);
         if (id >= c.open_cap) { raise(c.err, FP_ERR_CAPACITY); return; }
@@ -267,7 +271,7 @@ __global__ void k_big_sum(const uint32_t* counts, uint64_t cells, uint64_t* sum)
 // key-sorted records, smallest index of every child, hierarchy status, first-min
 // level; children that are still too large stay open, the others become pieces.
 __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, OpenNode* nxt, uint32_t* nnxt,
-                        uint32_t open_cap)
+                        uint32_t open_cap, int srt)
 {
     const uint32_t nc = *ncur;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -336,7 +340,7 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
                     ch.pad = 0;
                     nxt[id] = ch;
                 } else {
-                    emit_piece(c, cb, cn, q1, hier, A);
+                    emit_piece(c, cb, cn, q1, hier, A, srt);
                 }
             }
         }
@@ -348,7 +352,7 @@ struct UnitSmem {
     uint64_t key[kUnitCap];
     uint64_t key2[kUnitCap];
     uint32_t j[kUnitCap];       // by local index
-    uint32_t mt[kUnitCap];      // min-tree over hj: internal nodes 1..P-1 (leaves are hj itself)
+    uint32_t mt[kUnitCap];      // min-tree over hj: internal nodes 1..P-1 (the leaves are hj itself)
     uint16_t v[kUnitCap];       // local index by sorted position
     uint16_t v2[kUnitCap];
     uint16_t piece[kUnitCap];   // piece of a local index
@@ -366,7 +370,7 @@ struct UnitSmem {
     uint32_t scan[64];
     uint64_t wmin[kUnitWarps], wmax[kUnitWarps];
     unsigned long long kmin, kmax;
-    uint32_t np, cnt, p0, dl, nh;
+    uint32_t np, cnt, p0, dl, nh, smin;
 };
 
 // two units per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
             S.p0 = p0;
             S.np = unit_p0[u + 1] - p0;
             S.dl = 0;
+            S.smin = 255;
         }
         __syncthreads();
         const int np = (int)S.np;
@@ -480,7 +485,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         {
             constexpr int per = (kWindow + kUnitNT - 1) / kUnitNT;
             uint32_t cn[per], po[per];
-            uint32_t sum = 0, dmax = 0;
+            uint32_t sum = 0, dmax = 0, smin = 255;
 #pragma unroll
             for (int q = 0; q < per; ++q) {   // both levels of loads issued before use
                 const int pi = threadIdx.x * per + q;
@@ -509,12 +514,15 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
                         uint32_t d = p.hier == kInner ? (uint32_t)c.dl
                                                       : (uint32_t)min(kKeyLevels, c.s + (int)p.hier - 1);
                         dmax = max(dmax, d);
+                        smin = min(smin, (uint32_t)p.srt);
                     }
                 }
                 sum += cn[q];
             }
             dmax = __reduce_max_sync(0xFFFFFFFFu, dmax);
+            smin = __reduce_min_sync(0xFFFFFFFFu, smin);
             if (lane == 0 && dmax) atomicMax(&S.dl, dmax);
+            if (lane == 0 && smin < 255) atomicMin(&S.smin, smin);
             uint32_t tot;
             uint32_t ex = block_exclusive_scan<kUnitNT, uint32_t>(sum, S.scan, tot);
             for (int q = 0; q < per; ++q) {
@@ -610,7 +618,9 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         {
             const int dl_unit = (int)S.dl;
             const int clev = common_level(S.kmin, S.kmax);
-            const int hi_bit = 3 * (kKeyLevels - clev);
+            // records already in key order down to the needed depth (every large
+            // piece sorted that deep; pieces lie in key order) need no sort
+            const int hi_bit = (int)S.smin >= max(dl_unit, clev) ? 0 : 3 * (kKeyLevels - clev);
             const int lo_bit = 3 * (kKeyLevels - max(dl_unit, clev));
             bool in_key = true;
             for (int sh = lo_bit; sh < hi_bit; sh += 8) {
@@ -669,23 +679,35 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         __syncthreads();
         const int nh = (int)S.nh;
         // ---- nearest smaller index on each side of every representative, by a
-        // min-tree over hj (the leaves are hj itself, padded to a power of two):
-        // climb to the first sibling subtree that holds a smaller index, then
-        // descend into it towards the near side.  The level shared with that
-        // neighbour is the deepest level at which the representative is not
-        // its cell's minimum on that side (keys are sorted, so nearer records
-        // share at least as many levels).
-        int P = 1;
+        // min-tree over hj (the leaves are hj itself, padded to a power of two
+        // P >= 32): climb to the first sibling subtree that holds a smaller
+        // index, then descend into it towards the near side.  The five levels
+        // above the leaves are built per warp with shuffles, the rest by one
+        // warp.  The level shared with that neighbour is the deepest level at
+        // which the representative is not its cell's minimum on that side (keys
+        // are sorted, so nearer records share at least as many levels).
+        int P = 32;
         while (P < nh) P <<= 1;
+        for (int b = warp; b < (P >> 5); b += kUnitWarps) {
+            const int i = (b << 5) + lane;
+            uint32_t v = i < nh ? S.hj[i] : 0xFFFFFFFFu;
+#pragma unroll
+            for (int t = 1; t <= 5; ++t) {
+                v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, 1 << (t - 1)));
+                if ((lane & ((1 << t) - 1)) == 0) S.mt[(P + i) >> t] = v;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int m = P >> 6; m >= 1; m >>= 1) {
+                for (int k = m + lane; k < 2 * m; k += 32) S.mt[k] = min(S.mt[2 * k], S.mt[2 * k + 1]);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
         auto tv = [&](int k) -> uint32_t {
             return k >= P ? (k - P < nh ? S.hj[k - P] : 0xFFFFFFFFu) : S.mt[k];
         };
-        for (int k = max(1, P / 2) + (int)threadIdx.x; k < P; k += kUnitNT) S.mt[k] = min(tv(2 * k), tv(2 * k + 1));
-        __syncthreads();
-        for (int m = P / 4; m >= 1; m >>= 1) {
-            for (int k = m + (int)threadIdx.x; k < 2 * m; k += kUnitNT) S.mt[k] = min(S.mt[2 * k], S.mt[2 * k + 1]);
-            __syncthreads();
-        }
         for (int r = threadIdx.x; r < nh; r += kUnitNT) {
             const uint32_t jr = S.hj[r];
             const uint64_t kr = S.key2[r];
@@ -1126,20 +1148,21 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
     if ((e = scan_exclusive<uint32_t, uint32_t>(counts, B.cstart, Ly.cells, nullptr, B.leafw, B.cstart + Ly.cells,
                                                 (uint32_t*)nullptr, st)))
         return e;
-    OctCtx c;
-    c.counts = counts; c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
-    c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
-    c.dups = B.dups; c.ndups = B.counters + 1;
-    c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
-    c.own_code = B.own_code; c.leaf_code = B.leaf_code; c.open_cap = (uint32_t)Ly.open_cap;
-    c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
-
     // depth of the first split round: the rank of an open node and the digits of
     // R levels within 32 bits (four sort passes at most)
     int rank_bits = 1;
     while ((1ull << rank_bits) < std::min<uint64_t>(Ly.open_cap, Ly.cells)) ++rank_bits;
     const int R = std::max(1, (32 - rank_bits) / 3);
     const int r1 = std::min(R, dl - g);
+    OctCtx c;
+    c.counts = counts; c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
+    c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
+    c.dups = B.dups; c.ndups = B.counters + 1;
+    c.deep = B.deep; c.r1 = r1;
+    c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
+    c.own_code = B.own_code; c.leaf_code = B.leaf_code; c.open_cap = (uint32_t)Ly.open_cap;
+    c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
+
     // 2. group by level-g cell: stable scatter of (key21, j) by cell id.  When
     // more than a third of the points lie in cells of more than kPieceMax points,
     // sorting all records down to level g + r1 instead (two more passes over n)
@@ -1202,7 +1225,7 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
             for (int l = q; l < q + r; ++l) {
                 k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
                 k_split<<<gw, 256, 0, st>>>(c, B.open[cur], B.ocount + cur, B.open[1 - cur], B.ocount + (1 - cur),
-                                            cap);
+                                            cap, q + r);
                 cur = 1 - cur;
             }
             q += r;
