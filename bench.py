@@ -28,6 +28,8 @@ WORKLOADS = {
     "uniform-1M": ("uniform", 1_000_000, 1, 7, 7, 15, 100_000, 20_000),
     "uniform-1B": ("uniform", 1_000_000_000, 3, 7, 7, 8, 5_000_000, 50_000),
     "lidar-10M": ("lidar", 10_000_000, 2, 7, 7, 15, 100_000, 20_000),
+    # 256 clouds, sizes log-uniform in [1e4, 2e7], uniform or LiDAR generator per cloud (seed 1000 + i)
+    "batched-256": ("batch", 256, 1000, 7, 7, 15, 100_000, 20_000),
 }
 STAGES = ["bounds_decimate", "count", "merge", "distribute", "octree", "subsample"]
 # algorithmic HBM bytes per point of each stage (mandatory reads + writes), see the design doc
@@ -216,6 +218,196 @@ def run_reference(args, wl, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched workload
+def batch_sizes(count, seed):
+    """Cloud sizes log-uniform in [1e4, 2e7] and generator per cloud, from a seeded generator."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(np.log(1e4), np.log(2e7), count))).astype(np.int64)
+    kinds = np.where(rng.random(count) < 0.5, "uniform", "lidar")
+    return [int(x) for x in sizes], [str(k) for k in kinds]
+
+
+def run_batched(args, wl, rank, world, local):
+    """256 clouds built two ways on the same GPU: the plain calls cloud after
+    cloud on one stream, and fp_build_batched (tuned grid per cloud and lane
+    count) captured into one CUDA graph.  value = all points / batched time."""
+    import torch
+
+    from paper_2302_05002_gb300 import fastpoints as fp
+    from paper_2302_05002_gb300 import tune
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _, count, seed0, g, s, lmax, T, C = wl
+    sizes, kinds = batch_sizes(count, seed0)
+    total = sum(sizes)
+    base = fp.params(grid_log2=g, sub_log2=s, max_level=lmax, decim_modulus=16, chunk_threshold=T, node_capacity=C)
+    host = []
+    for i, (n, kind) in enumerate(zip(sizes, kinds)):
+        h = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+        make_cloud(kind, n, seed0 + i, h)
+        host.append(h)
+    pts = [h.to(dev) for h in host]
+    st = torch.cuda.Stream(dev)
+
+    # plain: the seven calls per cloud, one cloud after another, one stream, configured grid
+    plain_clouds = [(p, base) for p in pts]
+    plain_outs = [fp.cloud_outputs(p, base) for p in pts]
+    plain_descs = fp.batch_descs(plain_clouds, plain_outs)
+    ws_plain = torch.empty(max(fp.batch_workspace_size(plain_descs, count, 1), 1), dtype=torch.uint8, device=dev)
+
+    def run_plain():
+        for i in range(count):
+            fp.plain_calls(plain_descs[i], ws_plain, stream=st)
+
+    # batched: grid per cloud by the tuner, lanes by the tuner, one graph
+    def sample(n):
+        h = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+        make_cloud("lidar", n, 999, h)
+        return h.to(dev)
+
+    tuner = tune.BatchTuner(sample, stream=st)
+    clouds = tuner.tune_params(plain_clouds)
+    outs = [fp.cloud_outputs(p, prm) for p, prm in clouds]
+    descs = fp.batch_descs(clouds, outs)
+    ws_need = max(fp.batch_workspace_size(descs, count, L) for L in (4, 8, 16, 32))
+    ws = torch.empty(max(ws_need, 1), dtype=torch.uint8, device=dev)
+    lanes = tuner.tune_lanes(lambda L: fp.fp_build_batched(descs, count, L, ws, stream=st))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st, capture_error_mode="relaxed"):
+        fp.fp_build_batched(descs, count, lanes, ws, stream=st)
+
+    for _ in range(max(3, args.warmup)):
+        run_plain()
+        graph.replay()
+    torch.cuda.synchronize()
+    assert fp.get_device_error(stream=st) == 0, "device error word set"
+    # every cloud's octree equals the plain build's (the grid changes only the chunking)
+    same = True
+    for o, r in zip(outs, plain_outs):
+        M = int(r["num_nodes"].item())
+        same &= M == int(o["num_nodes"].item()) and torch.equal(o["nodes"][:M], r["nodes"][:M]) and \
+            torch.equal(o["final_perm"], r["final_perm"])
+    assert same, "batched octrees differ from the plain builds"
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        e0.record(st)
+        for _ in range(args.steps):
+            run_plain()
+        e1.record(st)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / args.steps
+
+    launches = count_kernels(lambda: fp.fp_build_batched(descs, count, lanes, ws, stream=st), torch, st)
+    clk = ClockSampler(local)
+    torch.cuda.synchronize()
+    clk.start()
+    with torch.cuda.stream(st):
+        e0.record(st)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = total / (ms * 1e-3) / 1e9
+    plain_value = total / (plain_ms * 1e-3) / 1e9
+
+    # end to end: every cloud copied in from pinned host memory, batch, node tables read back
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(st):
+            for p, h in zip(pts, host):
+                p.copy_(h, non_blocking=True)
+            fp.fp_build_batched(descs, count, lanes, ws, stream=st)
+            nums = torch.stack([o["num_nodes"][0] for o in outs]).cpu()
+            d2h = 0
+            for o, M in zip(outs, nums.tolist()):
+                o["nodes"][:M].cpu()
+                d2h += M * 40 + 4
+            st.synchronize()
+    e2e_ms = (time.perf_counter() - te0) * 1e3 / e2e_steps
+    peak, peak_kind = measured_peaks()
+    alg = sum(ALG_BYTES.values()) * total + FIXED_BYTES["merge"] * count
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = batch_oracle_rate(sizes, kinds, seed0, wl, float(os.environ.get("FP_ORACLE_BUDGET_S", "12")))
+        gs = {}
+        for _, prm in clouds:
+            gs[prm.grid_log2] = gs.get(prm.grid_log2, 0) + 1
+        line = {
+            "metric": "batched octree build throughput (Gpts/s)", "value": value, "unit": "Gpts/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "clouds": count, "points": total, "min_points": min(sizes),
+                       "max_points": max(sizes), "lanes": lanes, "grid_log2_per_cloud": gs,
+                       "chunk_threshold": T, "node_capacity": C, "max_level": lmax, "sub_log2": s,
+                       "plain_ms_per_step": plain_ms, "plain_gpts": plain_value,
+                       "batched_over_plain": value / plain_value, "graph": "one CUDA graph per batch",
+                       "l2": "inputs (%.1f GB) larger than L2" % (16 * total / 1e9)},
+            "e2e": {"value": total / (e2e_ms * 1e-3) / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": 16 * total,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "kernel": "whole batch", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                         "traffic": None, "alg_bytes_per_launch": alg},
+            "clocks": clocks,
+            "gpu_launches": launches * args.steps if launches else None,
+            "cpu_baseline": cpu,
+            "tuner": tuner.log[-8:],
+        }
+        print(json.dumps(line), flush=True)
+
+
+def batch_oracle_rate(sizes, kinds, seed0, wl, budget_s):
+    """Oracle (single thread) over the batch's clouds, smallest first, within the budget."""
+    import oracle
+    import synth
+    _, _, _, g, s, lmax, T, C = wl
+    prm = oracle.params(g, s, lmax, 16, T, C)
+    done, t_all, used = 0, 0.0, 0
+    for i in sorted(range(len(sizes)), key=lambda k: sizes[k]):
+        gen = synth.lidar if kinds[i] == "lidar" else synth.uniform
+        pts = gen(sizes[i], seed0 + i)
+        t0 = time.perf_counter()
+        oracle.build_all(pts, prm)
+        t_all += time.perf_counter() - t0
+        done += sizes[i]
+        used += 1
+        if t_all >= budget_s:
+            break
+    return {"value": done / t_all / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": "the %d smallest clouds of the batch (%d points), %.1f s" % (used, done, t_all)}
+
+
+def run_batched_reference(args, wl, rank):
+    if rank != 0:
+        return
+    sizes, kinds = batch_sizes(wl[1], wl[2])
+    budget = float(os.environ.get("FP_ORACLE_BUDGET_S", "12"))
+    rates = []
+    for _ in range(args.warmup):
+        batch_oracle_rate(sizes, kinds, wl[2], wl, budget / 4)
+    for _ in range(args.steps):
+        cpu = batch_oracle_rate(sizes, kinds, wl[2], wl, budget)
+        rates.append(cpu["value"])
+    v = statistics.median(rates)
+    cpu["value"] = v
+    line = {"impl": "reference", "metric": "batched octree build throughput (Gpts/s)", "value": v,
+            "unit": "Gpts/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "clouds": wl[1], "points": sum(sizes)}, "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,6 +422,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if wl[0] == "batch":
+        if args.impl == "reference":
+            run_batched_reference(args, wl, rank)
+        else:
+            run_batched(args, wl, rank, world, local)
+        return
     if args.impl == "reference":
         run_reference(args, wl, rank)
         return

@@ -232,6 +232,51 @@ fp_status fp_subsample(fp_node* d_nodes, const uint32_t* d_num_nodes, uint32_t n
                        fp_point* d_final, uint32_t* d_final_perm,
                        void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many clouds in one call.  The paper builds one cloud at a time; the batched
+ * form runs every cloud's whole pipeline (the seven calls above, in order) on
+ * one of nlanes library-owned streams forked from and joined back into
+ * `stream`, so small clouds overlap on the device and the whole batch can be
+ * captured into one CUDA graph (lanes are created on the first call with each
+ * device current: make that first call outside a stream capture).  Each
+ * cloud's outputs are bit-identical to the plain calls'.  Clouds go to lanes
+ * largest first, each to the lane with the fewest points so far. */
+typedef struct {
+    const fp_point* d_pts;            /* input, 16-byte aligned */
+    uint64_t n;
+    fp_params prm;
+    fp_cube* d_cube;                  /* outputs, sized as for the plain calls */
+    fp_point* d_preview;
+    uint64_t preview_cap;
+    uint64_t* d_preview_count;
+    uint32_t* d_counts;               /* 8^grid_log2 */
+    fp_chunk* d_chunks;               /* 8^grid_log2 */
+    uint32_t* d_num_chunks;
+    uint32_t* d_lut;                  /* 8^grid_log2 */
+    uint64_t* d_offsets;              /* 8^grid_log2 + 1 */
+    fp_point* d_dist;                 /* n */
+    uint32_t* d_perm;                 /* n */
+    fp_node* d_nodes;                 /* node_cap = fp_node_capacity_bound(n, &prm) */
+    uint32_t node_cap;
+    uint32_t* d_num_nodes;
+    fp_point* d_leaf_pts;             /* n, nullable */
+    uint32_t* d_leaf_perm;            /* n, nullable */
+    uint32_t* d_owner;                /* n */
+    fp_point* d_final;                /* n */
+    uint32_t* d_final_perm;           /* n */
+} fp_cloud_desc;
+
+#define FP_MAX_LANES 32
+
+/* Workspace bytes of fp_build_batched for these clouds on nlanes lanes
+ * (1 <= nlanes <= FP_MAX_LANES): each lane's largest per-cloud need. */
+size_t fp_batch_workspace_size(const fp_cloud_desc* h_clouds, uint32_t ncloud, uint32_t nlanes);
+
+/* Builds every cloud of h_clouds[0..ncloud) (host array of descriptors).  All
+ * descriptors are checked before anything is enqueued; on an error nothing is. */
+fp_status fp_build_batched(const fp_cloud_desc* h_clouds, uint32_t ncloud, uint32_t nlanes,
+                           void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -248,8 +248,8 @@ fp_status fp_build_chunk_octree(const fp_point* d_sorted, const uint32_t* d_perm
 {
     fp_status s = check_params(h_prm);
     if (s != FP_OK) return s;
-    if (!d_cube || !d_chunks || !d_num_chunks || !d_offsets || !d_counts || !d_num_nodes || !d_owner ||
-        (node_cap && !d_nodes) || (n && (!d_sorted || !d_perm)))
+    if (!d_cube || !d_chunks || !d_num_chunks || !d_offsets || !d_counts || !d_num_nodes || (node_cap && !d_nodes) ||
+        (n && (!d_sorted || !d_perm || !d_owner)))
         return FP_ERR_INVALID;
     if (n >= kMaxPoints) return FP_ERR_TOO_LARGE;
     if ((n && !aligned16(d_sorted)) || (d_leaf_pts && !aligned16(d_leaf_pts))) return FP_ERR_ALIGN;

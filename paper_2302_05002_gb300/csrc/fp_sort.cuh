@@ -97,6 +97,7 @@ struct SortArgs {
     const uint32_t* lut;      // DIG_CHUNK: cell -> chunk
     int g;
     const uint32_t* run_if;   // nullable: the pass runs only when *run_if != 0
+    int bulk;                 // 64-bit key layout with 16-byte aligned arrays: tiles arrive by bulk copy
     uint32_t* err;
 };
 
@@ -111,9 +112,19 @@ FP_DEV const T* pick_src(int slot, int npass, const T* src, T* dst, T* tmp)
 // Digits of at most 8 bits keep the per-warp histograms, the digit scan and the
 // look-back small enough for two CTAs per SM; wider digits measured several
 // times slower per pass than two 8-bit passes.
+// The 64-bit key layout (optionally with values) streams each full tile into
+// shared memory with bulk copies; the next tile's copy is issued as soon as the
+// current tile has been staged, so it overlaps the look-back and the writes.
+template <int DIG, bool CPT, bool CK64, bool CK32>
+constexpr bool sort_bulk_layout() { return DIG == DIG_K64 && CK64 && !CPT && !CK32; }
+
 template <int DIG, bool CPT, bool CK64, bool CK32>
 struct SortSmem {
     using dig_t = uint8_t;
+    static constexpr bool BULK = sort_bulk_layout<DIG, CPT, CK64, CK32>();
+    static constexpr size_t raw_k = BULK ? sizeof(uint64_t) * kSortTile : 0;   // first: 16-byte aligned
+    static constexpr size_t raw_v = BULK ? sizeof(uint32_t) * kSortTile : 0;
+    static constexpr size_t bar = BULK ? 16 : 0;
     static constexpr size_t pt = CPT ? sizeof(int4) * kSortTile : 0;
     static constexpr size_t k64 = CK64 ? sizeof(uint64_t) * kSortTile : 0;
     static constexpr size_t val = sizeof(uint32_t) * kSortTile;
@@ -125,7 +136,10 @@ struct SortSmem {
     static constexpr size_t off = sizeof(uint32_t) * (1 << kSortMaxBits);
     static constexpr size_t misc = 4 * (1 + kSortWarps + 15);   // block-scan scratch
     static constexpr size_t tiles = 4 * 2;                       // current and next tile id
-    static constexpr size_t total = pt + k64 + val + k32 + dig + whist + gbase + cnt + off + misc + tiles;
+    static constexpr size_t total =
+        raw_k + raw_v + bar + pt + k64 + val + k32 + dig + whist + gbase + cnt + off + misc + tiles;
+    // two CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
+    static_assert(!BULK || total <= 113 * 1024, "bulk layout must leave room for two CTAs per SM");
 };
 
 template <int DIG, bool CPT, bool CK64, bool CK32>
@@ -137,6 +151,9 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
     using dig_t = typename SM::dig_t;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* sp = smem;
+    uint64_t* raw_k = reinterpret_cast<uint64_t*>(sp); sp += SM::raw_k;
+    uint32_t* raw_v = reinterpret_cast<uint32_t*>(sp); sp += SM::raw_v;
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(sp); sp += SM::bar;
     int4* s_pt = reinterpret_cast<int4*>(sp); sp += SM::pt;
     uint64_t* s_k64 = reinterpret_cast<uint64_t*>(sp); sp += SM::k64;
     uint64_t* s_gbase = reinterpret_cast<uint64_t*>(sp); sp += SM::gbase;
@@ -172,10 +189,26 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
     if (DIG == DIG_CHUNK || DIG == DIG_CELL) cube = load_cube(a.cube);
     const float scale_g = DIG == DIG_CHUNK ? scale_at(cube, a.g) : 0.f;
 
+    const bool use_bulk = SM::BULK && a.bulk;
+    const bool has_val = in_val != nullptr;
+    const uint32_t tx_bytes = (uint32_t)(sizeof(uint64_t) * kSortTile + (has_val ? sizeof(uint32_t) * kSortTile : 0));
+    auto issue = [&](uint64_t t) {   // thread 0: bulk copy of full tile t, if any
+        if (t >= ntiles || (t + 1) * kSortTile > n) return;
+        fence_async_smem();
+        mbar_expect_tx(s_bar, tx_bytes);
+        bulk_g2s(raw_k, in_k64 + t * kSortTile, (uint32_t)(sizeof(uint64_t) * kSortTile), s_bar);
+        if (has_val) bulk_g2s(raw_v, in_val + t * kSortTile, (uint32_t)(sizeof(uint32_t) * kSortTile), s_bar);
+    };
+    uint32_t nwait = 0;   // bulk tiles waited for: the mbarrier's phase parity
+
     // Tiles are claimed in order through the counter; each CTA claims its next
     // tile while it works on the current one (a claimed tile only waits on
     // smaller ones, so holding one in reserve cannot deadlock the look-back).
-    if (threadIdx.x == 0) s_tile[0] = atomicAdd(a.counter, 1u);
+    if (threadIdx.x == 0) {
+        if (use_bulk) mbar_init(s_bar, 1);
+        s_tile[0] = atomicAdd(a.counter, 1u);
+        if (use_bulk) issue(s_tile[0]);
+    }
     for (int it = 0;; ++it) {
         // zero the per-warp histograms of this tile
         for (int q = threadIdx.x; q < kSortWarps * nb / 8; q += kSortNT)
@@ -187,6 +220,23 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
         const uint64_t base = tile * kSortTile;
         const int tn = (int)(n - base < (uint64_t)kSortTile ? n - base : (uint64_t)kSortTile);
         uint16_t* wh = s_whist + warp * nb;
+        if (use_bulk) {
+            if (tn == kSortTile) {   // this tile's bulk copy was issued a tile ago (or in the prologue)
+                const bool ok = mbar_wait(s_bar, nwait & 1);
+                ++nwait;
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) raise(a.err, FP_ERR_TIMEOUT);
+                    mbar_wait(s_bar, (nwait - 1) & 1);   // bounded: let the copy land before leaving
+                    break;
+                }
+            } else {                 // the ragged last tile: plain loads
+                for (int p = threadIdx.x; p < tn; p += kSortNT) {
+                    raw_k[p] = in_k64[base + p];
+                    if (has_val) raw_v[p] = in_val[base + p];
+                }
+                __syncthreads();
+            }
+        }
 
         // ---- phase 1: digits (all loads issued first), then in-warp stable ranks
         uint32_t dg[kSortIPT];
@@ -196,7 +246,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
             uint32_t d = 0xFFFFu;
             if (p < tn) {
                 const uint64_t i = base + p;
-                if (DIG == DIG_K64) d = (uint32_t)(in_k64[i] >> shift) & dmask;
+                if (DIG == DIG_K64) d = (uint32_t)((use_bulk ? raw_k[p] : in_k64[i]) >> shift) & dmask;
                 else if (DIG == DIG_K32) d = (in_k32[i] >> shift) & dmask;
                 else if (DIG == DIG_CELL) {
                     int4 q = __ldg(in_pt + i);
@@ -270,11 +320,15 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
                     if (CPT) s_pt[lp] = q;
                     if (CK64 && DIG == DIG_CELL) s_k64[lp] = key21(q.x, q.y, q.z, cube);
                 }
-                if (CK64 && DIG != DIG_CELL) s_k64[lp] = in_k64[i];
+                if (CK64 && DIG != DIG_CELL) s_k64[lp] = use_bulk ? raw_k[p] : in_k64[i];
                 if (CK32) s_k32[lp] = in_k32[i];
-                s_val[lp] = in_val ? in_val[i] : (uint32_t)i;
+                s_val[lp] = has_val ? (use_bulk ? raw_v[p] : in_val[i]) : (uint32_t)i;
                 s_dig[lp] = (dig_t)d;
             }
+        }
+        if (use_bulk) {   // the raw tile is consumed: start the next one
+            __syncthreads();
+            if (threadIdx.x == 0) issue(s_tile[(it + 1) & 1]);
         }
 
         // ---- look-back: exclusive prefix of every digit over earlier tiles
@@ -375,6 +429,11 @@ cudaError_t sort_run_pass(const SortScratch& sc, const SortArgs& a0, int slot, i
     k_sort_zero<<<std::max(1, std::min(num_sms * 4, (int)((ntiles * (1 << kSortMaxBits) + 1023) / 1024))), 256, 0,
                   st>>>(sc.status, sc.counter + slot, a.n, a.d_n, sc.plan, slot);
     if ((e = cudaGetLastError())) return e;
+    if (sort_bulk_layout<DIG, CPT, CK64, CK32>()) {
+        auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+        a.bulk = al(a.b.k64_src) && al(a.b.k64_tmp) && al(a.b.k64_dst) && al(a.b.val_src) && al(a.b.val_tmp) &&
+                 al(a.b.val_dst);
+    }
     return sort_launch<DIG, CPT, CK64, CK32>(a, slot, num_sms, st);
 }
 

@@ -29,6 +29,18 @@ class fp_params(ctypes.Structure):
                 ("node_capacity", ctypes.c_uint64)]
 
 
+class fp_cloud_desc(ctypes.Structure):
+    _fields_ = [("d_pts", ctypes.c_void_p), ("n", ctypes.c_uint64), ("prm", fp_params), ("d_cube", ctypes.c_void_p),
+                ("d_preview", ctypes.c_void_p), ("preview_cap", ctypes.c_uint64),
+                ("d_preview_count", ctypes.c_void_p), ("d_counts", ctypes.c_void_p), ("d_chunks", ctypes.c_void_p),
+                ("d_num_chunks", ctypes.c_void_p), ("d_lut", ctypes.c_void_p), ("d_offsets", ctypes.c_void_p),
+                ("d_dist", ctypes.c_void_p), ("d_perm", ctypes.c_void_p), ("d_nodes", ctypes.c_void_p),
+                ("node_cap", ctypes.c_uint32), ("d_num_nodes", ctypes.c_void_p), ("d_leaf_pts", ctypes.c_void_p),
+                ("d_leaf_perm", ctypes.c_void_p), ("d_owner", ctypes.c_void_p), ("d_final", ctypes.c_void_p),
+                ("d_final_perm", ctypes.c_void_p)]
+
+
+MAX_LANES = 32
 STAGE = dict(bounds=0, decimate=1, bounds_decimate=2, count=3, merge=4, distribute=5, octree=6, subsample=7)
 ERR_BITS = {1 << 6: "timeout", 1 << 9: "capacity"}
 NODE_BYTES, CHUNK_BYTES, CUBE_BYTES = 40, 16, 32
@@ -58,6 +70,8 @@ def load():
         "fp_distribute": (st, [p, u64, p, u32, p, p, p, p, p, p, sz, p]),
         "fp_build_chunk_octree": (st, [p, p, u64, p, p, p, p, p, p, p, u32, p, p, p, p, p, sz, p]),
         "fp_subsample": (st, [p, p, u32, p, p, p, u64, p, p, p, p, p, p, sz, p]),
+        "fp_batch_workspace_size": (sz, [p, u32, u32]),
+        "fp_build_batched": (st, [p, u32, u32, p, sz, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -243,6 +257,87 @@ def fp_subsample(nodes, num_nodes, sorted_pts, perm, owner, chunks, num_chunks, 
                                _ptr(final_perm), _ptr(w), w.numel(), _stream(stream)),
            "fp_subsample")
     return final, final_perm
+
+
+# ------------------------------------------------------------------ batches
+def cloud_outputs(pts, prm):
+    """Every output of the hot path for one cloud, allocated on the points' device."""
+    n = pts.shape[0]
+    dev = _dev(pts)
+    cells = 1 << (3 * prm.grid_log2)
+    ncap = node_capacity_bound(n, prm)
+    cap = _preview_cap(n, prm.decim_modulus)
+    i32 = dict(dtype=torch.int32, device=dev)
+    return dict(cube=torch.zeros(8, **i32), preview=torch.empty((max(cap, 1), 4), **i32),
+                preview_count=torch.zeros(1, dtype=torch.int64, device=dev), counts=torch.empty(cells, **i32),
+                chunks=torch.empty((cells, 4), **i32), num_chunks=torch.zeros(1, **i32), lut=torch.empty(cells, **i32),
+                offsets=torch.empty(cells + 1, dtype=torch.int64, device=dev), dist=torch.empty((max(n, 1), 4), **i32),
+                perm=torch.empty(max(n, 1), **i32), nodes=torch.zeros((max(ncap, 1), 10), **i32),
+                num_nodes=torch.zeros(1, **i32), leaf_pts=torch.empty((max(n, 1), 4), **i32),
+                leaf_perm=torch.empty(max(n, 1), **i32), owner=torch.empty(max(n, 1), **i32),
+                final=torch.empty((max(n, 1), 4), **i32), final_perm=torch.empty(max(n, 1), **i32),
+                preview_cap=cap, node_cap=ncap)
+
+
+def cloud_desc(pts, prm, out):
+    d = fp_cloud_desc()
+    P = lambda t: t.data_ptr()
+    d.d_pts, d.n, d.prm = P(pts), pts.shape[0], prm
+    d.d_cube, d.d_preview, d.preview_cap, d.d_preview_count = P(out["cube"]), P(out["preview"]), out["preview_cap"], \
+        P(out["preview_count"])
+    d.d_counts, d.d_chunks, d.d_num_chunks = P(out["counts"]), P(out["chunks"]), P(out["num_chunks"])
+    d.d_lut, d.d_offsets, d.d_dist, d.d_perm = P(out["lut"]), P(out["offsets"]), P(out["dist"]), P(out["perm"])
+    d.d_nodes, d.node_cap, d.d_num_nodes = P(out["nodes"]), out["node_cap"], P(out["num_nodes"])
+    d.d_leaf_pts, d.d_leaf_perm, d.d_owner = P(out["leaf_pts"]), P(out["leaf_perm"]), P(out["owner"])
+    d.d_final, d.d_final_perm = P(out["final"]), P(out["final_perm"])
+    return d
+
+
+def plain_calls(d, ws, stream=None):
+    """The seven plain calls of one cloud (descriptor d), in order, on one stream."""
+    L, S, W, Wn = load(), _stream(stream), _ptr(ws), ws.numel()
+    g, T = d.prm.grid_log2, d.prm.chunk_threshold
+    _check(L.fp_bounds_decimate(d.d_pts, d.n, d.d_cube, 0, d.prm.decim_modulus, d.d_preview, d.preview_cap,
+                                d.d_preview_count, W, Wn, S), "fp_bounds_decimate")
+    _check(L.fp_count(d.d_pts, d.n, d.d_cube, g, d.d_counts, 0, W, Wn, S), "fp_count")
+    _check(L.fp_merge_chunks(d.d_counts, g, T, d.d_chunks, d.d_num_chunks, d.d_lut, d.d_offsets, W, Wn, S),
+           "fp_merge_chunks")
+    _check(L.fp_distribute(d.d_pts, d.n, d.d_cube, g, d.d_lut, d.d_offsets, d.d_num_chunks, d.d_dist, d.d_perm, W,
+                           Wn, S), "fp_distribute")
+    _check(L.fp_build_chunk_octree(d.d_dist, d.d_perm, d.n, d.d_cube, d.d_chunks, d.d_num_chunks, d.d_offsets,
+                                   d.d_counts, ctypes.byref(d.prm), d.d_nodes, d.node_cap, d.d_num_nodes,
+                                   d.d_leaf_pts, d.d_leaf_perm, d.d_owner, W, Wn, S), "fp_build_chunk_octree")
+    _check(L.fp_subsample(d.d_nodes, d.d_num_nodes, d.node_cap, d.d_dist, d.d_perm, d.d_owner, d.n, d.d_chunks,
+                          d.d_num_chunks, d.d_offsets, d.d_final, d.d_final_perm, W, Wn, S), "fp_subsample")
+
+
+def batch_descs(clouds, outs):
+    arr = (fp_cloud_desc * max(len(clouds), 1))()
+    for i, ((pts, prm), out) in enumerate(zip(clouds, outs)):
+        arr[i] = cloud_desc(pts, prm, out)
+    return arr
+
+
+def batch_workspace_size(descs, ncloud, nlanes):
+    return int(load().fp_batch_workspace_size(descs, ncloud, nlanes))
+
+
+def fp_build_batched(descs, ncloud, nlanes, ws, stream=None):
+    _check(load().fp_build_batched(descs, ncloud, nlanes, _ptr(ws), ws.numel(), _stream(stream)), "fp_build_batched")
+
+
+def build_batched(clouds, nlanes=8, stream=None, outs=None, ws=None):
+    """clouds: list of (points tensor, fp_params).  Builds all of them with
+    fp_build_batched; returns (list of output dicts, descriptors, workspace)."""
+    if outs is None:
+        outs = [cloud_outputs(p, prm) for p, prm in clouds]
+    descs = batch_descs(clouds, outs)
+    need = batch_workspace_size(descs, len(clouds), nlanes)
+    dev = _dev(clouds[0][0]) if clouds else None
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    fp_build_batched(descs, len(clouds), nlanes, ws, stream=stream)
+    return outs, descs, ws
 
 
 # ------------------------------------------------------------------ decoding

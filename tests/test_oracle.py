@@ -334,3 +334,19 @@ def test_edge_cases():
     r = oracle.build_all(make_pts([[4, 5, 6]]), prm)
     assert len(r["nodes"]) == 1 and int(r["nodes"][0]["is_leaf"]) == 1 and r["final_perm"].tolist() == [0]
     assert [(int(c["level"]), int(c["count"])) for c in r["chunks"]] == [(0, 1)]
+
+
+def test_octree_independent_of_grid_and_threshold():
+    """The hierarchy is defined by C and L_max alone and the LOD by s and the
+    original indices, so the count grid g (g <= s, g <= L_max) and the chunk
+    threshold T (T >= C) only change how the work is cut into chunks: the node
+    table, the leaf grouping and the final layout are the same for all of them.
+    The batched builder's tuner relies on this to pick g and T per cloud."""
+    pts = synth.lidar(6000, 41)
+    ref = None
+    for g, T in [(1, 60), (2, 60), (3, 500), (4, 6000), (5, 100000)]:
+        got = oracle.build_all(pts, oracle.params(g, 5, 12, 16, T, 60))
+        key = (got["nodes"].tobytes(), got["leaf_perm"].tobytes(), got["final_perm"].tobytes())
+        if ref is None:
+            ref = key
+        assert key == ref, (g, T)
