@@ -277,6 +277,33 @@ size_t fp_batch_workspace_size(const fp_cloud_desc* h_clouds, uint32_t ncloud, u
 fp_status fp_build_batched(const fp_cloud_desc* h_clouds, uint32_t ncloud, uint32_t nlanes,
                            void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* ---------------------------------------------------------- out of core
+ * A cloud larger than the device memory it may use (Sec. 4.4: the converter
+ * streams clouds that do not fit, chunk by chunk).  The points stay in pinned
+ * host memory and are streamed in pieces of piece_points (<= 2^23) with
+ * cudaMemcpyAsync on a side stream; every device buffer of the build lies in
+ * d_arena (the budget); h_scratch (pinned, fp_ooc_host_bytes) holds the chunk
+ * groups between passes.  Passes:
+ * bounds + preview (preview_done(user) runs on a CUDA host-callback thread once
+ * the preview and its count are in h_preview / *h_preview_count; nullable),
+ * counts, chunks, then groups of consecutive chunks that fit the arena: each
+ * group's local octrees (levels and nodes below the count grid), the node table
+ * of the whole cloud, owners, and the final layout (points kept above the
+ * chunks merged across groups by a device sort).  The outputs equal the
+ * in-core calls' (cube, preview, node table, final points and perm).
+ * This call blocks the calling host thread until the build is done (it reads
+ * the chunk list between passes); h_* outputs are pinned host memory. */
+size_t fp_ooc_arena_min(uint64_t n, const fp_params* prm, uint64_t piece_points);
+size_t fp_ooc_host_bytes(uint64_t n, const fp_params* prm);
+
+/* group_points: largest chunk group in points (0: as large as the arena allows). */
+fp_status fp_build_ooc(const fp_point* h_pts, uint64_t n, const fp_params* h_prm, uint64_t piece_points,
+                       uint64_t group_points, void* d_arena, size_t arena_bytes, void* h_scratch, size_t scratch_bytes,
+                       fp_cube* h_cube, fp_point* h_preview, uint64_t preview_cap, uint64_t* h_preview_count,
+                       fp_node* h_nodes, uint32_t node_cap, uint32_t* h_num_nodes,
+                       fp_point* h_final, uint32_t* h_final_perm,
+                       void (*preview_done)(void*), void* user, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,42 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
                           const uint32_t* counts, const fp_params& prm, fp_node* nodes, uint32_t node_cap,
                           uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
                           const Workspace& ws, cudaStream_t st);
+// chunk groups of an out-of-core build (fp_ooc.cu)
+struct NodeRec;                      // a node before preorder numbering (fp_octree.cu)
+constexpr size_t kNodeRecBytes = 24;
+struct OctGroup {
+    const uint32_t* rec_counts;      // the group's points per level-g cell (0 outside the group)
+    uint32_t leaf_base;              // position of the group's first point in the whole distributed array
+    uint8_t* own_code;               // per group point: LOD owner level
+    uint8_t* leaf_code;              // per group point: leaf level
+    NodeRec* deep;                   // nodes below level g, appended at *num_deep
+    uint32_t deep_cap;
+    uint32_t* num_deep;
+};
+cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uint64_t n, const fp_cube* cube,
+                               const fp_chunk* chunks, const uint32_t* num_chunks, const uint64_t* offsets,
+                               const uint32_t* counts, const fp_params& prm, fp_node* nodes, uint32_t node_cap,
+                               uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
+                               const OctGroup* grp, const Workspace& ws, cudaStream_t st);
+struct NodeTables {                  // lookups of the id resolution, kept between calls
+    uint32_t* idxtab;                // node id of every (level <= g, key): (8^(g+1) - 1) / 7 + 8 entries
+    uint64_t* starts;                // preorder position -> start key at max_level resolution
+    uint8_t* slevel;                 // preorder position -> level
+    uint32_t* ndesc;                 // preorder position -> subtree size - 1
+    uint32_t* nown;                  // owned points per node (accumulated by the resolution)
+    uint32_t* nnode;                 // node count
+};
+size_t nodes_ws_bytes(const fp_params& p, uint64_t rec_cap);
+uint64_t upper_node_bound(const fp_params& p);
+cudaError_t launch_octree_nodes(const uint32_t* counts, const fp_params& prm, NodeRec* recs, uint64_t rec_cap,
+                                const uint32_t* num_deep, fp_node* nodes, uint32_t node_cap, uint32_t* num_nodes,
+                                const NodeTables& T, const Workspace& ws, cudaStream_t st);
+cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint8_t* own_code,
+                                  const uint8_t* leaf_code, const NodeTables& T, const fp_params& prm,
+                                  uint32_t* owner, const Workspace& ws, cudaStream_t st);
+cudaError_t launch_node_first(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const uint32_t* nown,
+                              uint64_t* first, uint32_t* nm, uint64_t* tiles64, cudaStream_t st);
+
 cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const fp_point* sorted,
                              const uint32_t* perm, const uint32_t* owner, uint64_t n, const fp_chunk* chunks,
                              const uint32_t* num_chunks, const uint64_t* offsets, fp_point* final_pts,

@@ -65,7 +65,9 @@ struct OpenNode {
 static_assert(sizeof(OpenNode) == 24, "OpenNode layout");
 
 struct OctCtx {   // device pointers of one fp_build_chunk_octree call
-    const uint32_t* counts;
+    const uint32_t* counts;    // points per level-g cell: the hierarchy
+    const uint32_t* rcounts;   // records per level-g cell: the points at hand (a chunk group's, or all)
+    uint32_t leaf_base;        // position of the first record in the whole distributed array
     const uint32_t* pyr;
     const uint32_t* cstart;
     uint8_t* cell_leaf;
@@ -113,7 +115,7 @@ FP_DEV void emit_node(const OctCtx& c, uint64_t key, int level, uint32_t count, 
     NodeRec r;
     r.key = key;
     r.count = count;
-    r.leaf_first = leaf_first;
+    r.leaf_first = leaf_first + c.leaf_base;
     r.level = (uint8_t)level;
     r.is_leaf = leaf ? 1 : 0;
     for (int q = 0; q < 6; ++q) r.pad[q] = 0;
@@ -149,7 +151,7 @@ __global__ void k_cell_setup(OctCtx c, OpenNode* open0, uint32_t* nopen0)
     uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t cells = 1ull << (3 * c.g);
     if (m >= cells) return;
-    uint32_t cnt = c.counts[m];
+    uint32_t cnt = c.rcounts[m];
     if (cnt == 0) { c.cell_leaf[m] = kEmpty; return; }
     uint8_t hier = kInner;
     for (int l = 0; l <= c.g; ++l) {
@@ -967,7 +969,7 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
                 ids[0] = ids[1] = 0;
             }
             owner[j] = ids[0];
-            leafid[j] = ids[1];
+            if (leafid) leafid[j] = ids[1];
             oid = ids[0];
         }
         uint32_t peers = __match_any_sync(0xFFFFFFFFu, oid);
@@ -1117,17 +1119,80 @@ static cudaError_t run_sort(const SortScratch& sc, SortArgs a, const Workspace& 
     return cudaSuccess;
 }
 
+// node records -> fp_node table in preorder, the level-g id table, sorted starts,
+// levels and subtree sizes (the lookups of the id resolution)
+struct NodeSortBufs {
+    uint64_t *nk, *nk2, *nk3, *nk4;
+    uint32_t *nl, *nv2, *nv3;
+    uint8_t* slevel;
+    uint32_t *idxtab, *leafw, *ndesc;
+};
+
+static cudaError_t node_table(const SortScratch& sc, const NodeRec* nrec, uint32_t* nnode, uint32_t ncap,
+                              const NodeSortBufs& B, fp_node* nodes, uint32_t node_cap, uint32_t* num_nodes, int g,
+                              int lmax, const Workspace& ws, cudaStream_t st)
+{
+    cudaError_t e;
+    const unsigned gn = (ncap + 255) / 256;
+    k_clamp<<<1, 1, 0, st>>>(nnode, ncap);
+    k_node_keys<<<gn, 256, 0, st>>>(nrec, nnode, B.nk, B.nl, lmax);
+    k_level_keys<<<gn, 256, 0, st>>>(B.nl, nnode, B.nk3);
+    if ((e = sort_plan_keys(sc, B.nk3, ncap, nnode, 0, 5, st))) return e;
+    SortArgs a{};
+    a.b.k64_src = B.nk3; a.b.k64_tmp = B.nk2; a.b.k64_dst = B.nk4;
+    a.b.val_src = nullptr; a.b.val_tmp = B.nv2; a.b.val_dst = B.nv3;
+    a.n = ncap; a.d_n = nnode; a.err = ws.err;
+    if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
+    k_gather_u64<<<gn, 256, 0, st>>>(B.nk, B.nv3, nnode, B.nk3);
+    if ((e = sort_plan_keys(sc, B.nk3, ncap, nnode, 0, (uint32_t)std::max(1, 3 * lmax), st))) return e;
+    SortArgs b2{};
+    b2.b.k64_src = B.nk3; b2.b.k64_tmp = B.nk2; b2.b.k64_dst = B.nk;   // nk <- sorted starts
+    b2.b.val_src = B.nv3; b2.b.val_tmp = B.nv2; b2.b.val_dst = B.nl;   // nl <- record of preorder position
+    b2.n = ncap; b2.d_n = nnode; b2.err = ws.err;
+    if ((e = run_sort<DIG_K64, false, true, false>(sc, b2, ws, st))) return e;
+    k_node_write<<<gn, 256, 0, st>>>(nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, num_nodes, B.idxtab, B.leafw,
+                                     g, lmax, ws.err);
+    k_node_fill<<<gn, 256, 0, st>>>(nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, B.ndesc, lmax);
+    k_node_children<<<gn, 256, 0, st>>>(nnode, B.nk, B.slevel, nodes, node_cap, lmax);
+    return cudaGetLastError();
+}
+
+// append the node records of a chunk group to the caller's array
+__global__ void k_append_nodes(const NodeRec* rec, const uint32_t* nrec, uint32_t cap_ws, NodeRec* out,
+                               uint32_t* nout, uint32_t out_cap, uint32_t* err)
+{
+    const uint32_t M = min(*nrec, cap_ws), base = *nout;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        if (base + i < out_cap) out[base + i] = rec[i];
+        else raise(err, FP_ERR_CAPACITY);
+    }
+}
+
+__global__ void k_add_u32(uint32_t* a, const uint32_t* b, uint32_t cap_b) { *a += min(*b, cap_b); }
+
 cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t n, const fp_cube* cube,
                           const fp_chunk* chunks, const uint32_t* num_chunks, const uint64_t* offsets,
                           const uint32_t* counts, const fp_params& prm, fp_node* nodes, uint32_t node_cap,
                           uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
                           const Workspace& ws, cudaStream_t st)
 {
+    return launch_octree_impl(sorted, perm, n, cube, chunks, num_chunks, offsets, counts, prm, nodes, node_cap,
+                              num_nodes, leaf_pts, leaf_perm, owner, nullptr, ws, st);
+}
+
+cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uint64_t n, const fp_cube* cube,
+                               const fp_chunk* chunks, const uint32_t* num_chunks, const uint64_t* offsets,
+                               const uint32_t* counts, const fp_params& prm, fp_node* nodes, uint32_t node_cap,
+                               uint32_t* num_nodes, fp_point* leaf_pts, uint32_t* leaf_perm, uint32_t* owner,
+                               const OctGroup* grp, const Workspace& ws, cudaStream_t st)
+{
     cudaError_t e;
     if (n == 0) {
-        k_set_u32<<<1, 1, 0, st>>>(num_nodes, 0);
+        if (!grp) k_set_u32<<<1, 1, 0, st>>>(num_nodes, 0);
         return cudaGetLastError();
     }
+    const uint32_t* rcounts = grp ? grp->rec_counts : counts;
     const int g = (int)prm.grid_log2, s = (int)prm.sub_log2, lmax = (int)prm.max_level;
     const int dl = std::min(kKeyLevels, std::max(s + lmax - 1, g + 1));
     const OctLayout Ly = oct_layout(n, prm);
@@ -1145,7 +1210,7 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         const uint32_t* child = l + 1 == g ? counts : B.pyr + ((1ull << (3 * (l + 1))) - 1) / 7;
         k_pyr_level<<<(unsigned)((np_ + 255) / 256), 256, 0, st>>>(child, B.pyr + (np_ - 1) / 7, np_);
     }
-    if ((e = scan_exclusive<uint32_t, uint32_t>(counts, B.cstart, Ly.cells, nullptr, B.leafw, B.cstart + Ly.cells,
+    if ((e = scan_exclusive<uint32_t, uint32_t>(rcounts, B.cstart, Ly.cells, nullptr, B.leafw, B.cstart + Ly.cells,
                                                 (uint32_t*)nullptr, st)))
         return e;
     // depth of the first split round: the rank of an open node and the digits of
@@ -1155,12 +1220,15 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
     const int R = std::max(1, (32 - rank_bits) / 3);
     const int r1 = std::min(R, dl - g);
     OctCtx c;
-    c.counts = counts; c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
+    c.counts = counts; c.rcounts = rcounts; c.leaf_base = grp ? grp->leaf_base : 0u;
+    c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
     c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
     c.dups = B.dups; c.ndups = B.counters + 1;
     c.deep = B.deep; c.r1 = r1;
     c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
-    c.own_code = B.own_code; c.leaf_code = B.leaf_code; c.open_cap = (uint32_t)Ly.open_cap;
+    c.own_code = grp ? grp->own_code : B.own_code;
+    c.leaf_code = grp ? grp->leaf_code : B.leaf_code;
+    c.open_cap = (uint32_t)Ly.open_cap;
     c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
 
     // 2. group by level-g cell: stable scatter of (key21, j) by cell id.  When
@@ -1171,11 +1239,11 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
     {
         if ((e = cudaMemsetAsync(B.bigsum, 0, sizeof(uint64_t), st))) return e;
         k_big_sum<<<std::max(1, std::min(ws.num_sms * 4, (int)((Ly.cells + 255) / 256))), 256, 0, st>>>(
-            counts, Ly.cells, B.bigsum);
+            rcounts, Ly.cells, B.bigsum);
         k_deep_flag<<<1, 1, 0, st>>>(B.bigsum, r1 > 0 ? N / 3 : ~0ull, B.deep);
-        if ((e = sort_plan_weights(sc, counts, nullptr, nullptr, Ly.cells, 3 * (kKeyLevels - g), st))) return e;
+        if ((e = sort_plan_weights(sc, rcounts, nullptr, nullptr, Ly.cells, 3 * (kKeyLevels - g), st))) return e;
         // deeper grouping: every key computed once into t_k2, read by the first pass
-        if ((e = sort_plan_cells_deep(sc, B.sc_deep, reinterpret_cast<const int4*>(sorted), N, cube, counts, Ly.cells,
+        if ((e = sort_plan_cells_deep(sc, B.sc_deep, reinterpret_cast<const int4*>(sorted), N, cube, rcounts, Ly.cells,
                                       (uint32_t)(3 * (kKeyLevels - g - r1)), (uint32_t)(3 * (g + r1)),
                                       (uint32_t)(3 * r1), B.t_k2, B.deep, st)))
             return e;
@@ -1231,8 +1299,8 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
             q += r;
         }
     }
-    // 5. nodes at levels <= g
-    {
+    // 5. nodes at levels <= g (a chunk group leaves them to the whole-cloud node table)
+    if (!grp) {
         uint64_t total = (Ly.cells * 8 - 1) / 7;
         k_nodes_upper<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c);
     }
@@ -1257,31 +1325,19 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
         k_units<<<grid, kUnitNT, smem, st>>>(c, B.unit_p0, B.pv, N);
         k_dup_pieces<<<ws.num_sms, 256, 0, st>>>(c);
     }
+    if (grp) {   // a chunk group: its nodes below level g are appended to the caller's list
+        const unsigned ga = (unsigned)std::max(1, std::min(ws.num_sms * 8, (int)((Ly.node_cap + 255) / 256)));
+        k_append_nodes<<<ga, 256, 0, st>>>(B.nrec, nnode, (uint32_t)Ly.node_cap, grp->deep, grp->num_deep,
+                                           grp->deep_cap, ws.err);
+        k_add_u32<<<1, 1, 0, st>>>(grp->num_deep, nnode, (uint32_t)Ly.node_cap);
+        return cudaGetLastError();
+    }
     // 7. node table in preorder: stable sort by level, then by start at max_level resolution
     {
-        const uint32_t ncap = (uint32_t)Ly.node_cap;
-        const unsigned gn = (ncap + 255) / 256;
-        k_clamp<<<1, 1, 0, st>>>(nnode, ncap);
-        k_node_keys<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nk, B.nl, lmax);
-        k_level_keys<<<gn, 256, 0, st>>>(B.nl, nnode, B.nk3);
-        if ((e = sort_plan_keys(sc, B.nk3, ncap, nnode, 0, 5, st))) return e;
-        SortArgs a{};
-        a.b.k64_src = B.nk3; a.b.k64_tmp = B.nk2; a.b.k64_dst = B.nk4;
-        a.b.val_src = nullptr; a.b.val_tmp = B.nv2; a.b.val_dst = B.nv3;
-        a.n = ncap; a.d_n = nnode; a.err = ws.err;
-        if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
-        k_gather_u64<<<gn, 256, 0, st>>>(B.nk, B.nv3, nnode, B.nk3);
-        if ((e = sort_plan_keys(sc, B.nk3, ncap, nnode, 0, (uint32_t)std::max(1, 3 * lmax), st))) return e;
-        SortArgs b2{};
-        b2.b.k64_src = B.nk3; b2.b.k64_tmp = B.nk2; b2.b.k64_dst = B.nk;   // nk <- sorted starts
-        b2.b.val_src = B.nv3; b2.b.val_tmp = B.nv2; b2.b.val_dst = B.nl;   // nl <- record of preorder position
-        b2.n = ncap; b2.d_n = nnode; b2.err = ws.err;
-        if ((e = run_sort<DIG_K64, false, true, false>(sc, b2, ws, st))) return e;
-        k_node_write<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, num_nodes, B.idxtab,
-                                         B.leafw, g, lmax, ws.err);
-        k_node_fill<<<gn, 256, 0, st>>>(B.nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, B.ndesc, lmax);
-        k_node_children<<<gn, 256, 0, st>>>(nnode, B.nk, B.slevel, nodes, node_cap, lmax);
-        if ((e = cudaMemsetAsync(B.nown, 0, (size_t)ncap * sizeof(uint32_t), st))) return e;
+        NodeSortBufs nb{B.nk, B.nk2, B.nk3, B.nk4, B.nl, B.nv2, B.nv3, B.slevel, B.idxtab, B.leafw, B.ndesc};
+        if ((e = node_table(sc, B.nrec, nnode, (uint32_t)Ly.node_cap, nb, nodes, node_cap, num_nodes, g, lmax, ws, st)))
+            return e;
+        if ((e = cudaMemsetAsync(B.nown, 0, (size_t)Ly.node_cap * sizeof(uint32_t), st))) return e;
     }
     // 8. owner and leaf ids per distributed point, owned counts
     {
@@ -1320,6 +1376,82 @@ cudaError_t launch_octree(const fp_point* sorted, const uint32_t* perm, uint64_t
     }
     return cudaGetLastError();
 }
+
+// ------------------------------------------- whole-cloud tables (chunk groups)
+__global__ void k_copy_u32(uint32_t* dst, const uint32_t* src) { *dst = *src; }
+
+struct NodesBufs {
+    SortScratch sc;
+    uint32_t *pyr, *cstart;
+    NodeSortBufs nb;
+};
+
+static NodesBufs nodes_carve(const Workspace& ws, const fp_params& p, uint64_t rec_cap)
+{
+    NodesBufs B;
+    const uint64_t cells = 1ull << (3 * p.grid_log2);
+    const uint64_t R = rec_cap ? rec_cap : 1;
+    B.sc = take_sort_scratch(ws, R);
+    B.pyr = ws.take<uint32_t>((cells - 1) / 7 ? (cells - 1) / 7 : 1);
+    B.cstart = ws.take<uint32_t>(cells + 1);
+    B.nb.nk2 = ws.take<uint64_t>(R); B.nb.nk3 = ws.take<uint64_t>(R); B.nb.nk4 = ws.take<uint64_t>(R);
+    B.nb.nl = ws.take<uint32_t>(R); B.nb.nv2 = ws.take<uint32_t>(R); B.nb.nv3 = ws.take<uint32_t>(R);
+    B.nb.leafw = ws.take<uint32_t>(std::max<uint64_t>(R, kScanMaxTiles));
+    return B;
+}
+
+size_t nodes_ws_bytes(const fp_params& p, uint64_t rec_cap)
+{
+    Workspace dry;
+    nodes_carve(dry, p, rec_cap);
+    return dry.used;
+}
+
+uint64_t upper_node_bound(const fp_params& p) { return ((1ull << (3 * p.grid_log2)) * 8 - 1) / 7; }
+
+cudaError_t launch_octree_nodes(const uint32_t* counts, const fp_params& prm, NodeRec* recs, uint64_t rec_cap,
+                                const uint32_t* num_deep, fp_node* nodes, uint32_t node_cap, uint32_t* num_nodes,
+                                const NodeTables& T, const Workspace& ws, cudaStream_t st)
+{
+    cudaError_t e;
+    const int g = (int)prm.grid_log2, lmax = (int)prm.max_level;
+    const uint64_t cells = 1ull << (3 * g);
+    const NodesBufs B = nodes_carve(ws, prm, rec_cap);
+    for (int l = g - 1; l >= 0; --l) {
+        uint64_t np_ = 1ull << (3 * l);
+        const uint32_t* child = l + 1 == g ? counts : B.pyr + ((1ull << (3 * (l + 1))) - 1) / 7;
+        k_pyr_level<<<(unsigned)((np_ + 255) / 256), 256, 0, st>>>(child, B.pyr + (np_ - 1) / 7, np_);
+    }
+    if ((e = scan_exclusive<uint32_t, uint32_t>(counts, B.cstart, cells, nullptr, B.nb.leafw, B.cstart + cells,
+                                                (uint32_t*)nullptr, st)))
+        return e;
+    k_copy_u32<<<1, 1, 0, st>>>(T.nnode, num_deep);
+    OctCtx c{};
+    c.counts = counts; c.rcounts = counts; c.leaf_base = 0;
+    c.pyr = B.pyr; c.cstart = B.cstart; c.nrec = recs; c.nnode = T.nnode; c.node_cap_ws = (uint32_t)rec_cap;
+    c.g = g; c.s = (int)prm.sub_log2; c.lmax = lmax; c.C = prm.node_capacity; c.err = ws.err;
+    k_nodes_upper<<<(unsigned)((upper_node_bound(prm) + 255) / 256), 256, 0, st>>>(c);
+    NodeSortBufs nb = B.nb;
+    nb.nk = T.starts; nb.slevel = T.slevel; nb.idxtab = T.idxtab; nb.ndesc = T.ndesc;
+    if ((e = node_table(B.sc, recs, T.nnode, (uint32_t)rec_cap, nb, nodes, node_cap, num_nodes, g, lmax, ws, st)))
+        return e;
+    return cudaMemsetAsync(T.nown, 0, rec_cap * sizeof(uint32_t), st);
+}
+
+cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint8_t* own_code,
+                                  const uint8_t* leaf_code, const NodeTables& T, const fp_params& prm,
+                                  uint32_t* owner, const Workspace& ws, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ws.num_sms * 16);
+    k_resolve<<<grid, 256, 0, st>>>(pts, n, cube, own_code, leaf_code, T.idxtab, T.starts, T.slevel, T.ndesc, T.nnode,
+                                    owner, nullptr, T.nown, (int)prm.grid_log2, (int)prm.max_level, ws.err);
+    return cudaGetLastError();
+}
+
+// n_own of every node from the owned counts, then first = exclusive prefix of n_own
+cudaError_t launch_node_first(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const uint32_t* nown,
+                              uint64_t* first, uint32_t* nm, uint64_t* tiles64, cudaStream_t st);
 
 // ------------------------------------------------------------ subsample
 __global__ void k_nown_in(const fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, uint32_t* nown)
@@ -1423,6 +1555,19 @@ __global__ void k_stitch_place(const uint32_t* nstaged, const uint64_t* key, con
         fin[f] = __ldg(pts + j);
         fperm[f] = perm[j];
     }
+}
+
+cudaError_t launch_node_first(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const uint32_t* nown,
+                              uint64_t* first, uint32_t* nm, uint64_t* tiles64, cudaStream_t st)
+{
+    const unsigned gM = (node_cap + 255) / 256;
+    k_write_nown<<<gM, 256, 0, st>>>(nodes, num_nodes, node_cap, nown);
+    k_clamp_copy<<<1, 1, 0, st>>>(num_nodes, node_cap, nm);
+    cudaError_t e = scan_exclusive<uint32_t, uint64_t>(nown, first, node_cap, nm, tiles64, (uint64_t*)nullptr,
+                                                       (uint64_t*)nullptr, st);
+    if (e) return e;
+    k_first_out<<<gM, 256, 0, st>>>(nodes, num_nodes, node_cap, first);
+    return cudaGetLastError();
 }
 
 static const uint64_t kMaxScanNodes = (uint64_t)kScanTile * kScanMaxTiles;

@@ -1,0 +1,675 @@
+// fp_ooc.cu -- fp_build_ooc: the out-of-core build of one cloud held in pinned
+// host memory, every device buffer inside a caller-given arena (the budget).
+//
+// The level-of-detail owner and the leaf of a point depend only on the points
+// of its level-g cell and on the count pyramid above it (owner levels at or
+// above g collapse to the root since g <= s), and chunks are unions of whole
+// level-g cells.  So the cloud is cut into groups of consecutive chunks that
+// fit the arena; every group's local octrees run on the device against the
+// whole cloud's count grid, the node table of the whole cloud is assembled
+// from the count pyramid and the groups' deeper nodes, and the final layout is
+// written group by group -- points kept by nodes above the chunks (count > T,
+// level < g) are staged and merged across groups by one device sort.
+//
+// Passes over the host points (pieces of piece_points, double-buffered copies
+// on a side stream): bounds + preview, counts, then one per group.  The pinned
+// host scratch is the out-of-core store between passes: the distributed points
+// and original indices of every group, the two levels and the owner of every
+// point, and the staged records.
+#include <algorithm>
+#include <vector>
+#include "fp_sort.cuh"
+
+namespace fp {
+
+fp_status check_params(const fp_params* p);
+size_t bounds_ws_bytes(uint64_t n, int num_sms);
+fp_status make_workspace(void* base, size_t bytes, size_t need, Workspace& ws);
+size_t merge_ws_bytes(int g);
+
+namespace {
+
+constexpr uint64_t kMaxPiece = 1ull << 23;   // the flag scan covers 8M entries
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_cube_fold(fp_cube* acc, const fp_cube* piece, int first)
+{
+    fp_cube a = *acc;
+    const fp_cube p = *piece;
+    if (first) {
+        a = p;
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            a.o[k] = min(a.o[k], p.o[k]);
+            a.mx[k] = max(a.mx[k], p.mx[k]);
+        }
+    }
+    uint64_t S = 0;
+    for (int k = 0; k < 3; ++k) S = max(S, (uint64_t)((int64_t)a.mx[k] - (int64_t)a.o[k]) + 1);
+    a.S = S;
+    *acc = a;
+}
+
+// the kept points of a piece appended to the host preview (index order is piece order)
+__global__ void k_preview_append(const int4* prev, const uint64_t* cnt, int4* out, uint64_t cap, const uint64_t* run,
+                                 uint32_t* err)
+{
+    const uint64_t c = *cnt, r = *run;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (r + i < cap) out[r + i] = prev[i];
+        else if (r + i == cap) raise(err, FP_ERR_CAPACITY);
+    }
+}
+
+__global__ void k_add_u64(uint64_t* run, const uint64_t* cnt) { *run += *cnt; }
+__global__ void k_add_u64_u32(uint64_t* run, const uint32_t* cnt) { *run += *cnt; }
+
+// 1 for the points of a piece whose chunk lies in [c0, c1)
+__global__ void k_group_flags(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
+                              uint32_t c0, uint32_t c1, uint32_t* flags)
+{
+    const CubeDev c = load_cube(cube);
+    const float sg = scale_at(c, g);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int4 p = ld_point(pts, i);
+        const uint32_t ch = __ldg(lut + key_small(p.x, p.y, p.z, c, sg, g));
+        flags[i] = ch >= c0 && ch < c1 ? 1u : 0u;
+    }
+}
+
+// stable compaction of the flagged points after the group's earlier pieces
+__global__ void k_group_compact(const fp_point* pts, uint64_t n, const uint32_t* flags, const uint32_t* pos,
+                                uint64_t index_base, const uint64_t* cursor, uint64_t cap, int4* out,
+                                uint32_t* out_idx, uint32_t* err)
+{
+    const uint64_t cur = *cursor;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!flags[i]) continue;
+        const uint64_t o = cur + pos[i];
+        if (o >= cap) { raise(err, FP_ERR_CAPACITY); continue; }
+        out[o] = ld_point(pts, i);
+        out_idx[o] = (uint32_t)(index_base + i);
+    }
+}
+
+// the group's points per cell (0 outside), chunk of a cell relative to c0, chunk offsets relative to the group
+__global__ void k_group_tables(const uint32_t* counts, const uint32_t* lut, uint64_t cells, uint32_t c0, uint32_t c1,
+                               uint32_t* rcounts, uint32_t* lut_local)
+{
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells;
+         m += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t ch = lut[m];
+        const bool in = ch >= c0 && ch < c1;
+        rcounts[m] = in ? counts[m] : 0u;
+        lut_local[m] = in ? ch - c0 : 0xFFFFFFFFu;
+    }
+}
+
+__global__ void k_group_offsets(const uint64_t* offsets, uint32_t c0, uint32_t k, uint64_t* off_local, uint32_t* kdev)
+{
+    const uint64_t b = offsets[c0];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= k; i += gridDim.x * blockDim.x)
+        off_local[i] = offsets[c0 + i] - b;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *kdev = k;
+}
+
+__global__ void k_compose(const uint32_t* perm_local, const uint32_t* idx, uint64_t n, uint32_t* perm)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        perm[i] = idx[perm_local[i]];
+}
+
+__global__ void k_owner_keys(const uint32_t* owner, uint64_t n, uint64_t* key)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        key[i] = owner[i];
+}
+
+// first position of every key run of a sorted array: soff[key >> shift] = t
+__global__ void k_run_starts(const uint64_t* key, uint64_t S, int shift, uint32_t* soff, uint32_t cap)
+{
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < S; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t X = key[t] >> shift;
+        if ((t == 0 || (key[t - 1] >> shift) != X) && X < cap) soff[X] = (uint32_t)t;
+    }
+}
+
+// A group's points sorted by owner: points of nodes inside the group's chunks go
+// to their final positions (index order inside an owner is the distributed
+// order); points of nodes above the chunks are staged with key (owner, index)
+// and their position in the store of group points.
+__global__ void k_group_place(const uint64_t* key, const uint32_t* src, uint64_t n, const uint32_t* soff,
+                              const fp_node* nodes, uint32_t M, uint64_t T, int g, const uint64_t* first,
+                              const int4* pts, const uint32_t* perm, uint64_t group_base, int4* h_final,
+                              uint32_t* h_final_perm, uint64_t n_all, uint64_t* h_st_key, uint32_t* h_st_src,
+                              uint64_t* st_run, uint64_t st_cap, int pbits, uint32_t* err)
+{
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t X = (uint32_t)key[t];
+        const uint32_t j = src[t];
+        if (X >= M) { raise(err, FP_ERR_CAPACITY); continue; }
+        const bool above = nodes[X].count > T && (int)nodes[X].level < g;
+        if (!above) {
+            const uint64_t f = first[X] + (t - soff[X]);
+            if (f >= n_all) { raise(err, FP_ERR_CAPACITY); continue; }
+            h_final[f] = pts[j];
+            h_final_perm[f] = perm[j];
+        } else {
+            const uint64_t o = atomicAdd((unsigned long long*)st_run, 1ull);
+            if (o >= st_cap) { raise(err, FP_ERR_CAPACITY); continue; }
+            h_st_key[o] = ((uint64_t)X << pbits) | perm[j];
+            h_st_src[o] = (uint32_t)(group_base + j);
+        }
+    }
+}
+
+// staged records sorted by (owner, index): position first[owner] + rank
+__global__ void k_stitch_final(const uint64_t* key, const uint32_t* val, uint64_t S, int pbits, const uint32_t* soff,
+                               const uint64_t* first, const uint32_t* h_st_src, const int4* h_pts,
+                               const uint32_t* h_perm, int4* h_final, uint32_t* h_final_perm, uint64_t n_all,
+                               uint32_t M, uint32_t* err)
+{
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < S; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t X = key[t] >> pbits;
+        if (X >= M) { raise(err, FP_ERR_CAPACITY); continue; }
+        const uint64_t f = first[X] + (t - soff[X]);
+        const uint32_t j = h_st_src[val[t]];
+        if (f >= n_all || j >= n_all) { raise(err, FP_ERR_CAPACITY); continue; }
+        h_final[f] = h_pts[j];
+        h_final_perm[f] = h_perm[j];
+    }
+}
+
+// ------------------------------------------------------------------ layout
+struct HostStore {
+    int4* pts;          // n: the distributed points, group after group
+    uint32_t* perm;     // n: their original indices
+    uint8_t* own;       // n: LOD owner level
+    uint8_t* leaf;      // n: leaf level
+    uint32_t* owner;    // n: owner id
+    uint64_t* st_key;   // n: staged (owner, index)
+    uint32_t* st_src;   // n: staged record's position in pts
+};
+
+HostStore host_carve(void* base, uint64_t n)
+{
+    Workspace w;
+    w.base = static_cast<char*>(base);
+    const uint64_t N = n ? n : 1;
+    HostStore h;
+    h.pts = w.take<int4>(N);
+    h.perm = w.take<uint32_t>(N);
+    h.own = w.take<uint8_t>(N);
+    h.leaf = w.take<uint8_t>(N);
+    h.owner = w.take<uint32_t>(N);
+    h.st_key = w.take<uint64_t>(N);
+    h.st_src = w.take<uint32_t>(N);
+    return h;
+}
+
+size_t host_bytes(uint64_t n)
+{
+    Workspace dry;
+    host_carve(nullptr, n);
+    const uint64_t N = n ? n : 1;
+    return Workspace::bytes_for({16 * N, 4 * N, N, N, 4 * N, 8 * N, 4 * N});
+}
+
+uint64_t preview_piece_cap(uint64_t p, uint32_t m)
+{   // a sum of p Bernoulli(1/m) draws: far below this bound
+    if (m <= 2) return p;
+    uint64_t mean = p / m;
+    uint64_t sd = 1;
+    while (sd * sd < mean) ++sd;
+    return std::min<uint64_t>(p, mean + 64 + 32 * sd);
+}
+
+struct Fixed {   // device buffers kept for the whole build
+    fp_cube *cube, *piece_cube;
+    uint32_t *counts, *lut, *num_chunks;
+    fp_chunk* chunks;
+    uint64_t *offsets, *prev_run, *prev_cnt, *cursor, *st_run;
+    int4* piece[2];
+    int4* prev_buf;
+    uint32_t *flags, *pos, *total;
+    NodeRec* recs;
+    fp_node* nodes;
+    uint32_t *num_deep, *num_nodes, *nm, *soff;
+    uint64_t *first, *tiles64;
+    uint32_t* tiles32;
+    NodeTables T;
+    uint32_t *rcounts, *lut_local, *kdev;
+    uint64_t* off_local;
+};
+
+Fixed fixed_carve(const Workspace& w, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+{
+    Fixed F;
+    const uint64_t cells = 1ull << (3 * p.grid_log2);
+    F.cube = w.take<fp_cube>(1);
+    F.piece_cube = w.take<fp_cube>(1);
+    F.counts = w.take<uint32_t>(cells);
+    F.lut = w.take<uint32_t>(cells);
+    F.num_chunks = w.take<uint32_t>(1);
+    F.chunks = w.take<fp_chunk>(cells);
+    F.offsets = w.take<uint64_t>(cells + 1);
+    F.prev_run = w.take<uint64_t>(1);
+    F.prev_cnt = w.take<uint64_t>(1);
+    F.cursor = w.take<uint64_t>(1);
+    F.st_run = w.take<uint64_t>(1);
+    F.piece[0] = w.take<int4>(P);
+    F.piece[1] = w.take<int4>(P);
+    F.prev_buf = w.take<int4>(preview_piece_cap(P, p.decim_modulus) + 1);
+    F.flags = w.take<uint32_t>(P);
+    F.pos = w.take<uint32_t>(P);
+    F.total = w.take<uint32_t>(1);
+    F.recs = reinterpret_cast<NodeRec*>(w.take<unsigned char>(kNodeRecBytes * node_cap));
+    F.nodes = w.take<fp_node>(node_cap);
+    F.num_deep = w.take<uint32_t>(1);
+    F.num_nodes = w.take<uint32_t>(1);
+    F.nm = w.take<uint32_t>(1);
+    F.soff = w.take<uint32_t>(node_cap);
+    F.first = w.take<uint64_t>(node_cap + 1);
+    F.tiles64 = w.take<uint64_t>(kScanMaxTiles);
+    F.tiles32 = w.take<uint32_t>(kScanMaxTiles);
+    F.T.idxtab = w.take<uint32_t>(cells * 8 / 7 + 8);
+    F.T.starts = w.take<uint64_t>(node_cap);
+    F.T.slevel = w.take<uint8_t>(node_cap);
+    F.T.ndesc = w.take<uint32_t>(node_cap);
+    F.T.nown = w.take<uint32_t>(node_cap);
+    F.T.nnode = w.take<uint32_t>(1);
+    F.rcounts = w.take<uint32_t>(cells);
+    F.lut_local = w.take<uint32_t>(cells);
+    F.kdev = w.take<uint32_t>(1);
+    F.off_local = w.take<uint64_t>(cells + 1);
+    (void)num_sms;
+    return F;
+}
+
+struct Group {   // device buffers of one chunk group (G points), reused group after group
+    int4 *in, *pts;
+    uint32_t *idx, *perm_local, *perm, *owner;
+    uint8_t *own, *leaf;
+    uint64_t *key, *key2, *key3;
+    uint32_t *val2, *val3;
+    char* ws;      // stage workspace
+    size_t ws_bytes;
+};
+
+size_t stage_ws(uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+{
+    size_t w = std::max(distribute_ws_bytes(G, (int)p.grid_log2), octree_ws_bytes(G, p));
+    w = std::max(w, bounds_ws_bytes(P, num_sms));
+    w = std::max(w, merge_ws_bytes((int)p.grid_log2));
+    w = std::max(w, nodes_ws_bytes(p, node_cap));
+    w = std::max(w, sort_scratch_bytes(G));
+    return w;
+}
+
+Group group_carve(const Workspace& w, uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+{
+    Group g;
+    const uint64_t N = G ? G : 1;
+    g.in = w.take<int4>(N);
+    g.pts = w.take<int4>(N);
+    g.idx = w.take<uint32_t>(N);
+    g.perm_local = w.take<uint32_t>(N);
+    g.perm = w.take<uint32_t>(N);
+    g.owner = w.take<uint32_t>(N);
+    g.own = w.take<uint8_t>(N);
+    g.leaf = w.take<uint8_t>(N);
+    g.key = w.take<uint64_t>(N);
+    g.key2 = w.take<uint64_t>(N);
+    g.key3 = w.take<uint64_t>(N);
+    g.val2 = w.take<uint32_t>(N);
+    g.val3 = w.take<uint32_t>(N);
+    g.ws_bytes = stage_ws(G, P, p, node_cap, num_sms);
+    g.ws = w.take<char>(g.ws_bytes);
+    return g;
+}
+
+size_t fixed_bytes(uint64_t P, const fp_params& p, uint64_t node_cap)
+{
+    Workspace dry;
+    fixed_carve(dry, P, p, node_cap, 152);
+    return dry.used;
+}
+
+size_t group_bytes(uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+{
+    Workspace dry;
+    group_carve(dry, G, P, p, node_cap, num_sms);
+    return dry.used;
+}
+
+// the largest group (points) that fits next to the fixed buffers
+uint64_t group_cap_for(size_t arena, uint64_t n, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+{
+    const size_t fixed = fixed_bytes(P, p, node_cap);
+    if (arena <= fixed) return 0;
+    uint64_t lo = 0, hi = std::max<uint64_t>(n, 1);
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) / 2;
+        if (fixed + group_bytes(mid, P, p, node_cap, num_sms) <= arena) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Piecer {   // double-buffered host -> device copies of the pieces on a side stream
+    cudaStream_t cs = nullptr, st = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    const fp_point* h = nullptr;
+    uint64_t n = 0, P = 0;
+    int4* buf[2] = {nullptr, nullptr};
+
+    cudaError_t init(cudaStream_t stream, const fp_point* hp, uint64_t nn, uint64_t pp, int4* b0, int4* b1)
+    {
+        st = stream; h = hp; n = nn; P = pp; buf[0] = b0; buf[1] = b1;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && !e; ++b) {
+            if ((e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming))) break;
+            e = cudaEventCreateWithFlags(&consumed[b], cudaEventDisableTiming);
+            if (!e) e = cudaEventRecord(consumed[b], st);
+        }
+        return e;
+    }
+    uint64_t pieces() const { return (n + P - 1) / P; }
+    uint64_t size(uint64_t k) const { return std::min(P, n - k * P); }
+    // enqueue the copy of piece k (after the work that read its buffer), compute stream waits for it
+    cudaError_t fetch(uint64_t k)
+    {
+        const int b = (int)(k & 1);
+        cudaError_t e;
+        if ((e = cudaStreamWaitEvent(cs, consumed[b], 0))) return e;
+        if ((e = cudaMemcpyAsync(buf[b], h + k * P, size(k) * sizeof(fp_point), cudaMemcpyHostToDevice, cs))) return e;
+        if ((e = cudaEventRecord(copied[b], cs))) return e;
+        return cudaStreamWaitEvent(st, copied[b], 0);
+    }
+    cudaError_t done(uint64_t k) { return cudaEventRecord(consumed[k & 1], st); }
+    // pass over all pieces: body(k, device pointer, size) enqueues the work on st
+    template <typename F>
+    cudaError_t pass(F body)
+    {
+        const uint64_t np = pieces();
+        cudaError_t e;
+        if (np && (e = fetch(0))) return e;
+        for (uint64_t k = 0; k < np; ++k) {
+            if (k + 1 < np && (e = fetch(k + 1))) return e;   // the next copy overlaps this piece's work
+            if ((e = body(k, reinterpret_cast<const fp_point*>(buf[k & 1]), size(k)))) return e;
+            if ((e = done(k))) return e;
+        }
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (cs) cudaStreamSynchronize(cs);
+        for (int b = 0; b < 2; ++b) {
+            if (copied[b]) cudaEventDestroy(copied[b]);
+            if (consumed[b]) cudaEventDestroy(consumed[b]);
+        }
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+fp_status cu(cudaError_t e) { return e == cudaSuccess ? FP_OK : FP_ERR_CUDA; }
+
+inline unsigned grid_for(uint64_t n, int num_sms) { return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms * 16)); }
+
+fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_t P, uint64_t group_points,
+                void* d_arena, size_t arena_bytes,
+                void* h_scratch, fp_cube* h_cube, fp_point* h_preview, uint64_t preview_cap,
+                uint64_t* h_preview_count, fp_node* h_nodes, uint32_t node_cap, uint32_t* h_num_nodes,
+                fp_point* h_final, uint32_t* h_final_perm, void (*preview_done)(void*), void* user, cudaStream_t st,
+                Piecer& io)
+{
+    Workspace base;
+    fp_status s = make_workspace(d_arena, arena_bytes, 0, base);
+    if (s != FP_OK) return s;
+    const int g = (int)prm.grid_log2;
+    const uint64_t cells = 1ull << (3 * g);
+    uint64_t G = group_cap_for(arena_bytes, n, P, prm, node_cap, base.num_sms);
+    if (group_points) G = std::min(G, group_points);
+    if (G == 0) return FP_ERR_WORKSPACE;
+    Workspace w = base;
+    const Fixed F = fixed_carve(w, P, prm, node_cap, base.num_sms);
+    const Group B = group_carve(w, G, P, prm, node_cap, base.num_sms);
+    Workspace ws = base;   // stage workspace view
+    ws.base = B.ws;
+    ws.bytes = B.ws_bytes;
+    ws.used = 0;
+    const HostStore H = host_carve(h_scratch, n);
+    const uint32_t* err = base.err;
+    cudaError_t e;
+    if ((e = io.init(st, h_pts, n, P, F.piece[0], F.piece[1]))) return FP_ERR_CUDA;
+
+    // ---- pass 1: bounds and preview
+    if ((e = cudaMemsetAsync(F.prev_run, 0, sizeof(uint64_t), st))) return cu(e);
+    const uint64_t pcap = preview_piece_cap(P, prm.decim_modulus);
+    e = io.pass([&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
+        ws.used = 0;
+        cudaError_t x = launch_bounds_decimate(p, np, F.piece_cube, true, true, k * P, prm.decim_modulus,
+                                               reinterpret_cast<fp_point*>(F.prev_buf), pcap, F.prev_cnt, ws, st);
+        if (x) return x;
+        k_cube_fold<<<1, 1, 0, st>>>(F.cube, F.piece_cube, k == 0);
+        k_preview_append<<<grid_for(pcap, ws.num_sms), 256, 0, st>>>(F.prev_buf, F.prev_cnt,
+                                                                     reinterpret_cast<int4*>(h_preview), preview_cap,
+                                                                     F.prev_run, base.err);
+        k_add_u64<<<1, 1, 0, st>>>(F.prev_run, F.prev_cnt);
+        return cudaGetLastError();
+    });
+    if (e) return cu(e);
+    if ((e = cudaMemcpyAsync(h_cube, F.cube, sizeof(fp_cube), cudaMemcpyDeviceToHost, st))) return cu(e);
+    if ((e = cudaMemcpyAsync(h_preview_count, F.prev_run, sizeof(uint64_t), cudaMemcpyDeviceToHost, st))) return cu(e);
+    if (preview_done && (e = cudaLaunchHostFunc(st, preview_done, user))) return cu(e);
+
+    // ---- pass 2: counts; chunks
+    e = io.pass([&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
+        ws.used = 0;
+        return launch_count(p, np, F.cube, g, F.counts, k > 0, ws, st);
+    });
+    if (e) return cu(e);
+    ws.used = 0;
+    if ((e = launch_merge(F.counts, g, prm.chunk_threshold, F.chunks, F.num_chunks, F.lut, F.offsets, ws, st)))
+        return cu(e);
+    uint32_t K = 0;
+    if ((e = cudaMemcpyAsync(&K, F.num_chunks, sizeof(K), cudaMemcpyDeviceToHost, st))) return cu(e);
+    if ((e = cudaStreamSynchronize(st))) return cu(e);
+    std::vector<uint64_t> off(K + 1);
+    if ((e = cudaMemcpyAsync(off.data(), F.offsets, (K + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st)))
+        return cu(e);
+    if ((e = cudaStreamSynchronize(st))) return cu(e);
+    if (off[K] != n) return FP_ERR_INVALID;
+    // consecutive chunks while they fit a group
+    std::vector<std::pair<uint32_t, uint32_t>> groups;
+    for (uint32_t c0 = 0; c0 < K;) {
+        uint32_t c1 = c0 + 1;
+        if (off[c1] - off[c0] > G) return FP_ERR_WORKSPACE;   // one chunk larger than the arena allows
+        while (c1 < K && off[c1 + 1] - off[c0] <= G) ++c1;
+        groups.push_back({c0, c1});
+        c0 = c1;
+    }
+
+    // ---- pass 3 per group: its points (distributed), levels, nodes below level g
+    if ((e = cudaMemsetAsync(F.num_deep, 0, sizeof(uint32_t), st))) return cu(e);
+    const unsigned gc = grid_for(cells, base.num_sms);
+    auto gather = [&](uint32_t c0, uint32_t c1, uint64_t ng) -> cudaError_t {
+        cudaError_t x;
+        k_group_tables<<<gc, 256, 0, st>>>(F.counts, F.lut, cells, c0, c1, F.rcounts, F.lut_local);
+        k_group_offsets<<<gc, 256, 0, st>>>(F.offsets, c0, c1 - c0, F.off_local, F.kdev);
+        if ((x = cudaMemsetAsync(F.cursor, 0, sizeof(uint64_t), st))) return x;
+        x = io.pass([&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
+            k_group_flags<<<grid_for(np, base.num_sms), 256, 0, st>>>(p, np, F.cube, g, F.lut, c0, c1, F.flags);
+            cudaError_t y = scan_exclusive<uint32_t, uint32_t>(F.flags, F.pos, np, nullptr, F.tiles32, F.total,
+                                                               (uint32_t*)nullptr, st);
+            if (y) return y;
+            k_group_compact<<<grid_for(np, base.num_sms), 256, 0, st>>>(p, np, F.flags, F.pos, k * P, F.cursor, G,
+                                                                        B.in, B.idx, base.err);
+            k_add_u64_u32<<<1, 1, 0, st>>>(F.cursor, F.total);
+            return cudaGetLastError();
+        });
+        if (x) return x;
+        ws.used = 0;
+        if ((x = launch_distribute(reinterpret_cast<const fp_point*>(B.in), ng, F.cube, g, F.lut_local, F.off_local,
+                                   F.kdev, reinterpret_cast<fp_point*>(B.pts), B.perm_local, ws, st)))
+            return x;
+        k_compose<<<grid_for(ng, base.num_sms), 256, 0, st>>>(B.perm_local, B.idx, ng, B.perm);
+        return cudaGetLastError();
+    };
+    for (auto [c0, c1] : groups) {
+        const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
+        if ((e = gather(c0, c1, ng))) return cu(e);
+        if ((e = cudaMemcpyAsync(H.pts + b0, B.pts, ng * 16, cudaMemcpyDeviceToHost, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(H.perm + b0, B.perm, ng * 4, cudaMemcpyDeviceToHost, st))) return cu(e);
+        OctGroup grp{F.rcounts, (uint32_t)b0, B.own, B.leaf, F.recs, node_cap, F.num_deep};
+        ws.used = 0;
+        if ((e = launch_octree_impl(reinterpret_cast<const fp_point*>(B.pts), B.perm, ng, F.cube, F.chunks + c0,
+                                    F.kdev, F.off_local, F.counts, prm, nullptr, 0, nullptr, nullptr, nullptr,
+                                    nullptr, &grp, ws, st)))
+            return cu(e);
+        if ((e = cudaMemcpyAsync(H.own + b0, B.own, ng, cudaMemcpyDeviceToHost, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(H.leaf + b0, B.leaf, ng, cudaMemcpyDeviceToHost, st))) return cu(e);
+    }
+
+    // ---- node table of the whole cloud
+    ws.used = 0;
+    if ((e = launch_octree_nodes(F.counts, prm, F.recs, node_cap, F.num_deep, F.nodes, node_cap, F.num_nodes, F.T, ws,
+                                 st)))
+        return cu(e);
+
+    // ---- pass 4 per group: owner ids, owned counts
+    for (auto [c0, c1] : groups) {
+        const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
+        if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(B.own, H.own + b0, ng, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(B.leaf, H.leaf + b0, ng, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = launch_octree_resolve(reinterpret_cast<const fp_point*>(B.pts), ng, F.cube, B.own, B.leaf, F.T, prm,
+                                       B.owner, ws, st)))
+            return cu(e);
+        if ((e = cudaMemcpyAsync(H.owner + b0, B.owner, ng * 4, cudaMemcpyDeviceToHost, st))) return cu(e);
+    }
+    if ((e = launch_node_first(F.nodes, F.num_nodes, node_cap, F.T.nown, F.first, F.nm, F.tiles64, st))) return cu(e);
+    uint32_t M = 0;
+    if ((e = cudaMemcpyAsync(&M, F.num_nodes, sizeof(M), cudaMemcpyDeviceToHost, st))) return cu(e);
+    if ((e = cudaStreamSynchronize(st))) return cu(e);
+    if (M > node_cap) return FP_ERR_INVALID;
+    int pbits = 1;
+    while ((1ull << pbits) < n) ++pbits;
+    int mbits = 1;
+    while ((1ull << mbits) < M) ++mbits;
+
+    // ---- pass 5 per group: final positions of points kept inside the chunks; the rest staged
+    if ((e = cudaMemsetAsync(F.st_run, 0, sizeof(uint64_t), st))) return cu(e);
+    ws.used = 0;
+    const SortScratch sc = take_sort_scratch(ws, G);
+    const size_t ws_after_sc = ws.used;
+    for (auto [c0, c1] : groups) {
+        const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
+        if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(B.perm, H.perm + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(B.owner, H.owner + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
+        k_owner_keys<<<grid_for(ng, base.num_sms), 256, 0, st>>>(B.owner, ng, B.key);
+        ws.used = ws_after_sc;
+        if ((e = sort_plan_keys(sc, B.key, ng, nullptr, 0, (uint32_t)mbits, st))) return cu(e);
+        SortArgs a{};
+        a.b.k64_src = B.key; a.b.k64_tmp = B.key2; a.b.k64_dst = B.key3;
+        a.b.val_src = nullptr; a.b.val_tmp = B.val2; a.b.val_dst = B.val3;
+        a.n = ng; a.err = base.err;
+        for (int slot = 0; slot < kSortMaxPass; ++slot)
+            if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a, slot, base.num_sms, st))) return cu(e);
+        k_run_starts<<<grid_for(ng, base.num_sms), 256, 0, st>>>(B.key3, ng, 0, F.soff, M);
+        k_group_place<<<grid_for(ng, base.num_sms), 256, 0, st>>>(
+            B.key3, B.val3, ng, F.soff, F.nodes, M, prm.chunk_threshold, g, F.first, B.pts, B.perm, b0,
+            reinterpret_cast<int4*>(h_final), h_final_perm, n, H.st_key, H.st_src, F.st_run, n, pbits, base.err);
+        if ((e = cudaGetLastError())) return cu(e);
+    }
+
+    // ---- the staged points: sorted by (owner, index), placed after their owners' earlier points
+    uint64_t S = 0;
+    if ((e = cudaMemcpyAsync(&S, F.st_run, sizeof(S), cudaMemcpyDeviceToHost, st))) return cu(e);
+    if ((e = cudaStreamSynchronize(st))) return cu(e);
+    if (S) {   // the sort of the staged records reuses the whole group region
+        Workspace wf = base;
+        wf.base = reinterpret_cast<char*>(B.in);
+        wf.bytes = group_bytes(G, P, prm, node_cap, base.num_sms);
+        wf.used = 0;
+        uint64_t* k1 = wf.take<uint64_t>(S);
+        uint64_t* k2 = wf.take<uint64_t>(S);
+        uint64_t* k3 = wf.take<uint64_t>(S);
+        uint32_t* v2 = wf.take<uint32_t>(S);
+        uint32_t* v3 = wf.take<uint32_t>(S);
+        const SortScratch sf = take_sort_scratch(wf, S);
+        if (wf.used > wf.bytes) return FP_ERR_WORKSPACE;
+        if ((e = cudaMemcpyAsync(k1, H.st_key, S * 8, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = sort_plan_keys(sf, k1, S, nullptr, 0, (uint32_t)(pbits + mbits), st))) return cu(e);
+        SortArgs a{};
+        a.b.k64_src = k1; a.b.k64_tmp = k2; a.b.k64_dst = k3;
+        a.b.val_src = nullptr; a.b.val_tmp = v2; a.b.val_dst = v3;
+        a.n = S; a.err = base.err;
+        for (int slot = 0; slot < kSortMaxPass; ++slot)
+            if ((e = sort_run_pass<DIG_K64, false, true, false>(sf, a, slot, base.num_sms, st))) return cu(e);
+        k_run_starts<<<grid_for(S, base.num_sms), 256, 0, st>>>(k3, S, pbits, F.soff, M);
+        k_stitch_final<<<grid_for(S, base.num_sms), 256, 0, st>>>(k3, v3, S, pbits, F.soff, F.first, H.st_src, H.pts,
+                                                                  H.perm, reinterpret_cast<int4*>(h_final),
+                                                                  h_final_perm, n, M, base.err);
+        if ((e = cudaGetLastError())) return cu(e);
+    }
+    if ((e = cudaMemcpyAsync(h_nodes, F.nodes, (size_t)M * sizeof(fp_node), cudaMemcpyDeviceToHost, st))) return cu(e);
+    if ((e = cudaMemcpyAsync(h_num_nodes, F.num_nodes, sizeof(uint32_t), cudaMemcpyDeviceToHost, st))) return cu(e);
+    (void)err;
+    return cu(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+}  // namespace fp
+
+using namespace fp;
+
+extern "C" {
+
+size_t fp_ooc_host_bytes(uint64_t n, const fp_params* prm)
+{
+    if (!prm || check_params(prm) != FP_OK) return 0;
+    return host_bytes(n);
+}
+
+size_t fp_ooc_arena_min(uint64_t n, const fp_params* prm, uint64_t piece_points)
+{
+    if (!prm || check_params(prm) != FP_OK) return 0;
+    const uint64_t P = piece_points ? std::min(piece_points, kMaxPiece) : kMaxPiece;
+    const uint64_t ncap = node_capacity_bound(n, *prm);
+    // the fixed buffers and a group of 2^20 points (or the whole cloud)
+    return fixed_bytes(P, *prm, ncap) + group_bytes(std::min<uint64_t>(std::max<uint64_t>(n, 1), 1ull << 20), P, *prm,
+                                                    ncap, 152);
+}
+
+fp_status fp_build_ooc(const fp_point* h_pts, uint64_t n, const fp_params* h_prm, uint64_t piece_points,
+                       uint64_t group_points, void* d_arena, size_t arena_bytes, void* h_scratch,
+                       size_t scratch_bytes, fp_cube* h_cube,
+                       fp_point* h_preview, uint64_t preview_cap, uint64_t* h_preview_count, fp_node* h_nodes,
+                       uint32_t node_cap, uint32_t* h_num_nodes, fp_point* h_final, uint32_t* h_final_perm,
+                       void (*preview_done)(void*), void* user, cudaStream_t stream)
+{
+    fp_status s = check_params(h_prm);
+    if (s != FP_OK) return s;
+    if (n == 0 || !h_pts || !d_arena || !h_scratch || !h_cube || !h_preview_count || !h_nodes || !h_num_nodes ||
+        !h_final || !h_final_perm || (preview_cap && !h_preview))
+        return FP_ERR_INVALID;
+    if (n >= (1ull << 30)) return FP_ERR_TOO_LARGE;
+    if ((reinterpret_cast<uintptr_t>(h_pts) | reinterpret_cast<uintptr_t>(h_final) |
+         reinterpret_cast<uintptr_t>(h_preview) | reinterpret_cast<uintptr_t>(d_arena) |
+         reinterpret_cast<uintptr_t>(h_scratch)) & 15u)
+        return FP_ERR_ALIGN;
+    if (scratch_bytes < host_bytes(n)) return FP_ERR_WORKSPACE;
+    if (node_cap < node_capacity_bound(n, *h_prm) || node_cap > (1u << 23)) return FP_ERR_UNSUPPORTED;
+    const uint64_t P = piece_points ? std::min(piece_points, kMaxPiece) : kMaxPiece;
+    Piecer io;
+    s = build(h_pts, n, *h_prm, P, group_points, d_arena, arena_bytes, h_scratch, h_cube, h_preview, preview_cap, h_preview_count,
+              h_nodes, node_cap, h_num_nodes, h_final, h_final_perm, preview_done, user, stream, io);
+    io.release();
+    // nothing of the build may still run once the caller gets the arena back
+    if (cudaStreamSynchronize(stream) != cudaSuccess && s == FP_OK) s = FP_ERR_CUDA;
+    return s;
+}
+
+}  // extern "C"

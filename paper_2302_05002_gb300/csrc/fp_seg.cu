@@ -146,7 +146,7 @@ cudaError_t seg_scatter(const SegScratch& sc, const SegCall& c, const Workspace&
     a.first = c.first; a.first_stride = c.first_stride;
     a.stitch = owner ? 1 : 0;
     a.st_key = c.st_key; a.st_src = c.st_src; a.st_count = c.st_count; a.st_cap = c.n; a.st_shift = c.st_shift;
-    a.n = c.n;
+    a.n = c.out_n ? c.out_n : c.n;
     a.d_fail = sc.cnt + 2;
     a.err = ws.err;
     const bool cpt = c.pt_in && c.pt_out;

@@ -52,7 +52,7 @@ struct SegArgs {
     uint32_t* st_count;
     uint64_t st_cap;
     int st_shift;
-    uint64_t n;                           // records, and output positions
+    uint64_t n;                           // bound of the output positions
 
     const uint32_t* d_fail;
     uint32_t* err;
@@ -246,6 +246,7 @@ struct SegCall {
     const uint32_t* val_in; uint32_t* val_out;
     const uint32_t* id_in;
     uint64_t n;
+    uint64_t out_n;       // bound of the output positions (0: n)
     const uint64_t* first; uint32_t first_stride;
     // owner layout: staging
     uint64_t* st_key; uint32_t* st_src; uint32_t* st_count; int st_shift;

@@ -41,6 +41,7 @@ class fp_cloud_desc(ctypes.Structure):
 
 
 MAX_LANES = 32
+PREVIEW_DONE = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
 STAGE = dict(bounds=0, decimate=1, bounds_decimate=2, count=3, merge=4, distribute=5, octree=6, subsample=7)
 ERR_BITS = {1 << 6: "timeout", 1 << 9: "capacity"}
 NODE_BYTES, CHUNK_BYTES, CUBE_BYTES = 40, 16, 32
@@ -71,6 +72,9 @@ def load():
         "fp_build_chunk_octree": (st, [p, p, u64, p, p, p, p, p, p, p, u32, p, p, p, p, p, sz, p]),
         "fp_subsample": (st, [p, p, u32, p, p, p, u64, p, p, p, p, p, p, sz, p]),
         "fp_batch_workspace_size": (sz, [p, u32, u32]),
+        "fp_ooc_arena_min": (sz, [u64, p, u64]),
+        "fp_ooc_host_bytes": (sz, [u64, p]),
+        "fp_build_ooc": (st, [p, u64, p, u64, u64, p, sz, p, sz, p, p, u64, p, p, u32, p, p, p, PREVIEW_DONE, p, p]),
         "fp_build_batched": (st, [p, u32, u32, p, sz, p]),
     }
     for name, (res, args) in sig.items():
@@ -338,6 +342,48 @@ def build_batched(clouds, nlanes=8, stream=None, outs=None, ws=None):
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     fp_build_batched(descs, len(clouds), nlanes, ws, stream=stream)
     return outs, descs, ws
+
+
+# ------------------------------------------------------------------ out of core
+def ooc_host_bytes(n, prm):
+    return int(load().fp_ooc_host_bytes(n, ctypes.byref(prm)))
+
+
+def ooc_arena_min(n, prm, piece_points=1 << 23):
+    return int(load().fp_ooc_arena_min(n, ctypes.byref(prm), piece_points))
+
+
+def ooc_outputs(n, prm):
+    """Pinned host outputs of fp_build_ooc for a cloud of n points."""
+    ncap = node_capacity_bound(n, prm)
+    cap = _preview_cap(n, prm.decim_modulus)
+    pin = lambda *shape, dtype=torch.int32: torch.empty(shape, dtype=dtype).pin_memory()
+    return dict(cube=pin(8), preview=pin(max(cap, 1), 4), preview_count=torch.zeros(1, dtype=torch.int64).pin_memory(),
+                nodes=pin(max(ncap, 1), 10), num_nodes=torch.zeros(1, dtype=torch.int32).pin_memory(),
+                final=pin(max(n, 1), 4), final_perm=pin(max(n, 1)), preview_cap=cap, node_cap=ncap)
+
+
+def build_ooc(host_pts, prm, arena, piece_points=1 << 23, group_points=0, scratch=None, out=None, on_preview=None,
+              stream=None):
+    """Out-of-core build of a cloud in pinned host memory ((n, 4) int32 CPU
+    tensor) inside the device arena (uint8 CUDA tensor).  Blocks until done;
+    on_preview() is called from a CUDA callback thread when the preview is in
+    out["preview"].  Returns the pinned host outputs."""
+    n = host_pts.shape[0]
+    if out is None:
+        out = ooc_outputs(n, prm)
+    need = ooc_host_bytes(n, prm)
+    if scratch is None or scratch.numel() < need:
+        scratch = torch.empty(need, dtype=torch.uint8).pin_memory()
+    cb = PREVIEW_DONE((lambda _u: on_preview()) if on_preview is not None else 0)
+    st = load().fp_build_ooc(_ptr(host_pts), n, ctypes.byref(prm), piece_points, group_points, _ptr(arena),
+                             arena.numel(),
+                             _ptr(scratch), scratch.numel(), _ptr(out["cube"]), _ptr(out["preview"]),
+                             out["preview_cap"], _ptr(out["preview_count"]), _ptr(out["nodes"]), out["node_cap"],
+                             _ptr(out["num_nodes"]), _ptr(out["final"]), _ptr(out["final_perm"]), cb, None,
+                             _stream(stream))
+    _check(st, "fp_build_ooc")
+    return out
 
 
 # ------------------------------------------------------------------ decoding

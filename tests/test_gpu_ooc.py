@@ -1,0 +1,58 @@
+"""fp_build_ooc: a cloud in pinned host memory built in chunk groups inside a
+device arena gives exactly the in-core build's cube, preview, node table and
+final layout (which the other GPU tests pin to the oracle), for several group
+and piece sizes, including groups of one chunk and clouds with points kept
+above the chunks."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def cloud(kind, n, seed):
+    if kind == "uniform":
+        return synth.uniform(n, seed)
+    if kind == "lidar":
+        return synth.lidar(n, seed)
+    base = synth.uniform(max(1, n // 40), seed, bits=9)   # duplicates
+    return base[(np.arange(n) * 7919) % len(base)]
+
+
+CASES = [
+    # kind, n, seed, g, s, lmax, T, C, piece, group
+    ("lidar", 300_000, 41, 7, 7, 15, 10_000, 2_000, 50_000, 70_000),
+    ("uniform", 200_000, 42, 5, 6, 12, 5_000, 500, 32_768, 40_000),
+    ("dups", 50_000, 43, 3, 3, 9, 1_000, 40, 8_192, 10_000),
+    ("lidar", 120_000, 44, 6, 7, 14, 30_000, 3_000, 1 << 20, 0),        # one piece, one group
+    ("uniform", 100_000, 45, 4, 4, 10, 2_000, 2_000, 25_000, 2_000),    # groups of about one chunk
+]
+
+
+@pytest.mark.parametrize("kind,n,seed,g,s,lmax,T,C,piece,group", CASES)
+def test_ooc_equals_in_core(gpu_lib, kind, n, seed, g, s, lmax, T, C, piece, group):
+    fp = gpu_lib
+    prm = fp.params(grid_log2=g, sub_log2=s, max_level=lmax, decim_modulus=16, chunk_threshold=T, node_capacity=C)
+    pts_np = cloud(kind, n, seed)
+    dev = fp.as_points(pts_np, "cuda")
+    ref = fp.build_octree(dev, prm)
+    torch.cuda.synchronize()
+    host = dev.cpu().pin_memory()
+    arena = torch.empty(max(fp.ooc_arena_min(n, prm, piece), 64 << 20), dtype=torch.uint8, device="cuda")
+    seen = []
+    out = fp.build_ooc(host, prm, arena, piece_points=piece, group_points=group, on_preview=lambda: seen.append(1))
+    assert fp.get_device_error() == 0
+    assert seen == [1]
+    assert torch.equal(out["cube"].view(torch.uint8), ref["cube"].cpu().view(torch.uint8).reshape(-1)[:32])
+    k = int(ref["preview_count"].item())
+    assert int(out["preview_count"].item()) == k
+    assert torch.equal(out["preview"][:k], ref["preview"][:k].cpu())
+    M = int(ref["num_nodes"].item())
+    assert int(out["num_nodes"].item()) == M
+    a = out["nodes"][:M].contiguous().view(torch.uint8).reshape(M, 40)
+    b = ref["nodes"][:M].cpu().contiguous().view(torch.uint8).reshape(M, 40)
+    assert torch.equal(a, b), "node tables differ"
+    assert torch.equal(out["final_perm"][:n], ref["final_perm"].cpu()[:n])
+    assert torch.equal(out["final"][:n], ref["final"].cpu()[:n])
