@@ -264,8 +264,9 @@ def fp_subsample(nodes, num_nodes, sorted_pts, perm, owner, chunks, num_chunks, 
 
 
 # ------------------------------------------------------------------ batches
-def cloud_outputs(pts, prm):
-    """Every output of the hot path for one cloud, allocated on the points' device."""
+def cloud_outputs(pts, prm, leaf=True):
+    """Every output of the hot path for one cloud, allocated on the points' device
+    (leaf=False: without the optional leaf-grouped points)."""
     n = pts.shape[0]
     dev = _dev(pts)
     cells = 1 << (3 * prm.grid_log2)
@@ -277,15 +278,15 @@ def cloud_outputs(pts, prm):
                 chunks=torch.empty((cells, 4), **i32), num_chunks=torch.zeros(1, **i32), lut=torch.empty(cells, **i32),
                 offsets=torch.empty(cells + 1, dtype=torch.int64, device=dev), dist=torch.empty((max(n, 1), 4), **i32),
                 perm=torch.empty(max(n, 1), **i32), nodes=torch.zeros((max(ncap, 1), 10), **i32),
-                num_nodes=torch.zeros(1, **i32), leaf_pts=torch.empty((max(n, 1), 4), **i32),
-                leaf_perm=torch.empty(max(n, 1), **i32), owner=torch.empty(max(n, 1), **i32),
+                num_nodes=torch.zeros(1, **i32), leaf_pts=torch.empty((max(n, 1), 4), **i32) if leaf else None,
+                leaf_perm=torch.empty(max(n, 1), **i32) if leaf else None, owner=torch.empty(max(n, 1), **i32),
                 final=torch.empty((max(n, 1), 4), **i32), final_perm=torch.empty(max(n, 1), **i32),
                 preview_cap=cap, node_cap=ncap)
 
 
 def cloud_desc(pts, prm, out):
     d = fp_cloud_desc()
-    P = lambda t: t.data_ptr()
+    P = lambda t: t.data_ptr() if t is not None else None
     d.d_pts, d.n, d.prm = P(pts), pts.shape[0], prm
     d.d_cube, d.d_preview, d.preview_cap, d.d_preview_count = P(out["cube"]), P(out["preview"]), out["preview_cap"], \
         P(out["preview_count"])
