@@ -30,6 +30,8 @@ WORKLOADS = {
     "lidar-10M": ("lidar", 10_000_000, 2, 7, 7, 15, 100_000, 20_000),
     # 256 clouds, sizes log-uniform in [1e4, 2e7], uniform or LiDAR generator per cloud (seed 1000 + i)
     "batched-256": ("batch", 256, 1000, 7, 7, 15, 100_000, 20_000),
+    # 32 LiDAR requests, sizes log-uniform in [1e6, 5e8], Poisson arrivals 4/s, 24 GB device budget (seed 5000 + i)
+    "served-32": ("served", 32, 5000, 7, 7, 15, 100_000, 20_000),
 }
 STAGES = ["bounds_decimate", "count", "merge", "distribute", "octree", "subsample"]
 # algorithmic HBM bytes per point of each stage (mandatory reads + writes), see the design doc
@@ -408,6 +410,174 @@ def run_batched_reference(args, wl, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ served workload
+def served_plan(count, seed):
+    """Request sizes (log-uniform in [1e6, 5e8]) and arrival offsets (Poisson, 4/s)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(np.log(1e6), np.log(5e8), count))).astype(np.int64)
+    arrivals = np.cumsum(rng.exponential(0.25, count)) - 0.25
+    return [int(x) for x in sizes], [max(0.0, float(t)) for t in arrivals]
+
+
+def host_mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def run_served(args, wl, rank, world, local):
+    """Poisson-arriving LiDAR clouds served under a 24 GB device budget
+    (serve.Server): p50/p99 time to preview and to the full octree, aggregate
+    points/s; the same clouds submitted at once (saturated); and the plain
+    per-cloud builds back to back (copy in, seven calls) on the same GPU."""
+    import torch
+
+    from paper_2302_05002_gb300 import fastpoints as fp
+    from paper_2302_05002_gb300 import serve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _, count, seed0, g, s, lmax, T, C = wl
+    sizes, arrivals = served_plan(count, seed0)
+    note = None
+    avail = host_mem_available()
+    need = sum(sizes) * 18 + 40 * max(sizes)
+    if avail is not None and need > 0.7 * avail:   # shrink every cloud alike to fit the host
+        f = 0.7 * avail / need
+        sizes = [max(1_000_000, int(x * f)) for x in sizes]
+        note = "sizes scaled by %.3f to fit %.0f GB of host memory" % (f, avail / 1e9)
+    budget, piece = 24 << 30, 1 << 23
+
+    def prm_for(n):
+        return fp.params(grid_log2=g, sub_log2=s, max_level=lmax, decim_modulus=16,
+                         chunk_threshold=5_000_000 if n >= 200_000_000 else T, node_capacity=C)
+
+    hosts, prev_bufs, prms = [], [], []
+    for i, n in enumerate(sizes):
+        h = torch.empty((n, 4), dtype=torch.int32).pin_memory()
+        make_cloud("lidar", n, seed0 + i, h)
+        hosts.append(h)
+        prms.append(prm_for(n))
+        prev_bufs.append(torch.empty(serve.preview_slots_shape(n, piece, 16), dtype=torch.int32).pin_memory())
+    ooc = [n for n, p in zip(sizes, prms) if serve.incore_need(n, p) > budget // 2]
+    ooc_max = max(ooc) if ooc else 0
+    ooc_prm = prm_for(ooc_max) if ooc_max else None
+
+    def serve_run(offsets):
+        srv = serve.Server(budget_bytes=budget, piece_points=piece, device=local, ooc_max_points=ooc_max,
+                           ooc_prm=ooc_prm)
+        reqs = [serve.Request(i, hosts[i], prms[i], preview_host=prev_bufs[i]) for i in range(count)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r, off in zip(reqs, offsets):
+            wait = t0 + off - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            srv.submit(r)
+        srv.drain(count)
+        srv.close()
+        errs = [r.error for r in reqs if r.error]
+        assert not errs, errs[0]
+        t_end = max(r.t_done for r in reqs)
+        for r in reqs:
+            r.result = None
+        torch.cuda.empty_cache()
+        return reqs, t0, t_end, srv.peak_active
+
+    # warm: the smallest request alone
+    k = min(range(count), key=lambda i: sizes[i])
+    srv = serve.Server(budget_bytes=budget, piece_points=piece, device=local)
+    r = serve.Request(k, hosts[k], prms[k], preview_host=prev_bufs[k])
+    srv.submit(r)
+    srv.drain(1)
+    srv.close()
+    assert r.error is None, r.error
+
+    clk = ClockSampler(local)
+    clk.start()
+    reqs, t0, t_end, peak = serve_run(arrivals)
+    clocks = clk.stop()
+    ttp = [(r.t_preview - r.arrival) * 1e3 for r in reqs]
+    ttf = [(r.t_done - r.arrival) * 1e3 for r in reqs]
+    total = sum(sizes)
+    served_rate = total / (t_end - t0)
+    sreqs, s0, s_end, speak = serve_run([0.0] * count)
+    saturated_rate = total / (s_end - s0)
+
+    # plain: each cloud in turn, copied in, the seven calls, resident result
+    torch.cuda.synchronize()
+    tp0 = time.perf_counter()
+    for h, p in zip(hosts, prms):
+        pts = h.to(dev, non_blocking=True)
+        r = fp.build_octree(pts, p)
+        del r, pts
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - tp0
+    torch.cuda.empty_cache()
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = served_oracle_rate(sizes, seed0, wl, float(os.environ.get("FP_ORACLE_BUDGET_S", "12")))
+        p50 = serve.percentile(ttp, 0.5)
+        line = {
+            "metric": "served time to preview p50 (ms)", "value": p50, "unit": "ms", "n_gpus": world,
+            "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "requests": count, "points": total, "min_points": min(sizes),
+                       "max_points": max(sizes), "arrival_rate_per_s": 4, "budget_gb": budget / 2 ** 30,
+                       "piece_points": piece, "out_of_core_requests": len(ooc), "peak_in_flight": peak,
+                       "size_note": note,
+                       "l2": "inputs (%.1f GB) larger than L2" % (16 * total / 1e9)},
+            "served": {"time_to_preview_ms": {"p50": p50, "p99": serve.percentile(ttp, 0.99)},
+                       "time_to_full_octree_ms": {"p50": serve.percentile(ttf, 0.5),
+                                                  "p99": serve.percentile(ttf, 0.99)},
+                       "aggregate_gpts": served_rate / 1e9, "span_s": t_end - t0},
+            "saturated": {"aggregate_gpts": saturated_rate / 1e9, "peak_in_flight": speak,
+                          "span_s": s_end - s0},
+            "plain": {"aggregate_gpts": total / plain_s / 1e9, "span_s": plain_s,
+                      "note": "per cloud: copy in, the seven calls in core, one after another"},
+            "e2e": {"value": saturated_rate / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": 16 * total,
+                    "d2h_bytes_per_step": None},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def served_oracle_rate(sizes, seed0, wl, budget_s):
+    import oracle
+    import synth
+    _, _, _, g, s, lmax, T, C = wl
+    prm = oracle.params(g, s, lmax, 16, T, C)
+    i = min(range(len(sizes)), key=lambda k: sizes[k])
+    n = min(sizes[i], 2_000_000)
+    pts = synth.lidar(n, seed0 + i)
+    t0 = time.perf_counter()
+    oracle.build_all(pts, prm)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d points of the smallest request, %.1f s" % (n, dt)}
+
+
+def run_served_reference(args, wl, rank):
+    if rank != 0:
+        return
+    sizes, _ = served_plan(wl[1], wl[2])
+    cpu = served_oracle_rate(sizes, wl[2], wl, float(os.environ.get("FP_ORACLE_BUDGET_S", "12")))
+    line = {"impl": "reference", "metric": "served octree build throughput (Gpts/s)", "value": cpu["value"],
+            "unit": "Gpts/s", "n_gpus": args.gpus, "steps": 1, "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "requests": wl[1]}, "cpu_baseline": cpu,
+            "e2e": {"value": cpu["value"], "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,6 +592,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if wl[0] == "served":
+        if args.impl == "reference":
+            run_served_reference(args, wl, rank)
+        else:
+            run_served(args, wl, rank, world, local)
+        return
     if wl[0] == "batch":
         if args.impl == "reference":
             run_batched_reference(args, wl, rank)

@@ -12,6 +12,9 @@ memory budget:
   - in-core requests stream their points in pieces with cudaMemcpyAsync on a
     side stream and decimate each piece as it lands, so the preview is back in
     pinned host memory before the octree is built; then the plain calls run;
+  - an in-core request's octree (node table, final points and perm) stays on
+    the device; an out-of-core one is written to pinned host memory (one such
+    request at a time, in host buffers allocated when the server starts);
   - per request: time to preview and time to the full octree (from arrival),
     both taken on the host when the device work is done.
 Results do not depend on the mix: every request runs the same calls on its own
@@ -27,11 +30,12 @@ from . import fastpoints as fp
 
 
 class Request:
-    def __init__(self, rid, host_pts, prm):
+    def __init__(self, rid, host_pts, prm, preview_host=None):
         self.rid = rid
         self.host = host_pts            # (n, 4) int32, pinned
         self.n = host_pts.shape[0]
         self.prm = prm
+        self.preview_host = preview_host   # optional pinned (slots, 4) int32 buffer for the streamed preview
         self.arrival = None
         self.t_admit = self.t_preview = self.t_done = None
         self.mode = None
@@ -54,11 +58,21 @@ def _preview_slot_cap(p, m):
     return fp._preview_cap(p, m)
 
 
+def preview_slots_shape(n, piece, m):
+    """Rows of the pinned preview buffer of an in-core request."""
+    return max(1, (n + piece - 1) // piece) * _preview_slot_cap(piece, m), 4
+
+
 class Server:
-    def __init__(self, budget_bytes=24 << 30, piece_points=1 << 23, device=0):
+    def __init__(self, budget_bytes=24 << 30, piece_points=1 << 23, device=0, ooc_max_points=0, ooc_prm=None):
         self.budget = budget_bytes
         self.free = budget_bytes
         self.piece = piece_points
+        self.ooc_busy = False
+        self.ooc_bufs = None
+        if ooc_max_points:   # pinned host store and outputs of the out-of-core slot
+            self.ooc_bufs = (torch.empty(fp.ooc_host_bytes(ooc_max_points, ooc_prm), dtype=torch.uint8).pin_memory(),
+                             fp.ooc_outputs(ooc_max_points, ooc_prm))
         self.device = torch.device("cuda", device)
         self.cv = threading.Condition()
         self.queue = collections.deque()
@@ -88,12 +102,15 @@ class Server:
                 while True:
                     if self._stop and not self.queue:
                         return
-                    pick = next((r for r in self.queue if r.need <= self.free), None)
+                    pick = next((r for r in self.queue if r.need <= self.free and
+                                 (r.mode == "in-core" or not self.ooc_busy)), None)
                     if pick is not None:
                         break
                     self.cv.wait()
                 self.queue.remove(pick)
                 self.free -= pick.need
+                if pick.mode == "out-of-core":
+                    self.ooc_busy = True
                 self.active += 1
                 self.peak_active = max(self.peak_active, self.active)
             pick.t_admit = time.perf_counter()
@@ -104,6 +121,8 @@ class Server:
     def _release(self, req):
         with self.cv:
             self.free += req.need
+            if req.mode == "out-of-core":
+                self.ooc_busy = False
             self.active -= 1
             self.done.append(req)
             self.cv.notify_all()
@@ -143,7 +162,13 @@ class Server:
         def on_preview():
             req.t_preview = time.perf_counter()
 
-        out = fp.build_ooc(req.host, req.prm, arena, piece_points=self.piece, on_preview=on_preview, stream=st)
+        scratch, out = self.ooc_bufs if self.ooc_bufs is not None and self.ooc_bufs[1]["final"].shape[0] >= req.n \
+            else (None, None)
+        if out is not None:   # the slot's outputs sized for the largest cloud: node capacity of this one
+            out = dict(out, node_cap=fp.node_capacity_bound(req.n, req.prm),
+                       preview_cap=fp._preview_cap(req.n, req.prm.decim_modulus))
+        out = fp.build_ooc(req.host, req.prm, arena, piece_points=self.piece, scratch=scratch, out=out,
+                           on_preview=on_preview, stream=st)
         req.t_done = time.perf_counter()
         k = int(out["preview_count"].item())
         req.result = dict(preview=out["preview"][:k], nodes=out["nodes"][: int(out["num_nodes"].item())],
@@ -165,7 +190,7 @@ class Server:
         pcap = _preview_slot_cap(P, prm.decim_modulus)
         slots = torch.empty((max(npieces, 1) * pcap, 4), dtype=torch.int32, device=dev)
         slot_n = torch.zeros(max(npieces, 1), dtype=torch.int64, device=dev)
-        h_slots = torch.empty_like(slots, device="cpu").pin_memory()
+        h_slots = req.preview_host if req.preview_host is not None else torch.empty_like(slots, device="cpu").pin_memory()
         h_slot_n = torch.empty_like(slot_n, device="cpu").pin_memory()
         for k in range(npieces):
             a, b = k * P, min(n, (k + 1) * P)
@@ -177,23 +202,14 @@ class Server:
             fp._check(L.fp_decimate(fp._ptr(pts[a:b]), b - a, a, prm.decim_modulus, fp._ptr(slots[k * pcap:]), pcap,
                                     fp._ptr(slot_n[k:]), W, Wn, S), "fp_decimate")
         with torch.cuda.stream(st):
-            h_slots.copy_(slots, non_blocking=True)
+            h_slots[: slots.shape[0]].copy_(slots, non_blocking=True)
             h_slot_n.copy_(slot_n, non_blocking=True)
             ev_prev = torch.cuda.Event()
             ev_prev.record(st)
-        # the octree: the plain calls on the resident cloud
+        # the octree: the plain calls on the resident cloud; it stays on the device
         d = fp.cloud_desc(pts[:n], prm, out)
         fp.plain_calls(d, ws, stream=st)
-        M_dev = out["num_nodes"]
-        h = dict(nodes=torch.empty_like(out["nodes"], device="cpu").pin_memory(),
-                 num_nodes=torch.empty_like(M_dev, device="cpu").pin_memory(),
-                 final=torch.empty((max(n, 1), 4), dtype=torch.int32).pin_memory(),
-                 final_perm=torch.empty(max(n, 1), dtype=torch.int32).pin_memory())
         with torch.cuda.stream(st):
-            h["nodes"].copy_(out["nodes"], non_blocking=True)
-            h["num_nodes"].copy_(M_dev, non_blocking=True)
-            h["final"].copy_(out["final"], non_blocking=True)
-            h["final_perm"].copy_(out["final_perm"], non_blocking=True)
             ev_done = torch.cuda.Event()
             ev_done.record(st)
         ev_prev.synchronize()
@@ -203,9 +219,10 @@ class Server:
         counts = h_slot_n.tolist()
         prev = torch.cat([h_slots[k * pcap:k * pcap + int(c)] for k, c in enumerate(counts)]) if npieces else \
             torch.empty((0, 4), dtype=torch.int32)
-        M = int(h["num_nodes"].item())
-        req.result = dict(preview=prev, nodes=h["nodes"][:M], final=h["final"][:n], final_perm=h["final_perm"][:n])
-        del pts, out, ws, slots
+        M = int(out["num_nodes"].item())
+        req.result = dict(preview=prev, nodes=out["nodes"][:M], final=out["final"][:n],
+                          final_perm=out["final_perm"][:n])
+        del pts, ws, slots
 
 
 def percentile(xs, q):

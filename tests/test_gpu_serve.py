@@ -16,7 +16,7 @@ REQS = [("lidar", 120_000, 51), ("uniform", 60_000, 52), ("lidar", 250_000, 53),
 
 def results_equal(a, b):
     for k in ("preview", "nodes", "final", "final_perm"):
-        x, y = a[k].contiguous().view(torch.uint8), b[k].contiguous().view(torch.uint8)
+        x, y = a[k].cpu().contiguous().view(torch.uint8), b[k].cpu().contiguous().view(torch.uint8)
         if x.shape != y.shape or not torch.equal(x, y):
             return k
     return None
