@@ -12,7 +12,9 @@
 // level < g) are staged and merged across groups by one device sort.
 //
 // Passes over the host points (pieces of piece_points, double-buffered copies
-// on a side stream): bounds + preview, counts, then one per group.  The pinned
+// on a side stream): bounds + preview, counts, and the distribution into the
+// host store (each piece scattered by chunk at per-chunk cursors); then the
+// groups are read back from the store.  The pinned
 // host scratch is the out-of-core store between passes: the distributed points
 // and original indices of every group, the two levels and the owner of every
 // point, and the staged records.
@@ -62,34 +64,53 @@ __global__ void k_preview_append(const int4* prev, const uint64_t* cnt, int4* ou
 }
 
 __global__ void k_add_u64(uint64_t* run, const uint64_t* cnt) { *run += *cnt; }
-__global__ void k_add_u64_u32(uint64_t* run, const uint32_t* cnt) { *run += *cnt; }
 
-// 1 for the points of a piece whose chunk lies in [c0, c1)
-__global__ void k_group_flags(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
-                              uint32_t c0, uint32_t c1, uint32_t* flags)
+// points of a piece per chunk (warp-aggregated)
+__global__ void k_piece_hist(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
+                             uint32_t* pcnt)
 {
     const CubeDev c = load_cube(cube);
     const float sg = scale_at(c, g);
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const int4 p = ld_point(pts, i);
-        const uint32_t ch = __ldg(lut + key_small(p.x, p.y, p.z, c, sg, g));
-        flags[i] = ch >= c0 && ch < c1 ? 1u : 0u;
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        uint32_t ch = 0xFFFFFFFFu;
+        if (i < n) {
+            const int4 p = ld_point(pts, i);
+            ch = __ldg(lut + key_small(p.x, p.y, p.z, c, sg, g));
+        }
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, ch);
+        if (ch != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&pcnt[ch], (uint32_t)__popc(peers));
     }
 }
 
-// stable compaction of the flagged points after the group's earlier pieces
-__global__ void k_group_compact(const fp_point* pts, uint64_t n, const uint32_t* flags, const uint32_t* pos,
-                                uint64_t index_base, const uint64_t* cursor, uint64_t cap, int4* out,
-                                uint32_t* out_idx, uint32_t* err)
+// a piece scattered stably by chunk: its run of chunk c lands at the chunk's cursor
+// in the whole cloud's distributed order (host store)
+__global__ void k_piece_scatter(const int4* dpts, const uint32_t* dperm, uint64_t n, const fp_cube* cube, int g,
+                                const uint32_t* lut, const uint64_t* poff, const uint64_t* ccur, uint64_t base,
+                                int4* h_pts, uint32_t* h_perm, uint64_t n_all, uint32_t* err)
 {
-    const uint64_t cur = *cursor;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        if (!flags[i]) continue;
-        const uint64_t o = cur + pos[i];
-        if (o >= cap) { raise(err, FP_ERR_CAPACITY); continue; }
-        out[o] = ld_point(pts, i);
-        out_idx[o] = (uint32_t)(index_base + i);
+    const CubeDev c = load_cube(cube);
+    const float sg = scale_at(c, g);
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
+        const int4 p = dpts[q];
+        const uint32_t ch = __ldg(lut + key_small(p.x, p.y, p.z, c, sg, g));
+        const uint64_t dest = ccur[ch] + (q - poff[ch]);
+        if (dest >= n_all) { raise(err, FP_ERR_CAPACITY); continue; }
+        h_pts[dest] = p;
+        h_perm[dest] = (uint32_t)(base + dperm[q]);
     }
+}
+
+__global__ void k_cursor_init(const uint64_t* offsets, uint32_t K, uint64_t* ccur)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) ccur[c] = offsets[c];
+}
+
+__global__ void k_cursor_advance(uint64_t* ccur, const uint32_t* pcnt, uint32_t K)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) ccur[c] += pcnt[c];
 }
 
 // the group's points per cell (0 outside), chunk of a cell relative to c0, chunk offsets relative to the group
@@ -111,12 +132,6 @@ __global__ void k_group_offsets(const uint64_t* offsets, uint32_t c0, uint32_t k
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= k; i += gridDim.x * blockDim.x)
         off_local[i] = offsets[c0 + i] - b;
     if (blockIdx.x == 0 && threadIdx.x == 0) *kdev = k;
-}
-
-__global__ void k_compose(const uint32_t* perm_local, const uint32_t* idx, uint64_t n, uint32_t* perm)
-{
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        perm[i] = idx[perm_local[i]];
 }
 
 __global__ void k_owner_keys(const uint32_t* owner, uint64_t n, uint64_t* key)
@@ -228,15 +243,16 @@ struct Fixed {   // device buffers kept for the whole build
     fp_cube *cube, *piece_cube;
     uint32_t *counts, *lut, *num_chunks;
     fp_chunk* chunks;
-    uint64_t *offsets, *prev_run, *prev_cnt, *cursor, *st_run;
+    uint64_t *offsets, *prev_run, *prev_cnt, *st_run;
     int4* piece[2];
     int4* prev_buf;
-    uint32_t *flags, *pos, *total;
+    int4* dpiece;        // a piece scattered by chunk
+    uint32_t *dperm, *pcnt;
+    uint64_t *poff, *ccur;
     NodeRec* recs;
     fp_node* nodes;
     uint32_t *num_deep, *num_nodes, *nm, *soff;
     uint64_t *first, *tiles64;
-    uint32_t* tiles32;
     NodeTables T;
     uint32_t *rcounts, *lut_local, *kdev;
     uint64_t* off_local;
@@ -255,14 +271,15 @@ Fixed fixed_carve(const Workspace& w, uint64_t P, const fp_params& p, uint64_t n
     F.offsets = w.take<uint64_t>(cells + 1);
     F.prev_run = w.take<uint64_t>(1);
     F.prev_cnt = w.take<uint64_t>(1);
-    F.cursor = w.take<uint64_t>(1);
     F.st_run = w.take<uint64_t>(1);
     F.piece[0] = w.take<int4>(P);
     F.piece[1] = w.take<int4>(P);
     F.prev_buf = w.take<int4>(preview_piece_cap(P, p.decim_modulus) + 1);
-    F.flags = w.take<uint32_t>(P);
-    F.pos = w.take<uint32_t>(P);
-    F.total = w.take<uint32_t>(1);
+    F.dpiece = w.take<int4>(P);
+    F.dperm = w.take<uint32_t>(P);
+    F.pcnt = w.take<uint32_t>(cells);
+    F.poff = w.take<uint64_t>(cells + 1);
+    F.ccur = w.take<uint64_t>(cells);
     F.recs = reinterpret_cast<NodeRec*>(w.take<unsigned char>(kNodeRecBytes * node_cap));
     F.nodes = w.take<fp_node>(node_cap);
     F.num_deep = w.take<uint32_t>(1);
@@ -271,7 +288,6 @@ Fixed fixed_carve(const Workspace& w, uint64_t P, const fp_params& p, uint64_t n
     F.soff = w.take<uint32_t>(node_cap);
     F.first = w.take<uint64_t>(node_cap + 1);
     F.tiles64 = w.take<uint64_t>(kScanMaxTiles);
-    F.tiles32 = w.take<uint32_t>(kScanMaxTiles);
     F.T.idxtab = w.take<uint32_t>(cells * 8 / 7 + 8);
     F.T.starts = w.take<uint64_t>(node_cap);
     F.T.slevel = w.take<uint8_t>(node_cap);
@@ -287,8 +303,8 @@ Fixed fixed_carve(const Workspace& w, uint64_t P, const fp_params& p, uint64_t n
 }
 
 struct Group {   // device buffers of one chunk group (G points), reused group after group
-    int4 *in, *pts;
-    uint32_t *idx, *perm_local, *perm, *owner;
+    int4* pts;      // first: the start of the group region
+    uint32_t *perm, *owner;
     uint8_t *own, *leaf;
     uint64_t *key, *key2, *key3;
     uint32_t *val2, *val3;
@@ -298,7 +314,7 @@ struct Group {   // device buffers of one chunk group (G points), reused group a
 
 size_t stage_ws(uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
 {
-    size_t w = std::max(distribute_ws_bytes(G, (int)p.grid_log2), octree_ws_bytes(G, p));
+    size_t w = std::max(distribute_ws_bytes(P, (int)p.grid_log2), octree_ws_bytes(G, p));
     w = std::max(w, bounds_ws_bytes(P, num_sms));
     w = std::max(w, merge_ws_bytes((int)p.grid_log2));
     w = std::max(w, nodes_ws_bytes(p, node_cap));
@@ -310,10 +326,7 @@ Group group_carve(const Workspace& w, uint64_t G, uint64_t P, const fp_params& p
 {
     Group g;
     const uint64_t N = G ? G : 1;
-    g.in = w.take<int4>(N);
     g.pts = w.take<int4>(N);
-    g.idx = w.take<uint32_t>(N);
-    g.perm_local = w.take<uint32_t>(N);
     g.perm = w.take<uint32_t>(N);
     g.owner = w.take<uint32_t>(N);
     g.own = w.take<uint8_t>(N);
@@ -490,37 +503,38 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         c0 = c1;
     }
 
-    // ---- pass 3 per group: its points (distributed), levels, nodes below level g
+    // ---- pass 3: the whole cloud in distributed order into the host store.  Each
+    // piece is scattered stably by chunk on the device; its run of every chunk
+    // lands after the earlier pieces' points of that chunk (a cursor per chunk).
+    const unsigned gK = grid_for(K, base.num_sms);
+    k_cursor_init<<<gK, 256, 0, st>>>(F.offsets, K, F.ccur);
+    e = io.pass([&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
+        cudaError_t x;
+        if ((x = cudaMemsetAsync(F.pcnt, 0, (size_t)K * sizeof(uint32_t), st))) return x;
+        k_piece_hist<<<grid_for(np, base.num_sms), 256, 0, st>>>(p, np, F.cube, g, F.lut, F.pcnt);
+        if ((x = scan_exclusive<uint32_t, uint64_t>(F.pcnt, F.poff, K, nullptr, F.tiles64, F.poff + K,
+                                                    (uint64_t*)nullptr, st)))
+            return x;
+        ws.used = 0;
+        if ((x = launch_distribute(p, np, F.cube, g, F.lut, F.poff, F.num_chunks, reinterpret_cast<fp_point*>(F.dpiece),
+                                   F.dperm, ws, st)))
+            return x;
+        k_piece_scatter<<<grid_for(np, base.num_sms), 256, 0, st>>>(F.dpiece, F.dperm, np, F.cube, g, F.lut, F.poff,
+                                                                    F.ccur, k * P, H.pts, H.perm, n, base.err);
+        k_cursor_advance<<<gK, 256, 0, st>>>(F.ccur, F.pcnt, K);
+        return cudaGetLastError();
+    });
+    if (e) return cu(e);
+
+    // ---- per group: its points from the store; levels and nodes below level g
     if ((e = cudaMemsetAsync(F.num_deep, 0, sizeof(uint32_t), st))) return cu(e);
     const unsigned gc = grid_for(cells, base.num_sms);
-    auto gather = [&](uint32_t c0, uint32_t c1, uint64_t ng) -> cudaError_t {
-        cudaError_t x;
-        k_group_tables<<<gc, 256, 0, st>>>(F.counts, F.lut, cells, c0, c1, F.rcounts, F.lut_local);
-        k_group_offsets<<<gc, 256, 0, st>>>(F.offsets, c0, c1 - c0, F.off_local, F.kdev);
-        if ((x = cudaMemsetAsync(F.cursor, 0, sizeof(uint64_t), st))) return x;
-        x = io.pass([&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
-            k_group_flags<<<grid_for(np, base.num_sms), 256, 0, st>>>(p, np, F.cube, g, F.lut, c0, c1, F.flags);
-            cudaError_t y = scan_exclusive<uint32_t, uint32_t>(F.flags, F.pos, np, nullptr, F.tiles32, F.total,
-                                                               (uint32_t*)nullptr, st);
-            if (y) return y;
-            k_group_compact<<<grid_for(np, base.num_sms), 256, 0, st>>>(p, np, F.flags, F.pos, k * P, F.cursor, G,
-                                                                        B.in, B.idx, base.err);
-            k_add_u64_u32<<<1, 1, 0, st>>>(F.cursor, F.total);
-            return cudaGetLastError();
-        });
-        if (x) return x;
-        ws.used = 0;
-        if ((x = launch_distribute(reinterpret_cast<const fp_point*>(B.in), ng, F.cube, g, F.lut_local, F.off_local,
-                                   F.kdev, reinterpret_cast<fp_point*>(B.pts), B.perm_local, ws, st)))
-            return x;
-        k_compose<<<grid_for(ng, base.num_sms), 256, 0, st>>>(B.perm_local, B.idx, ng, B.perm);
-        return cudaGetLastError();
-    };
     for (auto [c0, c1] : groups) {
         const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
-        if ((e = gather(c0, c1, ng))) return cu(e);
-        if ((e = cudaMemcpyAsync(H.pts + b0, B.pts, ng * 16, cudaMemcpyDeviceToHost, st))) return cu(e);
-        if ((e = cudaMemcpyAsync(H.perm + b0, B.perm, ng * 4, cudaMemcpyDeviceToHost, st))) return cu(e);
+        k_group_tables<<<gc, 256, 0, st>>>(F.counts, F.lut, cells, c0, c1, F.rcounts, F.lut_local);
+        k_group_offsets<<<gc, 256, 0, st>>>(F.offsets, c0, c1 - c0, F.off_local, F.kdev);
+        if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(B.perm, H.perm + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
         OctGroup grp{F.rcounts, (uint32_t)b0, B.own, B.leaf, F.recs, node_cap, F.num_deep};
         ws.used = 0;
         if ((e = launch_octree_impl(reinterpret_cast<const fp_point*>(B.pts), B.perm, ng, F.cube, F.chunks + c0,
@@ -590,7 +604,7 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     if ((e = cudaStreamSynchronize(st))) return cu(e);
     if (S) {   // the sort of the staged records reuses the whole group region
         Workspace wf = base;
-        wf.base = reinterpret_cast<char*>(B.in);
+        wf.base = reinterpret_cast<char*>(B.pts);
         wf.bytes = group_bytes(G, P, prm, node_cap, base.num_sms);
         wf.used = 0;
         uint64_t* k1 = wf.take<uint64_t>(S);

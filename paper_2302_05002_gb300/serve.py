@@ -7,14 +7,15 @@ memory budget:
     free budget (first fit in arrival order), so requests that arrive while
     others run are built alongside them (each on its own CUDA stream; their
     kernels overlap on the device);
-  - a cloud whose in-core need exceeds half the budget is built out of core
-    (fp_build_ooc) in an arena of half the budget;
+  - a cloud whose in-core need exceeds three quarters of the budget is built
+    out of core (fp_build_ooc) in an arena of half the budget;
   - in-core requests stream their points in pieces with cudaMemcpyAsync on a
     side stream and decimate each piece as it lands, so the preview is back in
     pinned host memory before the octree is built; then the plain calls run;
   - an in-core request's octree (node table, final points and perm) stays on
-    the device; an out-of-core one is written to pinned host memory (one such
-    request at a time, in host buffers allocated when the server starts);
+    the device; an out-of-core one is written to pinned host memory (at most
+    `ooc_slots` such requests at a time, each in its own host buffers,
+    allocated when the server starts);
   - per request: time to preview and time to the full octree (from arrival),
     both taken on the host when the device work is done.
 Results do not depend on the mix: every request runs the same calls on its own
@@ -40,6 +41,7 @@ class Request:
         self.t_admit = self.t_preview = self.t_done = None
         self.mode = None
         self.need = 0
+        self.slot = None
         self.result = None
         self.error = None
 
@@ -64,15 +66,16 @@ def preview_slots_shape(n, piece, m):
 
 
 class Server:
-    def __init__(self, budget_bytes=24 << 30, piece_points=1 << 23, device=0, ooc_max_points=0, ooc_prm=None):
+    def __init__(self, budget_bytes=24 << 30, piece_points=1 << 23, device=0, ooc_max_points=0, ooc_prm=None,
+                 ooc_slots=2):
         self.budget = budget_bytes
         self.free = budget_bytes
         self.piece = piece_points
-        self.ooc_busy = False
-        self.ooc_bufs = None
-        if ooc_max_points:   # pinned host store and outputs of the out-of-core slot
-            self.ooc_bufs = (torch.empty(fp.ooc_host_bytes(ooc_max_points, ooc_prm), dtype=torch.uint8).pin_memory(),
-                             fp.ooc_outputs(ooc_max_points, ooc_prm))
+        self.ooc_slots = ooc_slots
+        self.ooc_free = []   # pinned host store and outputs of every out-of-core slot (None: allocated per request)
+        for _ in range(ooc_slots):
+            self.ooc_free.append((torch.empty(fp.ooc_host_bytes(ooc_max_points, ooc_prm), dtype=torch.uint8)
+                                  .pin_memory(), fp.ooc_outputs(ooc_max_points, ooc_prm)) if ooc_max_points else None)
         self.device = torch.device("cuda", device)
         self.cv = threading.Condition()
         self.queue = collections.deque()
@@ -87,7 +90,7 @@ class Server:
     # ---- admission
     def submit(self, req):
         req.arrival = time.perf_counter()
-        if incore_need(req.n, req.prm) <= self.budget // 2:
+        if incore_need(req.n, req.prm) <= self.budget * 3 // 4:
             req.mode, req.need = "in-core", incore_need(req.n, req.prm)
         else:
             req.mode, req.need = "out-of-core", self.budget // 2
@@ -103,14 +106,14 @@ class Server:
                     if self._stop and not self.queue:
                         return
                     pick = next((r for r in self.queue if r.need <= self.free and
-                                 (r.mode == "in-core" or not self.ooc_busy)), None)
+                                 (r.mode == "in-core" or self.ooc_free)), None)
                     if pick is not None:
                         break
                     self.cv.wait()
                 self.queue.remove(pick)
                 self.free -= pick.need
                 if pick.mode == "out-of-core":
-                    self.ooc_busy = True
+                    pick.slot = self.ooc_free.pop()
                 self.active += 1
                 self.peak_active = max(self.peak_active, self.active)
             pick.t_admit = time.perf_counter()
@@ -122,7 +125,7 @@ class Server:
         with self.cv:
             self.free += req.need
             if req.mode == "out-of-core":
-                self.ooc_busy = False
+                self.ooc_free.append(req.slot)
             self.active -= 1
             self.done.append(req)
             self.cv.notify_all()
@@ -162,8 +165,7 @@ class Server:
         def on_preview():
             req.t_preview = time.perf_counter()
 
-        scratch, out = self.ooc_bufs if self.ooc_bufs is not None and self.ooc_bufs[1]["final"].shape[0] >= req.n \
-            else (None, None)
+        scratch, out = req.slot if req.slot is not None and req.slot[1]["final"].shape[0] >= req.n else (None, None)
         if out is not None:   # the slot's outputs sized for the largest cloud: node capacity of this one
             out = dict(out, node_cap=fp.node_capacity_bound(req.n, req.prm),
                        preview_cap=fp._preview_cap(req.n, req.prm.decim_modulus))

@@ -35,7 +35,7 @@ def test_served_alone_mixed_plain(gpu_lib):
     piece = 1 << 18
     # the out-of-core arena (half the budget) holds the largest request's minimum; the others fit in core
     budget = 2 * max(max(needs[:-1]), fp.ooc_arena_min(hosts[-1].shape[0], prm, piece)) + (1 << 20)
-    assert needs[-1] > budget // 2, "the largest request must go out of core"
+    assert needs[-1] > budget * 3 // 4, "the largest request must go out of core"
 
     # plain, in core
     plain = []
