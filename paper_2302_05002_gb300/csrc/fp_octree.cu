@@ -368,15 +368,32 @@ struct UnitSmem {
     uint16_t psrt[kWindow + 1]; // start of each piece in the unit (load order = sorted order)
     uint8_t pq[kWindow + 1], phier[kWindow + 1], pA[kWindow + 1], pkind[kWindow + 1];
     uint16_t pn[kWindow + 1];   // points of the piece (0 for an oversized one)
+    uint16_t ptab[kWindow + 1]; // table pieces: first entry of the piece's level tables
+    uint16_t pfst[kWindow + 1]; // table pieces: start of the piece's records in the table phase
+    uint8_t pD[kWindow + 1];    // table pieces: levels below the piece that decide lambda
+    uint32_t pmin[kWindow + 1]; // table pieces: smallest index of the piece
     uint16_t whist[kUnitWarps][256];
     uint32_t scan[64];
     uint64_t wmin[kUnitWarps], wmax[kUnitWarps];
     unsigned long long kmin, kmax;
-    uint32_t np, cnt, p0, dl, nh, smin;
+    uint32_t np, cnt, p0, dl, nh, smin, fcnt, tabn;
 };
 
 // two units per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
 static_assert(sizeof(UnitSmem) <= 113 * 1024, "UnitSmem must leave room for two CTAs per SM");
+
+// Table pieces.  A piece whose node is not inner needs lambda only at the
+// levels q+1 .. dl of the piece (coarser: the piece minimum's rule; deeper: the
+// leaf).  When there are at most kTabLevels of them, one direct-mapped table
+// per level (8^d entries at q+d) takes the smallest index of every occupied
+// cell by shared-memory atomicMin, and lambda of a record is the shallowest of
+// those levels at which it is its cell's minimum -- no sort and no
+// nearest-smaller search.  The tables overlay the arrays of the general path
+// (key .. v2), which runs after them.
+constexpr int kTabLevels = 4;
+constexpr int kTabCap = (int)((offsetof(UnitSmem, piece) - offsetof(UnitSmem, key)) / sizeof(uint32_t));
+static_assert(kTabCap >= 3 * 4680, "tables of three pieces of four levels");
+FP_DEV uint32_t tab_size(int D) { return D <= 0 ? 0u : (uint32_t)(((1u << (3 * (D + 1))) - 8u) / 7u); }
 
 // stable LSD pass over the unit's records by 8 key bits at `shift`
 FP_DEV void unit_sort_pass(UnitSmem& S, const uint64_t* kin, const uint16_t* vin, uint64_t* kout, uint16_t* vout,
@@ -442,6 +459,18 @@ FP_DEV int piece_of(const UnitSmem& S, int np, int r)
     return a - 1;
 }
 
+// last piece whose table-phase start is <= r
+FP_DEV int piece_of_tab(const UnitSmem& S, int np, int r)
+{
+    int a = 0, b = np;
+    while (a < b) {
+        int m = (a + b) >> 1;
+        if ((int)S.pfst[m] <= r) a = m + 1;
+        else b = m;
+    }
+    return a - 1;
+}
+
 // One CTA per window of kWindow record positions: the pieces starting in it.
 // Per unit:
 //   sort the records by key (stable, 8-bit LSD passes in shared memory);
@@ -482,12 +511,14 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
         const int np = (int)S.np;
         // piece descriptors.  Pieces of one point need nothing but their minimum
         // rule; pieces of at most 32 points are handled by one warp with
-        // shuffles; larger pieces (and pieces whose node is still inner) go
-        // through the shared-memory sort.  A block scan places the large ones.
+        // shuffles; pieces whose lambda is decided within kTabLevels levels
+        // take the table path while the tables fit; the other pieces (and
+        // pieces whose node is still inner) go through the shared-memory sort.
+        // Block scans place the tables and the records of both paths.
         {
             constexpr int per = (kWindow + kUnitNT - 1) / kUnitNT;
-            uint32_t cn[per], po[per];
-            uint32_t sum = 0, dmax = 0, smin = 255;
+            uint32_t po[per], tz[per];
+            uint32_t tsum = 0;
 #pragma unroll
             for (int q = 0; q < per; ++q) {   // both levels of loads issued before use
                 const int pi = threadIdx.x * per + q;
@@ -499,27 +530,51 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
                 if ((int)threadIdx.x * per + q < np) pr[q] = c.pieces[po[q]];
 #pragma unroll
             for (int q = 0; q < per; ++q) {
-                int pi = threadIdx.x * per + q;
-                cn[q] = 0;
+                const int pi = threadIdx.x * per + q;
+                tz[q] = 0xFFFFFFFFu;   // not a table candidate
                 if (pi < np) {
                     const Piece p = pr[q];
                     S.pbeg[pi] = p.begin;
                     S.pq[pi] = p.q;
                     S.phier[pi] = p.hier;
                     S.pA[pi] = p.A;
+                    S.pn[pi] = (uint16_t)(p.dup ? 0 : p.count);
                     const bool large = !p.dup && (p.count > 32 || p.hier == kInner);
                     S.pkind[pi] = p.dup ? 3 : (large ? 2 : (p.count == 1 ? 0 : 1));
-                    S.pn[pi] = (uint16_t)(p.dup ? 0 : p.count);
-                    cn[q] = large ? p.count : 0u;
-                    S.pcnt[pi] = (uint16_t)cn[q];
-                    if (large) {
+                    if (large && p.hier != kInner) {
+                        const int D = min(kKeyLevels, c.s + (int)p.hier - 1) - (int)p.q;
+                        if (D <= kTabLevels) {
+                            tz[q] = tab_size(D);
+                            S.pD[pi] = (uint8_t)max(D, 0);
+                            tsum += tz[q];
+                        }
+                    }
+                }
+            }
+            uint32_t ttot;
+            uint32_t tex = block_exclusive_scan<kUnitNT, uint32_t>(min(tsum, (uint32_t)kTabCap + 1u), S.scan, ttot);
+            uint32_t cn[per], fn[per];
+            uint32_t sum = 0, dmax = 0, smin = 255;
+#pragma unroll
+            for (int q = 0; q < per; ++q) {
+                const int pi = threadIdx.x * per + q;
+                cn[q] = fn[q] = 0;
+                if (pi < np && S.pkind[pi] == 2) {
+                    const Piece p = pr[q];
+                    if (tz[q] != 0xFFFFFFFFu && tex + tz[q] <= (uint32_t)kTabCap) {
+                        S.pkind[pi] = 4;
+                        S.ptab[pi] = (uint16_t)tex;
+                        fn[q] = p.count;
+                    } else {
+                        cn[q] = p.count;
                         uint32_t d = p.hier == kInner ? (uint32_t)c.dl
                                                       : (uint32_t)min(kKeyLevels, c.s + (int)p.hier - 1);
                         dmax = max(dmax, d);
                         smin = min(smin, (uint32_t)p.srt);
                     }
                 }
-                sum += cn[q];
+                if (tz[q] != 0xFFFFFFFFu) tex += tz[q];
+                sum += cn[q] | (fn[q] << 16);
             }
             dmax = __reduce_max_sync(0xFFFFFFFFu, dmax);
             smin = __reduce_min_sync(0xFFFFFFFFu, smin);
@@ -529,10 +584,18 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
             uint32_t ex = block_exclusive_scan<kUnitNT, uint32_t>(sum, S.scan, tot);
             for (int q = 0; q < per; ++q) {
                 int pi = threadIdx.x * per + q;
-                if (pi < np) S.psrt[pi] = (uint16_t)ex;
-                ex += cn[q];
+                if (pi < np) {
+                    S.psrt[pi] = (uint16_t)(ex & 0xFFFFu);
+                    S.pcnt[pi] = (uint16_t)cn[q];
+                    S.pfst[pi] = (uint16_t)(ex >> 16);
+                }
+                ex += cn[q] | (fn[q] << 16);
             }
-            if (threadIdx.x == 0) S.cnt = tot;
+            if (threadIdx.x == 0) {
+                S.cnt = tot & 0xFFFFu;
+                S.fcnt = tot >> 16;
+                S.tabn = min(ttot, (uint32_t)kTabCap);
+            }
         }
         __syncthreads();
         // ---- pieces of one point: the point is its piece's minimum
@@ -569,6 +632,70 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
                 c.own_code[jj] = (uint8_t)K;
                 c.leaf_code[jj] = (uint8_t)leafl;
             }
+        }
+        // ---- table pieces: per-level smallest index of every occupied cell
+        if (S.fcnt) {
+            const int fcnt = (int)S.fcnt;
+            uint32_t* tab = reinterpret_cast<uint32_t*>(S.key);
+            const int tabn4 = (int)((S.tabn + 3u) >> 2);
+            for (int x = threadIdx.x; x < tabn4; x += kUnitNT)
+                reinterpret_cast<uint4*>(tab)[x] = make_uint4(kNone, kNone, kNone, kNone);
+            for (int pi = threadIdx.x; pi < np; pi += kUnitNT)
+                if (S.pkind[pi] == 4) S.pmin[pi] = kNone;
+            constexpr int kPer = kUnitCap / kUnitNT;
+            uint32_t gi[kPer], jq[kPer];
+            uint64_t kq[kPer];
+            int pp[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int r = threadIdx.x + q * kUnitNT;
+                pp[q] = -1;
+                gi[q] = 0;
+                if (r < fcnt) {
+                    pp[q] = piece_of_tab(S, np, r);
+                    gi[q] = S.pbeg[pp[q]] + (uint32_t)(r - S.pfst[pp[q]]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q)   // all loads in flight together
+                if (pp[q] >= 0) { kq[q] = c.gk[gi[q]]; jq[q] = c.gj[gi[q]]; }
+            __syncthreads();   // tables cleared
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                if (pp[q] < 0) continue;
+                const int pi = pp[q], D = S.pD[pi], q0 = S.pq[pi];
+                atomicMin(&S.pmin[pi], jq[q]);
+                uint32_t off = S.ptab[pi];
+                for (int d = 1; d <= D; ++d) {
+                    const uint32_t idx = (uint32_t)(kq[q] >> (3 * (kKeyLevels - q0 - d))) & ((1u << (3 * d)) - 1u);
+                    atomicMin(&tab[off + idx], jq[q]);
+                    off += 1u << (3 * d);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                if (pp[q] < 0) continue;
+                const int pi = pp[q], D = S.pD[pi], q0 = S.pq[pi];
+                int lambda = kKeyLevels + 1;   // never its cell's minimum down to the piece's depth
+                if (jq[q] == S.pmin[pi]) {
+                    lambda = S.pA[pi];           // the piece minimum: from the split tree
+                } else {
+                    uint32_t off = S.ptab[pi];
+                    for (int d = 1; d <= D; ++d) {
+                        const uint32_t idx =
+                            (uint32_t)(kq[q] >> (3 * (kKeyLevels - q0 - d))) & ((1u << (3 * d)) - 1u);
+                        if (tab[off + idx] == jq[q]) { lambda = q0 + d; break; }
+                        off += 1u << (3 * d);
+                    }
+                }
+                const int leafl = S.phier[pi];
+                int K = lambda - c.s;
+                K = K < 0 ? 0 : (K > leafl ? leafl : K);
+                c.own_code[jq[q]] = (uint8_t)K;
+                c.leaf_code[jq[q]] = (uint8_t)leafl;
+            }
+            __syncthreads();   // the tables overlay the general path's arrays
         }
         const int cnt = (int)S.cnt;
         if (cnt == 0) { __syncthreads(); continue; }

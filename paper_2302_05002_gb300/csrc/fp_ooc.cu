@@ -452,7 +452,6 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     ws.bytes = B.ws_bytes;
     ws.used = 0;
     const HostStore H = host_carve(h_scratch, n);
-    const uint32_t* err = base.err;
     cudaError_t e;
     if ((e = io.init(st, h_pts, n, P, F.piece[0], F.piece[1]))) return FP_ERR_CUDA;
 
@@ -630,7 +629,6 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     }
     if ((e = cudaMemcpyAsync(h_nodes, F.nodes, (size_t)M * sizeof(fp_node), cudaMemcpyDeviceToHost, st))) return cu(e);
     if ((e = cudaMemcpyAsync(h_num_nodes, F.num_nodes, sizeof(uint32_t), cudaMemcpyDeviceToHost, st))) return cu(e);
-    (void)err;
     return cu(cudaStreamSynchronize(st));
 }
 

@@ -83,6 +83,8 @@ CASES = [
     ("lidar", 100_000, 4, 4, 5, 12, 3_000, 300),
     ("clustered", 120_000, 5, 5, 6, 16, 4_000, 500),         # one dense blob: split tree, pieces
     ("dups", 50_000, 6, 3, 3, 9, 1_000, 40),                 # identical points: oversized leaves
+    ("uniform", 2_000_000, 14, 5, 6, 8, 50_000, 2_000),      # leaves above the cells: level tables, 4 levels
+    ("uniform", 1_500_000, 15, 5, 5, 9, 40_000, 2_000),      # ... 3 levels, many tables per unit
     ("uniform", 5_000, 7, 2, 2, 20, 100, 10),
     ("uniform", 1, 8, 7, 7, 15, 100, 10),
     ("uniform", 3, 9, 1, 1, 21, 1, 1),
