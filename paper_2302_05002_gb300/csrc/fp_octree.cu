@@ -15,8 +15,9 @@
 // per level-g cell.  Inside a chunk the distributed order is index order.
 //
 // Steps:
-//   1. group the distributed points by level-g cell (stable scatter: records
-//      (key21, j) with j the position in the chunk array, i.e. index order);
+//   1. group the distributed points by level-g cell (records (key21, j) with j
+//      the position in the chunk array, i.e. index order; any order inside a
+//      cell);
 //   2. cells with more than kPieceMax points are key-sorted and cut into
 //      node-aligned pieces of at most kPieceMax points (split tree, one warp per
 //      open node); the split tree also gives the nodes between level g and the
@@ -143,6 +144,66 @@ FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, u
 }
 
 // ---------------------------------------------------------------- cells
+// Records (key21, j) grouped by level-g cell, j = position in the chunk array:
+// cell m's records fill [cstart[m], cstart[m] + rcounts[m]) in any order --
+// every later step is independent of the order inside a cell (minima are
+// reductions, keys are sorted where their order matters).  One pass over the
+// points; the lanes of a warp that share a cell take their slots with one
+// atomic on the cell's cursor, which starts at cstart[m].  The points arrive
+// chunk by chunk, so the cells in use at any time are consecutive: cursors sit
+// at bit-reversed cell ids, which spreads those atomics over the whole array
+// (and every L2 slice).  A cursor that does not end at cstart[m + 1] means the
+// count grid was not the grid of these points (reported by k_cell_check).
+FP_DEV uint32_t cursor_slot(uint32_t m, int g) { return __brev(m) >> (32 - 3 * g); }
+
+__global__ void k_cell_cursor_init(const uint32_t* __restrict__ cstart, uint64_t cells, uint32_t* cursor, int g,
+                                   const uint32_t* run_if)
+{
+    if (!*run_if) return;
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x)
+        cursor[cursor_slot((uint32_t)m, g)] = cstart[m];
+}
+
+__global__ void __launch_bounds__(256) k_cell_scatter(const int4* __restrict__ pts, uint64_t n, const fp_cube* cube_p,
+                                                      uint32_t* cursor, uint64_t* __restrict__ gk,
+                                                      uint32_t* __restrict__ gj, int g, const uint32_t* run_if,
+                                                      uint32_t* err)
+{
+    if (!*run_if) return;
+    const CubeDev cube = load_cube(cube_p);
+    const int lane = threadIdx.x & 31;
+    const int sh = 3 * (kKeyLevels - g);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {   // warp-uniform trip count
+        const uint64_t i = i0 + threadIdx.x;
+        uint64_t k = 0;
+        uint32_t m = kNone;
+        if (i < n) {
+            const int4 q = __ldg(pts + i);
+            k = key21(q.x, q.y, q.z, cube);
+            m = (uint32_t)(k >> sh);
+        }
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, m);
+        const int leader = __ffs(peers) - 1;
+        uint32_t at = 0;
+        if (lane == leader && m != kNone) at = atomicAdd(&cursor[cursor_slot(m, g)], (uint32_t)__popc(peers));
+        at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
+        if (m != kNone) {
+            if (at >= n) { raise(err, FP_ERR_CAPACITY); continue; }   // a count grid of other points
+            gk[at] = k;
+            gj[at] = (uint32_t)i;
+        }
+    }
+}
+
+__global__ void k_cell_check(const uint32_t* __restrict__ cstart, uint64_t cells, const uint32_t* cursor, int g,
+                             const uint32_t* run_if, uint32_t* err)
+{
+    if (!*run_if) return;
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x)
+        if (cursor[cursor_slot((uint32_t)m, g)] != cstart[m + 1]) raise(err, FP_ERR_CAPACITY);
+}
+
 // Per level-g cell: leaf level if the hierarchy ends at or above g, kInner if
 // the cell node is inner, kEmpty for an empty cell.  Nonempty cells with at
 // most kPieceMax points become pieces; larger ones open the split tree.
@@ -250,6 +311,15 @@ __global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uin
     if (i >= cap) return;
     const bool skip = d_skip && *d_skip > skip_min;
     cnt_out[i] = i < *nopen0 && !skip ? open0[i].count : 0;
+}
+
+// a one-pass plan: the deeper grouping's passes (selected over it when it runs) or none
+__global__ void k_plan_one(SortPlan* p)
+{
+    p->npass = 1;
+    p->bits = kSortMaxBits;
+    p->shift0 = 0;
+    p->pad = 0;
 }
 
 __global__ void k_deep_flag(const uint64_t* bigsum, uint64_t min_sum, uint32_t* flag)
@@ -931,16 +1001,25 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* 
 
 // oversized pieces (more than kPieceMax identical keys down to the deepest
 // needed level): only their first record, the smallest index, can be a minimum
-__global__ void k_dup_pieces(OctCtx c)
+__global__ void __launch_bounds__(256) k_dup_pieces(OctCtx c)
 {
+    __shared__ uint32_t s_min[8];
     const uint32_t nd = *c.ndups < c.piece_cap ? *c.ndups : c.piece_cap;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t k = blockIdx.x; k < nd; k += gridDim.x) {
         const Piece p = c.pieces[c.dups[k]];
         const int leafl = p.hier == kInner ? c.lmax : (int)p.hier;
+        uint32_t mn = kNone;
+        for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) mn = min(mn, c.gj[p.begin + r]);
+        mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+        if (lane == 0) s_min[warp] = mn;
+        __syncthreads();
+        mn = s_min[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mn = min(mn, s_min[w]);
         for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) {
             uint32_t jj = c.gj[p.begin + r];
             int K = leafl;
-            if (r == 0) {
+            if (jj == mn) {
                 K = (int)p.A - c.s;
                 if (K < 0) K = 0;
                 if (K > leafl) K = leafl;
@@ -948,6 +1027,7 @@ __global__ void k_dup_pieces(OctCtx c)
             c.own_code[jj] = (uint8_t)K;
             c.leaf_code[jj] = (uint8_t)leafl;
         }
+        __syncthreads();
     }
 }
 
@@ -1158,7 +1238,7 @@ struct OctBufs {
     uint32_t *t_j1, *t_j2, *t_j3;
     int4* lt_pt;
     uint32_t *lt_val, *lt_k32;
-    uint32_t *pyr, *cstart;
+    uint32_t *pyr, *cstart, *cursor;
     uint8_t* cell_leaf;
     uint64_t* gk;
     uint32_t* gj;
@@ -1201,6 +1281,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     ws.used = std::max(phase_end, ws.used);
     B.pyr = ws.take<uint32_t>(Ly.npyr ? Ly.npyr : 1);
     B.cstart = ws.take<uint32_t>(Ly.cells + 1);
+    B.cursor = ws.take<uint32_t>(Ly.cells);
     B.cell_leaf = ws.take<uint8_t>(Ly.cells);
     B.gk = ws.take<uint64_t>(N); B.gj = ws.take<uint32_t>(N);
     B.pieces = ws.take<Piece>(Ly.piece_cap);
@@ -1358,33 +1439,34 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     c.open_cap = (uint32_t)Ly.open_cap;
     c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
 
-    // 2. group by level-g cell: stable scatter of (key21, j) by cell id.  When
-    // more than a third of the points lie in cells of more than kPieceMax points,
-    // sorting all records down to level g + r1 instead (two more passes over n)
-    // is cheaper than the first split round's gather, sort and scatter of them,
-    // and that round then has nothing to do.
+    // 2. group by level-g cell: (key21, j) scattered by cell id.  When more
+    // than a third of the points lie in cells of more than kPieceMax points,
+    // sorting all records down to level g + r1 instead (stable key passes)
+    // is cheaper than the first split round's gather, sort and scatter of
+    // them, and that round then has nothing to do.
     {
         if ((e = cudaMemsetAsync(B.bigsum, 0, sizeof(uint64_t), st))) return e;
         k_big_sum<<<std::max(1, std::min(ws.num_sms * 4, (int)((Ly.cells + 255) / 256))), 256, 0, st>>>(
             rcounts, Ly.cells, B.bigsum);
         k_deep_flag<<<1, 1, 0, st>>>(B.bigsum, r1 > 0 ? N / 3 : ~0ull, B.deep);
-        if ((e = sort_plan_weights(sc, rcounts, nullptr, nullptr, Ly.cells, 3 * (kKeyLevels - g), st))) return e;
+        k_plan_one<<<1, 1, 0, st>>>(sc.plan);
         // deeper grouping: every key computed once into t_k2, read by the first pass
         if ((e = sort_plan_cells_deep(sc, B.sc_deep, reinterpret_cast<const int4*>(sorted), N, cube, rcounts, Ly.cells,
                                       (uint32_t)(3 * (kKeyLevels - g - r1)), (uint32_t)(3 * (g + r1)),
                                       (uint32_t)(3 * r1), B.t_k2, B.deep, st)))
             return e;
+        const int gcell = (int)std::max<uint64_t>(1, std::min<uint64_t>((Ly.cells + 255) / 256, ws.num_sms * 8ull));
+        k_cell_cursor_init<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g, B.deep + 1);
+        const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 8));
+        k_cell_scatter<<<gs, 256, 0, st>>>(reinterpret_cast<const int4*>(sorted), N, cube, B.cursor, B.gk, B.gj, g,
+                                           B.deep + 1, ws.err);
+        k_cell_check<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g, B.deep + 1, ws.err);
         SortArgs a{};
-        a.b.pt_src = reinterpret_cast<const int4*>(sorted);
         a.b.k64_src = B.t_k2; a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.gk;
         a.b.val_src = nullptr; a.b.val_tmp = B.t_j1; a.b.val_dst = B.gj;
         a.n = N; a.cube = cube; a.g = g; a.err = ws.err;
-        SortArgs a_cell = a, a_key = a;
-        a_cell.run_if = B.deep + 1;   // keys from the points in the first pass
-        a_key.run_if = B.deep;        // keys from t_k2
-        if ((e = sort_run_pass<DIG_CELL, false, true, false>(sc, a_cell, 0, ws.num_sms, st))) return e;
-        if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a_key, 0, ws.num_sms, st))) return e;
-        for (int slot = 1; slot < kSortMaxPass; ++slot)
+        a.run_if = B.deep;
+        for (int slot = 0; slot < kSortMaxPass; ++slot)
             if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a, slot, ws.num_sms, st))) return e;
     }
     // 3. cells: pieces, leaf levels, open big cells

@@ -30,7 +30,7 @@ constexpr uint32_t kStFlagAgg = 1u << 30;
 constexpr uint32_t kStFlagInc = 2u << 30;
 constexpr uint32_t kStMask = (1u << 30) - 1;
 
-enum DigitSource { DIG_K64 = 0, DIG_K32 = 1, DIG_CHUNK = 2, DIG_CELL = 3 };
+enum DigitSource { DIG_K64 = 0, DIG_K32 = 1, DIG_CHUNK = 2 };
 
 // Decoupled look-back of one digit: the sum of the counts of tiles t, t-1, ...
 // down to the nearest one that published an inclusive prefix (tile t_first
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
     const uint64_t* bases = a.bases + (size_t)slot * (1 << kSortMaxBits);
 
     CubeDev cube;
-    if (DIG == DIG_CHUNK || DIG == DIG_CELL) cube = load_cube(a.cube);
+    if (DIG == DIG_CHUNK) cube = load_cube(a.cube);
     const float scale_g = DIG == DIG_CHUNK ? scale_at(cube, a.g) : 0.f;
 
     const bool use_bulk = SM::BULK && a.bulk;
@@ -248,10 +248,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
                 const uint64_t i = base + p;
                 if (DIG == DIG_K64) d = (uint32_t)((use_bulk ? raw_k[p] : in_k64[i]) >> shift) & dmask;
                 else if (DIG == DIG_K32) d = (in_k32[i] >> shift) & dmask;
-                else if (DIG == DIG_CELL) {
-                    int4 q = __ldg(in_pt + i);
-                    d = (uint32_t)(key21(q.x, q.y, q.z, cube) >> shift) & dmask;
-                } else {
+                else {
                     int4 q = __ldg(in_pt + i);
                     d = key_small(q.x, q.y, q.z, cube, scale_g, a.g);   // cell; its chunk below
                 }
@@ -315,12 +312,8 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
                 const uint32_t d = pack[r] & 0xFFFFu;
                 const uint32_t lp = s_off[d] + s_whist[warp * nb + d] + (pack[r] >> 16);
                 const uint64_t i = base + p;
-                if (CPT || DIG == DIG_CELL) {
-                    int4 q = __ldg(in_pt + i);
-                    if (CPT) s_pt[lp] = q;
-                    if (CK64 && DIG == DIG_CELL) s_k64[lp] = key21(q.x, q.y, q.z, cube);
-                }
-                if (CK64 && DIG != DIG_CELL) s_k64[lp] = use_bulk ? raw_k[p] : in_k64[i];
+                if (CPT) s_pt[lp] = __ldg(in_pt + i);
+                if (CK64) s_k64[lp] = use_bulk ? raw_k[p] : in_k64[i];
                 if (CK32) s_k32[lp] = in_k32[i];
                 s_val[lp] = has_val ? (use_bulk ? raw_v[p] : in_val[i]) : (uint32_t)i;
                 s_dig[lp] = (dig_t)d;
