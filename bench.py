@@ -32,6 +32,8 @@ WORKLOADS = {
     "batched-256": ("batch", 256, 1000, 7, 7, 15, 100_000, 20_000),
     # 32 LiDAR requests, sizes log-uniform in [1e6, 5e8], Poisson arrivals 4/s, 24 GB device budget (seed 5000 + i)
     "served-32": ("served", 32, 5000, 7, 7, 15, 100_000, 20_000),
+    # spatially constrained random preview of the 100M LiDAR cloud: one point per occupied level-7 cell
+    "spatial-preview-100M": ("spatial", 100_000_000, 2, 7, 7, 15, 100_000, 20_000),
 }
 STAGES = ["bounds_decimate", "count", "merge", "distribute", "octree", "subsample"]
 # algorithmic HBM bytes per point of each stage (mandatory reads + writes), see the design doc
@@ -436,6 +438,131 @@ def run_batched_reference(args, wl, rank):
 
 
 # ------------------------------------------------------------------ served workload
+def run_spatial(args, wl, rank, world, local):
+    """Bounds + spatially constrained preview (fp_bounds, fp_preview_spatial) of
+    a resident cloud per step; e2e adds the cloud's copy in and the preview's
+    copy out."""
+    import torch
+
+    from paper_2302_05002_gb300 import fastpoints as fp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _, n, seed, level = wl[0], wl[1], wl[2], wl[3]
+    host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+    make_cloud("lidar", n, seed, host)
+    pts = host.to(dev)
+    st = torch.cuda.Stream(dev)
+    cap = min(n, 1 << (3 * level))
+    out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+    cube = torch.empty(8, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    prm = fp.params(grid_log2=level, sub_log2=level, max_level=level)
+    ws = torch.empty(max(fp.workspace_size("preview_spatial", n, prm), fp.workspace_size("bounds", n)),
+                     dtype=torch.uint8, device=dev)
+    L, P, S = fp.load(), fp._ptr, fp._stream(st)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step(src, record=False):
+        if record:
+            ev[0].record(st)
+        fp._check(L.fp_bounds(P(src), n, P(cube), P(ws), ws.numel(), S), "fp_bounds")
+        if record:
+            ev[1].record(st)
+        fp._check(L.fp_preview_spatial(P(src), n, P(cube), level, 0, P(out), cap, P(cnt), P(ws), ws.numel(), S),
+                  "fp_preview_spatial")
+        if record:
+            ev[2].record(st)
+
+    for _ in range(max(3, args.warmup)):
+        step(pts)
+    torch.cuda.synchronize()
+    assert fp.get_device_error(stream=st) == 0
+    launches = count_kernels(lambda: step(pts), torch, st)
+    clk = ClockSampler(local)
+    clk.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sp_ms = []
+    t0.record(st)
+    for _ in range(args.steps):
+        step(pts, True)
+        st.synchronize()
+        sp_ms.append(ev[1].elapsed_time(ev[2]))
+    t1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    k = int(cnt.item())
+    # e2e: pinned cloud in, preview out
+    e2e_pts = torch.empty_like(pts)
+    out_host = torch.empty((cap, 4), dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    reps = max(1, min(args.steps, 3))
+    for _ in range(reps):
+        with torch.cuda.stream(st):
+            e2e_pts.copy_(host, non_blocking=True)
+            step(e2e_pts)
+            kk = int(cnt.item())
+            out_host[:kk].copy_(out[:kk], non_blocking=True)
+            st.synchronize()
+    e2e_ms = (time.perf_counter() - te) * 1e3 / reps
+    peak, peak_kind = measured_peaks()
+    sp = statistics.median(sp_ms)
+    alg = 32 * n + 16 * k + 2 * 8 * (1 << (3 * level))   # two reads of the cloud, the kept points, the table
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = spatial_oracle_rate(n, seed, level, float(os.environ.get("FP_ORACLE_BUDGET_S", "12")))
+        line = {
+            "metric": "spatial preview throughput (Gpts/s)", "value": n / (ms * 1e-3) / 1e9, "unit": "Gpts/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "points": n, "level": level, "kept": k,
+                       "parallelism": "single", "l2": "inputs (%.1f GB) larger than L2" % (16 * n / 1e9)},
+            "e2e": {"value": n / (e2e_ms * 1e-3) / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": 16 * n,
+                    "d2h_bytes_per_step": 16 * k + 8},
+            "roofline": {"bound": "hbm", "kernel": "fp_preview_spatial (cell minima + compaction)",
+                         "achieved": alg / (sp * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": alg / (sp * 1e-3) / 1e9 / peak, "traffic": None, "alg_bytes_per_launch": alg},
+            "stage_ms": {"bounds": ms - sp, "preview_spatial": sp},
+            "clocks": clocks, "gpu_launches": launches * args.steps if launches else None, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def spatial_oracle_rate(n, seed, level, budget_s):
+    import oracle
+    import synth
+    m = 1_000_000
+    while True:
+        pts = synth.lidar(m, seed)
+        t0 = time.perf_counter()
+        oracle.preview_spatial(pts, oracle.bounds(pts), level)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s / 4 or m >= min(n, 64_000_000):
+            break
+        m *= 2
+    return {"value": m / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d points of the LiDAR cloud, bounds + spatial preview, %.1f s" % (m, dt)}
+
+
+def run_spatial_reference(args, wl, rank):
+    if rank != 0:
+        return
+    budget = float(os.environ.get("FP_ORACLE_BUDGET_S", "12"))
+    rates = [spatial_oracle_rate(wl[1], wl[2], wl[3], budget / 2)["value"] for _ in range(max(1, args.steps))]
+    v = statistics.median(rates)
+    cpu = spatial_oracle_rate(wl[1], wl[2], wl[3], budget / 2)
+    print(json.dumps({"impl": "reference", "metric": "spatial preview throughput (Gpts/s)", "value": v,
+                      "unit": "Gpts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+                      "config": {"workload": args.workload, "points": wl[1], "level": wl[3]},
+                      "cpu_baseline": dict(cpu, value=v),
+                      "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
 def served_plan(count, seed):
     """Request sizes (log-uniform in [1e6, 5e8]) and arrival offsets (Poisson, 4/s)."""
     import numpy as np
@@ -635,6 +762,12 @@ def main():
             run_served_reference(args, wl, rank)
         else:
             run_served(args, wl, rank, world, local)
+        return
+    if wl[0] == "spatial":
+        if args.impl == "reference":
+            run_spatial_reference(args, wl, rank)
+        else:
+            run_spatial(args, wl, rank, world, local)
         return
     if wl[0] == "batch":
         if args.impl == "reference":

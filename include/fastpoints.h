@@ -9,6 +9,7 @@
  *
  *   fp_bounds              cube of the cloud                    (Sec. 4.4, extent)
  *   fp_decimate            hash-uniform preview                 (Sec. 3, Sec. 4.2)
+ *   fp_preview_spatial     one random point per occupied cell   (Sec. 6, proposed sampler)
  *   fp_count               points per cell of the 2^g grid      (Sec. 4.4, "sorted into chunks")
  *   fp_merge_chunks        cells merged into chunks under T     (Fig. "octree": chunk = node of the tree)
  *   fp_distribute          stable scatter of points into chunks (Sec. 4.4, Fig. "octree")
@@ -109,7 +110,8 @@ typedef enum {
     FP_STAGE_MERGE = 4,
     FP_STAGE_DISTRIBUTE = 5,
     FP_STAGE_OCTREE = 6,
-    FP_STAGE_SUBSAMPLE = 7
+    FP_STAGE_SUBSAMPLE = 7,
+    FP_STAGE_PREVIEW_SPATIAL = 8   /* prm->grid_log2 is the sampler's level (NULL: level 7) */
 } fp_stage;
 
 /* Bytes of workspace a stage needs for n points with these parameters
@@ -142,6 +144,25 @@ fp_status fp_bounds(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
 fp_status fp_decimate(const fp_point* d_pts, uint64_t n, uint64_t first_index, uint32_t modulus,
                       fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
                       void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Modulus of a preview of about `target` points (Sec. 5: the preview is the
+ * cloud downsampled to a fixed budget of points): max(1, ceil(n / target));
+ * 1 when target is 0.  Pass it to fp_decimate / fp_bounds_decimate. */
+uint32_t fp_preview_modulus(uint64_t n, uint64_t target);
+
+/* Spatially constrained random preview (the sampler Sec. 6 proposes for clouds
+ * whose file order makes the uniform preview uneven).  Of the points of every
+ * occupied cell of the 2^level grid over *d_cube (cells as in fp_count,
+ * 1 <= level <= 7), the one with the smallest splitmix64(first_index + i) is
+ * kept; kept points are written to d_out in ascending index, their number to
+ * *d_out_count (= the number of occupied cells; beyond out_cap they are not
+ * written and FP_ERR_CAPACITY is raised in the device word).  Two passes over
+ * the points; the workspace holds an 8^level table of 64-bit minima
+ * (fp_workspace_size(FP_STAGE_PREVIEW_SPATIAL, n, prm) with prm->grid_log2 =
+ * level).  The whole cloud must be in one call (the minimum is over the cloud). */
+fp_status fp_preview_spatial(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uint32_t level,
+                             uint64_t first_index, fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
+                             void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* fp_bounds and fp_decimate in one pass over the points (one read of the cloud). */
 fp_status fp_bounds_decimate(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,

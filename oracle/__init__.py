@@ -53,6 +53,8 @@ def _load():
         L.orc_splitmix64.argtypes = [u64]; L.orc_splitmix64.restype = u64
         L.orc_bounds.argtypes = [p, u64, p]
         L.orc_decimate.argtypes = [p, u64, u64, u32, p, p]; L.orc_decimate.restype = u64
+        L.orc_preview_modulus.argtypes = [u64, u64]; L.orc_preview_modulus.restype = u32
+        L.orc_preview_spatial.argtypes = [p, u64, p, u32, u64, p, p]; L.orc_preview_spatial.restype = u64
         L.orc_axis_cell.argtypes = [ctypes.c_int32, ctypes.c_int32, u64, u32]; L.orc_axis_cell.restype = u64
         L.orc_morton.argtypes = [u64, u64, u64, u32]; L.orc_morton.restype = u64
         L.orc_point_key.argtypes = [p, p, u32]; L.orc_point_key.restype = u64
@@ -116,6 +118,21 @@ def decimate(pts, first_index=0, modulus=16):
     out = np.empty(max(len(pts), 1), POINT)
     idx = np.empty(max(len(pts), 1), np.uint64)
     k = _load().orc_decimate(_p(pts), len(pts), first_index, modulus, _p(out), _p(idx))
+    return out[:k].copy(), idx[:k].copy()
+
+
+def preview_modulus(n, target):
+    return int(_load().orc_preview_modulus(n, target))
+
+
+def preview_spatial(pts, cube, level, first_index=0):
+    """One point per occupied level cell (smallest index hash), ascending index: (points, indices)."""
+    pts = _pts(pts)
+    out = np.empty(max(len(pts), 1), POINT)
+    idx = np.empty(max(len(pts), 1), np.uint64)
+    k = _load().orc_preview_spatial(_p(pts), len(pts), _p(cube), level, first_index, _p(out), _p(idx))
+    if k == 0xFFFFFFFFFFFFFFFF:
+        raise MemoryError("oracle allocation failed")
     return out[:k].copy(), idx[:k].copy()
 
 

@@ -65,6 +65,15 @@ uint64_t orc_decimate(const orc_point* pts, uint64_t n, uint64_t first_index, ui
     return k;
 }
 
+/* Sec. 5 sizes the preview by a point budget (1,000,000 points): the modulus
+ * is the smallest one whose expected preview fits, ceil(n / target). */
+uint32_t orc_preview_modulus(uint64_t n, uint64_t target)
+{
+    if (target == 0 || n <= target) return 1;
+    uint64_t m = n / target + (n % target != 0);
+    return m > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)m;
+}
+
 /* ------------------------------------------------------------------ cells */
 uint64_t orc_axis_cell(int32_t p, int32_t o, uint64_t S, uint32_t level)
 {
@@ -85,6 +94,37 @@ uint64_t orc_point_key(const orc_point* p, const orc_cube* c, uint32_t level)
     return orc_morton(orc_axis_cell(p->x, c->o[0], c->S, level),
                       orc_axis_cell(p->y, c->o[1], c->S, level),
                       orc_axis_cell(p->z, c->o[2], c->S, level), level);
+}
+
+/* ------------------------------------------------------- spatial preview */
+/* Sec. 6 proposes a spatially constrained random sampler for the preview.
+ * Reading: a grid of 2^level cells per axis over the cube; in every occupied
+ * cell the point whose index hash splitmix64(first_index + i) is smallest is
+ * kept (a random point of the cell, fixed by the hash); kept points in
+ * ascending index.  Written as: the smallest hash per cell, then a sweep that
+ * keeps the points holding it. */
+uint64_t orc_preview_spatial(const orc_point* pts, uint64_t n, const orc_cube* cube, uint32_t level,
+                             uint64_t first_index, orc_point* out, uint64_t* out_idx)
+{
+    uint64_t cells = 1ull << (3 * level);
+    uint64_t* best = (uint64_t*)malloc(cells * sizeof(uint64_t));
+    if (!best) return ~0ull;
+    for (uint64_t c = 0; c < cells; ++c) best[c] = ~0ull;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t c = orc_point_key(&pts[i], cube, level);
+        uint64_t h = orc_splitmix64(first_index + i);
+        if (h < best[c]) best[c] = h;
+    }
+    uint64_t k = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (best[orc_point_key(&pts[i], cube, level)] == orc_splitmix64(first_index + i)) {
+            out[k] = pts[i];
+            if (out_idx) out_idx[k] = first_index + i;
+            ++k;
+        }
+    }
+    free(best);
+    return k;
 }
 
 /* ------------------------------------------------------------------ count */

@@ -52,6 +52,14 @@ void orc_bounds(const orc_point* pts, uint64_t n, orc_cube* cube);
 uint64_t orc_decimate(const orc_point* pts, uint64_t n, uint64_t first_index, uint32_t modulus,
                       orc_point* out, uint64_t* out_idx);
 
+/* modulus of a preview of about `target` points: max(1, ceil(n / target)) */
+uint32_t orc_preview_modulus(uint64_t n, uint64_t target);
+
+/* one point per occupied level cell: the smallest splitmix64(first_index + i);
+ * kept points in ascending index; returns their number (~0 on allocation failure) */
+uint64_t orc_preview_spatial(const orc_point* pts, uint64_t n, const orc_cube* cube, uint32_t level,
+                             uint64_t first_index, orc_point* out, uint64_t* out_idx);
+
 /* exact integer cell coordinate of one axis at level l (0 <= l <= 21) */
 uint64_t orc_axis_cell(int32_t p, int32_t o, uint64_t S, uint32_t level);
 /* Morton key of a cell at level l; x bit most significant inside each 3-bit digit */

@@ -120,6 +120,7 @@ size_t fp_workspace_size(fp_stage stage, uint64_t n, const fp_params* prm)
     case FP_STAGE_DISTRIBUTE: return distribute_ws_bytes(n, g);
     case FP_STAGE_OCTREE: return prm ? octree_ws_bytes(n, *prm) : 0;
     case FP_STAGE_SUBSAMPLE: return prm ? subsample_ws_bytes(n, node_capacity_bound(n, *prm)) : 0;
+    case FP_STAGE_PREVIEW_SPATIAL: return spatial_ws_bytes(n, g, sms);
     }
     return 0;
 }
@@ -159,6 +160,31 @@ fp_status fp_bounds(const fp_point* d_pts, uint64_t n, fp_cube* d_cube, void* d_
     fp_status s = make_ws(d_ws, ws_bytes, fp_workspace_size(FP_STAGE_BOUNDS, n, nullptr), ws);
     if (s != FP_OK) return s;
     return cuda_status(launch_bounds_decimate(d_pts, n, d_cube, true, false, 0, 1, nullptr, 0, nullptr, ws, stream));
+}
+
+uint32_t fp_preview_modulus(uint64_t n, uint64_t target)
+{
+    if (target == 0 || n <= target) return 1;
+    const uint64_t m = (n + target - 1) / target;
+    return m > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)m;
+}
+
+// Sec. 6 (future work): spatially constrained random preview
+fp_status fp_preview_spatial(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uint32_t level,
+                             uint64_t first_index, fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
+                             void* d_ws, size_t ws_bytes, cudaStream_t stream)
+{
+    if (!d_out_count || !d_cube || (n && (!d_pts || (out_cap && !d_out)))) return FP_ERR_INVALID;
+    if (level < 1 || level > 7) return FP_ERR_UNSUPPORTED;
+    if (n >= kMaxPoints) return FP_ERR_TOO_LARGE;
+    if ((n && !aligned16(d_pts)) || (d_out && !aligned16(d_out))) return FP_ERR_ALIGN;
+    fp_params p{};
+    p.grid_log2 = level;
+    Workspace ws;
+    fp_status s = make_ws(d_ws, ws_bytes, fp_workspace_size(FP_STAGE_PREVIEW_SPATIAL, n, &p), ws);
+    if (s != FP_OK) return s;
+    return cuda_status(launch_preview_spatial(d_pts, n, d_cube, (int)level, first_index, d_out, out_cap, d_out_count,
+                                              ws, stream));
 }
 
 // Sec. 3 / Sec. 4.2: uniform preview, made index-deterministic by a hash

@@ -24,13 +24,20 @@ constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagInc = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 
-template <bool BOUNDS, bool DECIM>
+// keep rule of the compaction: none, index hash modulo m (the uniform
+// preview), or the smallest index hash of the point's cell (the spatial one)
+enum KeepRule { KEEP_NONE = 0, KEEP_MODULUS = 1, KEEP_CELL_MIN = 2 };
+
+template <bool BOUNDS, int KEEP>
 __global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __restrict__ pts, uint64_t n,
                                                            uint64_t first, uint32_t modulus, fp_point* __restrict__ out,
                                                            uint64_t out_cap, uint64_t* __restrict__ out_count,
                                                            int32_t* __restrict__ partial, uint64_t* tile_status,
-                                                           uint32_t* tile_counter, uint64_t ntiles, uint32_t* err)
+                                                           uint32_t* tile_counter, uint64_t ntiles, uint32_t* err,
+                                                           const uint64_t* __restrict__ cell_min,
+                                                           const fp_cube* cube_p, int level)
 {
+    constexpr bool DECIM = KEEP != KEEP_NONE;
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_cnt[kBdIPT][kBdNT / 32];
     __shared__ uint64_t s_base;
@@ -41,6 +48,9 @@ __global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __res
 
     int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
     int32_t hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    CubeDev cube;
+    if (KEEP == KEEP_CELL_MIN) cube = load_cube(cube_p);
+    const int csh = 3 * (kKeyLevels - level);
 
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
@@ -52,14 +62,19 @@ __global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __res
 
         uint32_t keepmask = 0;   // bit r: item r of this thread kept
         if (DECIM) {
-            // the keep decision depends on the index only: count first, publish early
+            // the keep decisions first (the uniform rule needs the index only), then publish
 #pragma unroll
             for (int r = 0; r < kBdIPT; ++r) {
                 uint64_t i = base + (uint64_t)r * kBdNT + threadIdx.x;
                 bool k = false;
                 if (i < n) {
                     uint64_t h = splitmix64(first + i);
-                    k = pow2 ? (h & mmask) == 0 : (h % modulus) == 0;
+                    if (KEEP == KEEP_MODULUS) {
+                        k = pow2 ? (h & mmask) == 0 : (h % modulus) == 0;
+                    } else {
+                        const int4 q = ld_point(pts, i);
+                        k = cell_min[key21(q.x, q.y, q.z, cube) >> csh] == h;
+                    }
                 }
                 uint32_t bal = __ballot_sync(0xFFFFFFFFu, k);
                 if (lane == 0) s_cnt[r][warp] = __popc(bal);
@@ -326,16 +341,75 @@ cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cub
     if (decim && n == 0) k_zero_count<<<1, 1, 0, st>>>(out_count);
     if (n) {
         if (bounds && decim)
-            k_bounds_decimate<true, true><<<grid, kBdNT, 0, st>>>(pts, n, first, modulus, out, out_cap, out_count,
-                                                                   partial, status, counter, ntiles, ws.err);
+            k_bounds_decimate<true, KEEP_MODULUS><<<grid, kBdNT, 0, st>>>(
+                pts, n, first, modulus, out, out_cap, out_count, partial, status, counter, ntiles, ws.err, nullptr,
+                nullptr, 0);
         else if (bounds)
-            k_bounds_decimate<true, false><<<grid, kBdNT, 0, st>>>(pts, n, first, modulus, out, out_cap, out_count,
-                                                                    partial, status, counter, ntiles, ws.err);
+            k_bounds_decimate<true, KEEP_NONE><<<grid, kBdNT, 0, st>>>(
+                pts, n, first, modulus, out, out_cap, out_count, partial, status, counter, ntiles, ws.err, nullptr,
+                nullptr, 0);
         else
-            k_bounds_decimate<false, true><<<grid, kBdNT, 0, st>>>(pts, n, first, modulus, out, out_cap,
-                                                                    out_count, partial, status, counter, ntiles, ws.err);
+            k_bounds_decimate<false, KEEP_MODULUS><<<grid, kBdNT, 0, st>>>(
+                pts, n, first, modulus, out, out_cap, out_count, partial, status, counter, ntiles, ws.err, nullptr,
+                nullptr, 0);
     }
     if (bounds) k_bounds_final<<<1, 256, 0, st>>>(partial, n ? grid : 0, n, cube);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------- spatial preview
+// Spatially constrained random sampler (the alternative preview the paper
+// proposes for clouds whose file order makes the uniform one uneven, Sec. 6):
+// of the points of every occupied cell of the 2^level grid, the one with the
+// smallest splitmix64(first + i) is kept (a uniformly random point of the cell,
+// the same on every run).  Pass 1 takes each cell's smallest hash; pass 2 is
+// the preview compaction with "hash == its cell's smallest" as the keep rule.
+__global__ void __launch_bounds__(256) k_cell_min_hash(const fp_point* __restrict__ pts, uint64_t n, uint64_t first,
+                                                       const fp_cube* cube_p, int level,
+                                                       unsigned long long* cell_min)
+{
+    const CubeDev cube = load_cube(cube_p);
+    const int csh = 3 * (kKeyLevels - level);
+    // a cell's running minimum only falls: a hash not below any value read for
+    // it (however stale) cannot be the minimum, and the atomic is skipped --
+    // in a cell of c points in random order about ln c atomics remain
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int4 q = ld_point_cs(pts, i);
+        unsigned long long* slot = &cell_min[key21(q.x, q.y, q.z, cube) >> csh];
+        const unsigned long long h = splitmix64(first + i);
+        if (h < __ldcg(slot)) atomicMin(slot, h);
+    }
+}
+
+size_t spatial_ws_bytes(uint64_t n, int level, int num_sms)
+{
+    return Workspace::bytes_for({sizeof(uint64_t) << (3 * level)}) + bounds_ws_bytes(n, num_sms);
+}
+
+cudaError_t launch_preview_spatial(const fp_point* pts, uint64_t n, const fp_cube* cube, int level, uint64_t first,
+                                   fp_point* out, uint64_t out_cap, uint64_t* out_count, const Workspace& ws,
+                                   cudaStream_t st)
+{
+    const uint64_t cells = 1ull << (3 * level);
+    uint64_t* cell_min = ws.take<uint64_t>(cells);
+    uint64_t ntiles = (n + kBdTile - 1) / kBdTile;
+    int grid = (int)std::min<uint64_t>(ntiles ? ntiles : 1, (uint64_t)ws.num_sms * 8);
+    int32_t* partial = ws.take<int32_t>(6 * (size_t)grid);
+    uint64_t* status = ws.take<uint64_t>(ntiles ? ntiles : 1);
+    uint32_t* counter = ws.take<uint32_t>(4);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(counter, 0, 4 * sizeof(uint32_t), st))) return e;
+    if (n == 0) {
+        k_zero_count<<<1, 1, 0, st>>>(out_count);
+        return cudaGetLastError();
+    }
+    if ((e = cudaMemsetAsync(status, 0, ntiles * sizeof(uint64_t), st))) return e;
+    if ((e = cudaMemsetAsync(cell_min, 0xFF, cells * sizeof(uint64_t), st))) return e;
+    const int gm = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ws.num_sms * 8);
+    k_cell_min_hash<<<gm, 256, 0, st>>>(pts, n, first, cube, level, reinterpret_cast<unsigned long long*>(cell_min));
+    k_bounds_decimate<false, KEEP_CELL_MIN><<<grid, kBdNT, 0, st>>>(pts, n, first, 1, out, out_cap, out_count, partial,
+                                                                    status, counter, ntiles, ws.err, cell_min, cube,
+                                                                    level);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,10 @@ cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cub
                                    uint64_t first, uint32_t modulus, fp_point* out, uint64_t out_cap,
                                    uint64_t* out_count, const Workspace& ws, cudaStream_t st);
 size_t bounds_ws_bytes(uint64_t n, int num_sms);
+size_t spatial_ws_bytes(uint64_t n, int level, int num_sms);
+cudaError_t launch_preview_spatial(const fp_point* pts, uint64_t n, const fp_cube* cube, int level, uint64_t first,
+                                   fp_point* out, uint64_t out_cap, uint64_t* out_count, const Workspace& ws,
+                                   cudaStream_t st);
 cudaError_t launch_count(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, uint32_t* counts,
                          bool accumulate, const Workspace& ws, cudaStream_t st);
 size_t merge_ws_bytes(int g);

@@ -42,7 +42,8 @@ class fp_cloud_desc(ctypes.Structure):
 
 MAX_LANES = 32
 PREVIEW_DONE = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
-STAGE = dict(bounds=0, decimate=1, bounds_decimate=2, count=3, merge=4, distribute=5, octree=6, subsample=7)
+STAGE = dict(bounds=0, decimate=1, bounds_decimate=2, count=3, merge=4, distribute=5, octree=6, subsample=7,
+             preview_spatial=8)
 ERR_BITS = {1 << 6: "timeout", 1 << 9: "capacity"}
 NODE_BYTES, CHUNK_BYTES, CUBE_BYTES = 40, 16, 32
 
@@ -65,6 +66,8 @@ def load():
         "fp_get_device_error": (st, [p, p, i32]),
         "fp_bounds": (st, [p, u64, p, p, sz, p]),
         "fp_decimate": (st, [p, u64, u64, u32, p, u64, p, p, sz, p]),
+        "fp_preview_spatial": (st, [p, u64, p, u32, u64, p, u64, p, p, sz, p]),
+        "fp_preview_modulus": (u32, [u64, u64]),
         "fp_bounds_decimate": (st, [p, u64, p, u64, u32, p, u64, p, p, sz, p]),
         "fp_count": (st, [p, u64, p, u32, p, i32, p, sz, p]),
         "fp_merge_chunks": (st, [p, u32, u64, p, p, p, p, p, sz, p]),
@@ -88,7 +91,7 @@ def declared_functions():
     """Names of the functions include/fastpoints.h declares."""
     with open(HEADER) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^\s*(?:fp_status|size_t|const char\*)\s+(fp_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:fp_status|size_t|uint32_t|const char\*)\s+(fp_\w+)\s*\(", text, re.M)))
 
 
 def params(grid_log2=7, sub_log2=7, max_level=15, decim_modulus=16, chunk_threshold=100000, node_capacity=20000):
@@ -166,6 +169,26 @@ def fp_decimate(pts, first_index=0, modulus=16, out=None, stream=None, ws=None):
     w, need = _ws("decimate", n, None, _dev(pts), ws)
     _check(load().fp_decimate(_ptr(pts), n, first_index, modulus, _ptr(out), cap, _ptr(count), _ptr(w), w.numel(),
                               _stream(stream)), "fp_decimate")
+    return out, count
+
+
+def fp_preview_modulus(n, target):
+    """Modulus of a preview of about `target` points: max(1, ceil(n / target))."""
+    return int(load().fp_preview_modulus(n, target))
+
+
+def fp_preview_spatial(pts, cube, level=7, first_index=0, out=None, stream=None, ws=None):
+    """One random point (smallest index hash) per occupied cell of the 2^level
+    grid, ascending index: (out, count)."""
+    n = pts.shape[0]
+    cap = out.shape[0] if out is not None else min(n, 1 << (3 * level))
+    if out is None:
+        out = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=_dev(pts))
+    count = torch.zeros(1, dtype=torch.int64, device=_dev(pts))
+    prm = params(grid_log2=level, sub_log2=level, max_level=level)
+    w, need = _ws("preview_spatial", n, prm, _dev(pts), ws)
+    _check(load().fp_preview_spatial(_ptr(pts), n, _ptr(cube), level, first_index, _ptr(out), cap, _ptr(count),
+                                     _ptr(w), w.numel(), _stream(stream)), "fp_preview_spatial")
     return out, count
 
 

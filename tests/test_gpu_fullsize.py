@@ -39,11 +39,15 @@ def u32(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-def sampled_chunks(chunks, C, rng, k=4):
+def sampled_chunks(chunks, C, rng, k=4, spread=True):
+    """The largest chunk above C points, plus (spread) the median and smallest
+    of them, plus k random ones."""
     big = np.flatnonzero(chunks["count"] > C)
     assert big.size, "no chunk above the node capacity"
     order = big[np.argsort(chunks["count"][big], kind="stable")]
-    pick = {int(order[-1]), int(order[len(order) // 2]), int(order[0])}
+    pick = {int(order[-1])}
+    if spread:
+        pick.update((int(order[len(order) // 2]), int(order[0])))
     pick.update(int(x) for x in rng.choice(big, size=min(k, big.size), replace=False))
     return sorted(pick)
 
@@ -175,10 +179,21 @@ def test_full_size(gpu_lib, kind, n, seed, g, s, lmax, T, C):
     assert np.array_equal(perm_np, want_perm)
     del want_perm
 
+    # spatial preview (one random point per occupied level-7 cell) on the same cloud
+    if n <= 200_000_000:
+        sp, sp_n = fp.fp_preview_spatial(pts, r["cube"], 7)
+        want_sp, _ = oracle.preview_spatial(pts_np, cube, 7)
+        k = int(sp_n.item())
+        assert k == len(want_sp)
+        assert np.array_equal(sp[:k].cpu().numpy().view(np.uint32).reshape(-1, 4),
+                              np.ascontiguousarray(want_sp).view(np.uint32).reshape(-1, 4))
+        del sp, want_sp
+
     # octree on sampled chunks
     nodes = fp.nodes_to_host(r["nodes"], r["num_nodes"])
     rng = np.random.default_rng(seed)
-    for c in sampled_chunks(chunks, C, rng):
+    # (the 1B cloud's chunks are all alike: two of them)
+    for c in sampled_chunks(chunks, C, rng, *((1, False) if n > 500_000_000 else (4, True))):
         check_chunk(fp, pts_np, cube, oprm, C, r, nodes, chunks[c], offsets[c:c + 2], r["owner"], perm_np)
     del perm_np
     # layout properties of the whole cloud

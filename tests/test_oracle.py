@@ -61,6 +61,56 @@ def test_preview_matches_independent_bigint_hash():
     assert len(oracle.decimate(pts[:100], 0, 7)[1]) == sum(brute.splitmix64(i) % 7 == 0 for i in range(100))
 
 
+def test_preview_modulus_closed_forms():
+    # ceil(n / target), at least 1; the 1B-point cloud at a 1M-point budget keeps every 1000th hash
+    assert oracle.preview_modulus(10 ** 9, 10 ** 6) == 1000
+    assert oracle.preview_modulus(10 ** 9 + 1, 10 ** 6) == 1001
+    assert oracle.preview_modulus(999_999, 10 ** 6) == 1
+    assert oracle.preview_modulus(0, 10) == 1
+    assert oracle.preview_modulus(10 ** 6, 0) == 1
+    assert oracle.preview_modulus(1 << 40, 1) == 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("n,seed,level,first", [(300, 1, 1, 0), (500, 2, 2, 7), (800, 3, 3, 1 << 33), (1, 4, 7, 0),
+                                                (0, 5, 4, 0)])
+def test_preview_spatial_bruteforce(n, seed, level, first):
+    rnd = random.Random(seed)
+    xyz = [(rnd.randrange(-50, 50), rnd.randrange(0, 9), rnd.randrange(-3, 200)) for _ in range(n)]
+    pts = make_pts(xyz)
+    cube = oracle.bounds(pts)
+    got, idx = oracle.preview_spatial(pts, cube, level, first)
+    # independent: Python integers, a dictionary of the best (hash, index) per cell
+    cb = brute.cube(xyz)
+    best = {}
+    for i, p in enumerate(xyz):
+        k = brute.key(p, cb, level)
+        h = brute.splitmix64(first + i)
+        if k not in best or h < best[k][0]:
+            best[k] = (h, i)
+    want = sorted(i for _, i in best.values())
+    assert [int(v) - first for v in idx] == want
+    assert np.array_equal(got, pts[want]) if n else len(got) == 0
+
+
+def test_preview_spatial_invariants():
+    pts = synth.lidar(200_000, 8)
+    cube = oracle.bounds(pts)
+    for level in (4, 6):
+        got, idx = oracle.preview_spatial(pts, cube, level)
+        occupied = int((oracle.count(pts, cube, level) > 0).sum())
+        assert len(got) == occupied                       # one point per occupied cell
+        assert np.all(np.diff(idx.astype(np.int64)) > 0)  # ascending index
+        keys = oracle.point_keys(pts[idx[:2000].astype(np.int64)], cube, level)
+        assert len(set(keys.tolist())) == len(keys)       # distinct cells
+    # every other point of a sampled cell has a larger hash than the kept one
+    got, idx = oracle.preview_spatial(pts[:5000], oracle.bounds(pts[:5000]), 3)
+    cb = oracle.bounds(pts[:5000])
+    allkeys = oracle.point_keys(pts[:5000], cb, 3)
+    for i in idx[:20].astype(np.int64):
+        same = np.flatnonzero(allkeys == allkeys[i])
+        assert min(same, key=lambda j: oracle.splitmix64(int(j))) == i
+
+
 # ---------------------------------------------------------------------- cells
 def test_cell_closed_forms():
     for level in (0, 1, 7, 13, 21):
