@@ -34,7 +34,10 @@ WORKLOADS = {
     "served-32": ("served", 32, 5000, 7, 7, 15, 100_000, 20_000),
     # spatially constrained random preview of the 100M LiDAR cloud: one point per occupied level-7 cell
     "spatial-preview-100M": ("spatial", 100_000_000, 2, 7, 7, 15, 100_000, 20_000),
+    # headless frame of the 100M LiDAR octree: node selection + rasterisation at 1920x1080
+    "render-100M": ("render", 100_000_000, 2, 7, 7, 15, 100_000, 20_000),
 }
+RENDER_W, RENDER_H, RENDER_MIN_PX = 1920, 1080, 30.0
 STAGES = ["bounds_decimate", "count", "merge", "distribute", "octree", "subsample"]
 # algorithmic HBM bytes per point of each stage (mandatory reads + writes), see the design doc
 ALG_BYTES = {"bounds_decimate": 17, "count": 16, "merge": 0, "distribute": 36, "octree": 44, "subsample": 44}
@@ -531,6 +534,167 @@ def run_spatial(args, wl, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def render_camera(fp, host_np):
+    import numpy as np
+    lo = np.array([host_np[:, a].min() for a in range(3)], np.float64)
+    hi = np.array([host_np[:, a].max() for a in range(3)], np.float64)
+    c, size = (lo + hi) / 2, float((hi - lo).max())
+    m = fp.view_projection(c + np.array([0.45, -0.6, 0.25]) * size, c, fovy_deg=60, aspect=RENDER_W / RENDER_H,
+                           near=size * 1e-3, far=size * 10)
+    return fp.camera(m, RENDER_W, RENDER_H, RENDER_MIN_PX), m
+
+
+def run_render(args, wl, rank, world, local):
+    """One headless frame per step of the resident octree of the 100M LiDAR
+    cloud: fp_select_nodes + fp_rasterize at 1920x1080.  value = drawn points
+    per second; e2e adds reading the framebuffer back to the host."""
+    import torch
+
+    from paper_2302_05002_gb300 import fastpoints as fp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _, n, seed, g, s, lmax, T, C = wl
+    host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+    make_cloud("lidar", n, seed, host)
+    pts = host.to(dev)
+    prm = fp.params(grid_log2=g, sub_log2=s, max_level=lmax, decim_modulus=16, chunk_threshold=T, node_capacity=C)
+    r = fp.build_octree(pts, prm)
+    torch.cuda.synchronize()
+    M = int(r["num_nodes"].item())
+    nodes = r["nodes"][:M].contiguous()
+    cam, m = render_camera(fp, host.numpy())
+    st = torch.cuda.Stream(dev)
+    ws = torch.empty(fp.render_workspace_size(M), dtype=torch.uint8, device=dev)
+    fb = torch.empty((RENDER_H, RENDER_W), dtype=torch.int64, device=dev)
+    ids = torch.empty(M, dtype=torch.int32, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    npts = torch.zeros(1, dtype=torch.int64, device=dev)
+    L, P, S = fp.load(), fp._ptr, fp._stream(st)
+    import ctypes
+    cref = ctypes.byref(cam)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step(record=False):
+        if record:
+            ev[0].record(st)
+        fp._check(L.fp_select_nodes(P(nodes), P(r["num_nodes"]), M, P(r["cube"]), cref, P(ids), P(nsel), P(npts),
+                                    P(ws), ws.numel(), S), "fp_select_nodes")
+        if record:
+            ev[1].record(st)
+        fp._check(L.fp_rasterize(P(nodes), P(ids), P(nsel), M, P(r["final"]), n, cref, P(fb), P(ws), ws.numel(), S),
+                  "fp_rasterize")
+        if record:
+            ev[2].record(st)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert fp.get_device_error(stream=st) == 0
+    launches = count_kernels(lambda: step(), torch, st)
+    drawn = int(npts.item())
+    clk = ClockSampler(local)
+    clk.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sel_ms, ras_ms = [], []
+    t0.record(st)
+    for _ in range(args.steps):
+        step(True)
+        st.synchronize()
+        sel_ms.append(ev[0].elapsed_time(ev[1]))
+        ras_ms.append(ev[1].elapsed_time(ev[2]))
+    t1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    fb_host = torch.empty((RENDER_H, RENDER_W), dtype=torch.int64, pin_memory=True)
+    te = time.perf_counter()
+    reps = max(1, min(args.steps, 5))
+    for _ in range(reps):
+        with torch.cuda.stream(st):
+            step()
+            fb_host.copy_(fb, non_blocking=True)
+            st.synchronize()
+    e2e_ms = (time.perf_counter() - te) * 1e3 / reps
+    peak, peak_kind = measured_peaks()
+    ras = statistics.median(ras_ms)
+    alg = 16 * drawn + 2 * 8 * RENDER_W * RENDER_H + 40 * M   # drawn points, framebuffer set + read-modify, nodes
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = render_oracle_rate(fp, r, M, m)
+        line = {
+            "metric": "rendered points per second (Gpts/s)", "value": drawn / (ms * 1e-3) / 1e9, "unit": "Gpts/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": args.workload, "points": n, "nodes": M, "drawn_nodes": int(nsel.item()),
+                       "drawn_points": drawn, "width": RENDER_W, "height": RENDER_H, "min_node_px": RENDER_MIN_PX,
+                       "fps": 1e3 / ms, "parallelism": "single",
+                       "l2": "drawn points (%.2f GB) larger than L2" % (16 * drawn / 1e9)},
+            "e2e": {"value": drawn / (e2e_ms * 1e-3) / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 8 * RENDER_W * RENDER_H},
+            "roofline": {"bound": "hbm", "kernel": "fp_rasterize", "achieved": alg / (ras * 1e-3) / 1e9, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": alg / (ras * 1e-3) / 1e9 / peak,
+                         "traffic": None, "alg_bytes_per_launch": alg},
+            "stage_ms": {"select": statistics.median(sel_ms), "rasterize": ras},
+            "clocks": clocks, "gpu_launches": launches * args.steps if launches else None, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def render_oracle_rate(fp, r, M, m):
+    """The oracle's selection and rasterisation of the same frame (node table
+    and final points copied to the host)."""
+    import numpy as np
+
+    import oracle
+    nodes = fp.nodes_to_host(r["nodes"], r["num_nodes"])
+    fin = r["final"].cpu().numpy().view(np.uint8).reshape(-1, 16).copy().view(oracle.POINT).reshape(-1)
+    cube = r["cube"].cpu().numpy().view(np.uint8).copy().view(oracle.CUBE)
+    cam = oracle.camera(m, RENDER_W, RENDER_H, RENDER_MIN_PX)
+    t0 = time.perf_counter()
+    sel = oracle.render_select(nodes, cube, cam)
+    oracle.rasterize(nodes, sel, fin, cam)
+    dt = time.perf_counter() - t0
+    drawn = int(nodes["n_own"][sel].astype(np.int64).sum())
+    return {"value": drawn / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": "the whole frame (%d drawn points), %.1f s" % (drawn, dt)}
+
+
+def run_render_reference(args, wl, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+    from paper_2302_05002_gb300 import fastpoints as fp
+    # the oracle builds a bounded prefix of the cloud and renders one frame of it
+    n = 2_000_000
+    pts = synth.lidar(n, wl[2])
+    _, _, _, g, s, lmax, T, C = wl
+    cube = oracle.bounds(pts)
+    t = oracle.octree_lod(pts, cube, oracle.params(g, s, lmax, 16, T, C))
+    _, m = render_camera(fp, pts.view(np.int32).reshape(-1, 4))
+    cam = oracle.camera(m, RENDER_W, RENDER_H, RENDER_MIN_PX)
+    rates = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        sel = oracle.render_select(t["nodes"], cube, cam)
+        oracle.rasterize(t["nodes"], sel, t["final_pts"], cam)
+        dt = time.perf_counter() - t0
+        rates.append(int(t["nodes"]["n_own"][sel].astype(np.int64).sum()) / dt / 1e9)
+    v = statistics.median(rates)
+    print(json.dumps({"impl": "reference", "metric": "rendered points per second (Gpts/s)", "value": v,
+                      "unit": "Gpts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "fp32", "data": "synthetic",
+                      "config": {"workload": args.workload, "points": wl[1], "width": RENDER_W, "height": RENDER_H},
+                      "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+                                       "sample": "one frame of the octree of the first %d points" % n},
+                      "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
 def spatial_oracle_rate(n, seed, level, budget_s):
     import oracle
     import synth
@@ -762,6 +926,12 @@ def main():
             run_served_reference(args, wl, rank)
         else:
             run_served(args, wl, rank, world, local)
+        return
+    if wl[0] == "render":
+        if args.impl == "reference":
+            run_render_reference(args, wl, rank)
+        else:
+            run_render(args, wl, rank, world, local)
         return
     if wl[0] == "spatial":
         if args.impl == "reference":

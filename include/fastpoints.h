@@ -99,7 +99,8 @@ typedef enum {
     FP_ERR_TIMEOUT = 6,      /* device word: a bounded inter-block wait ran out */
     FP_ERR_CUDA = 7,         /* a CUDA call failed (no device, launch error) */
     FP_ERR_UNSUPPORTED = 8,  /* parameters outside the limits above */
-    FP_ERR_CAPACITY = 9      /* device word: an output array was too small */
+    FP_ERR_CAPACITY = 9,     /* device word: an output array was too small */
+    FP_ERR_IO = 10           /* a file could not be opened, read or written */
 } fp_status;
 
 typedef enum {
@@ -324,6 +325,107 @@ fp_status fp_build_ooc(const fp_point* h_pts, uint64_t n, const fp_params* h_prm
                        fp_node* h_nodes, uint32_t node_cap, uint32_t* h_num_nodes,
                        fp_point* h_final, uint32_t* h_final_perm,
                        void (*preview_done)(void*), void* user, cudaStream_t stream);
+
+/* ------------------------------------------------------ octree file, cache
+ * The stitched global octree written to one file and loaded back (Sec. 4.4:
+ * the global octree is written to a file; Sec. 4.5: the renderer loads the
+ * points of the nodes it draws on demand), and a digest of the input cloud
+ * that keys a cache of built octrees (Sec. 3, Fig. "pipeline": a cloud whose
+ * octree was built before is not built again).
+ *
+ * File layout (little-endian): fp_file_header at offset 0; the node table
+ * (num_nodes fp_node records, preorder) at nodes_offset; the points in the
+ * final layout (n fp_point records; node i's kept points are records
+ * [first, first + n_own)) at points_offset; when flags has FP_FILE_HAS_PERM,
+ * the original index of every final point (n uint32) at perm_offset.  Offsets
+ * are multiples of 4096 except perm_offset (= points_offset + 16 n). */
+#define FP_FILE_HAS_PERM 1u
+typedef struct {
+    char magic[8];                 /* "FPOCTREE" */
+    uint32_t version, header_bytes;   /* 1, sizeof(fp_file_header) */
+    fp_params prm;
+    fp_cube cube;
+    uint64_t n;
+    uint32_t num_nodes, flags;
+    uint64_t digest;               /* fp_cloud_digest of the input cloud (0: not recorded) */
+    uint64_t nodes_offset, points_offset, perm_offset;
+    uint64_t reserved[4];
+} fp_file_header;
+
+/* Digest of a cloud: n + sum over i of splitmix64(splitmix64(i) ^
+ * splitmix64(x | y << 32) ^ splitmix64((z | rgba << 32) ^ 0x5851F42D4C957F2D))
+ * (mod 2^64), with x, y, z, rgba the record's four 32-bit words as unsigned.
+ * Depends on every point and on the order.  Written to *d_digest. */
+fp_status fp_cloud_digest(const fp_point* d_pts, uint64_t n, uint64_t* d_digest, cudaStream_t stream);
+
+/* Writes the octree of fp_build_chunk_octree + fp_subsample (device outputs)
+ * to `path`: header, node table, final points, and the final permutation when
+ * d_final_perm is not NULL.  h_staging: pinned host memory of staging_bytes
+ * (>= 8 KiB; larger pieces overlap better), used in two halves so the device
+ * copy of one piece overlaps the file write of the other.  Blocks the calling
+ * thread until the file is closed.  FP_ERR_IO when the file cannot be written. */
+fp_status fp_octree_save(const char* path, const fp_params* h_prm, const fp_cube* d_cube, const fp_node* d_nodes,
+                         const uint32_t* d_num_nodes, const fp_point* d_final, const uint32_t* d_final_perm,
+                         uint64_t n, uint64_t digest, void* h_staging, size_t staging_bytes, cudaStream_t stream);
+
+/* Reads and checks the header (FP_ERR_INVALID: not an octree file of this version). */
+fp_status fp_octree_read_header(const char* path, fp_file_header* h_hdr);
+
+/* Loads into device memory the node table (d_nodes non-NULL; node_cap >=
+ * num_nodes, else FP_ERR_CAPACITY) and final points [first, first + count)
+ * (d_points non-NULL), with their original indices (d_perm non-NULL; the file
+ * must hold them) -- a node's points are first = node.first, count = n_own.
+ * Staging as for fp_octree_save.  Blocks until the data are on the device. */
+fp_status fp_octree_load(const char* path, fp_node* d_nodes, uint32_t node_cap, fp_point* d_points,
+                         uint32_t* d_perm, uint64_t first, uint64_t count, void* h_staging, size_t staging_bytes,
+                         cudaStream_t stream);
+
+/* ------------------------------------------------------ rendering, headless
+ * The renderer's side of the octree (Sec. 4.5: a traversal picks the nodes the
+ * camera needs, their points are drawn), into a device framebuffer instead of
+ * a graphics API.
+ *
+ * Camera: m is a row-major 4x4 view-projection matrix; a position p maps to
+ * clip = m (x, y, z, 1) with every row evaluated as
+ * fmaf(m0, x, fmaf(m1, y, fmaf(m2, z, m3))) in fp32 (x, y, z the coordinates
+ * rounded to fp32).  A point is inside when w > 0, -w <= x, y <= w and
+ * 0 <= z <= w; its pixel is (floor(sx), floor(sy)) clamped to the image with
+ * sx = fmaf(x / w, 0.5, 0.5) * width (sy likewise with y, height; IEEE
+ * division), framebuffer index py * width + px; its depth is z / w + 0.
+ *
+ * Node box: the integer range of the points a node can hold, per axis
+ * [o + ceil(c S / 2^L), o + ceil((c + 1) S / 2^L) - 1] for cell coordinate c at
+ * level L.  A node is outside when all 8 box corners (as fp32) are beyond the
+ * same clip plane (x < -w, x > w, y < -w, y > w, z < 0 or z > w).  Its screen
+ * size is the larger of the x and y extents of the corners' sx, sy, infinite
+ * when a corner has w <= 0.  A node is drawn when it is not outside and every
+ * ancestor was refined; refined = drawn, not a leaf, size > min_node_px. */
+typedef struct {
+    float m[16];
+    uint32_t width, height;   /* 1 .. 16384 */
+    float min_node_px;
+    uint32_t reserved;
+} fp_camera;
+
+/* Workspace of fp_select_nodes and fp_rasterize for a node table of node_cap entries. */
+size_t fp_render_workspace_size(uint32_t node_cap);
+
+/* The drawn nodes in preorder (ids into d_nodes) to d_selected (node_cap
+ * entries), their number to *d_num_selected and their kept points in total to
+ * *d_num_points.  node_cap <= 2^23. */
+fp_status fp_select_nodes(const fp_node* d_nodes, const uint32_t* d_num_nodes, uint32_t node_cap,
+                          const fp_cube* d_cube, const fp_camera* h_cam, uint32_t* d_selected,
+                          uint32_t* d_num_selected, uint64_t* d_num_points, void* d_ws, size_t ws_bytes,
+                          cudaStream_t stream);
+
+/* The kept points of the selected nodes (final layout of n points: node.first,
+ * n_own) rasterised into d_framebuffer (width * height entries, set by the
+ * call): every pixel holds the minimum over its points of
+ * (depth bits << 32 | rgba), all ones where no point lands.  Records outside
+ * [0, n) are skipped. */
+fp_status fp_rasterize(const fp_node* d_nodes, const uint32_t* d_selected, const uint32_t* d_num_selected,
+                       uint32_t node_cap, const fp_point* d_final, uint64_t n, const fp_camera* h_cam,
+                       uint64_t* d_framebuffer, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

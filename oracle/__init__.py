@@ -39,7 +39,8 @@ def build(force=False):
         return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + _SRC)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + _SRC +
+                          ["-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -54,6 +55,9 @@ def _load():
         L.orc_bounds.argtypes = [p, u64, p]
         L.orc_decimate.argtypes = [p, u64, u64, u32, p, p]; L.orc_decimate.restype = u64
         L.orc_preview_modulus.argtypes = [u64, u64]; L.orc_preview_modulus.restype = u32
+        L.orc_cloud_digest.argtypes = [p, u64]; L.orc_cloud_digest.restype = u64
+        L.orc_render_select.argtypes = [p, u32, p, p, p]; L.orc_render_select.restype = u32
+        L.orc_rasterize.argtypes = [p, p, u32, p, p, p]
         L.orc_preview_spatial.argtypes = [p, u64, p, u32, u64, p, p]; L.orc_preview_spatial.restype = u64
         L.orc_axis_cell.argtypes = [ctypes.c_int32, ctypes.c_int32, u64, u32]; L.orc_axis_cell.restype = u64
         L.orc_morton.argtypes = [u64, u64, u64, u32]; L.orc_morton.restype = u64
@@ -121,6 +125,11 @@ def decimate(pts, first_index=0, modulus=16):
     return out[:k].copy(), idx[:k].copy()
 
 
+def cloud_digest(pts):
+    pts = _pts(pts)
+    return int(_load().orc_cloud_digest(_p(pts), len(pts)))
+
+
 def preview_modulus(n, target):
     return int(_load().orc_preview_modulus(n, target))
 
@@ -134,6 +143,33 @@ def preview_spatial(pts, cube, level, first_index=0):
     if k == 0xFFFFFFFFFFFFFFFF:
         raise MemoryError("oracle allocation failed")
     return out[:k].copy(), idx[:k].copy()
+
+
+CAMERA = np.dtype([("m", "<f4", (16,)), ("width", "<u4"), ("height", "<u4"), ("min_node_px", "<f4"),
+                   ("reserved", "<u4")])
+
+
+def camera(m, width, height, min_node_px):
+    c = np.zeros(1, CAMERA)
+    c["m"][0] = np.asarray(m, dtype=np.float32).reshape(16)
+    c["width"], c["height"], c["min_node_px"] = width, height, min_node_px
+    return c
+
+
+def render_select(nodes, cube, cam):
+    """Ids (preorder) of the nodes the camera draws."""
+    nodes = np.ascontiguousarray(nodes)
+    sel = np.empty(max(len(nodes), 1), np.uint32)
+    k = _load().orc_render_select(_p(nodes), len(nodes), _p(cube), _p(cam), _p(sel))
+    return sel[:k].copy()
+
+
+def rasterize(nodes, sel, final_pts, cam):
+    """Framebuffer (height, width) of uint64: (depth bits << 32 | rgba), all ones where empty."""
+    fb = np.empty(int(cam["width"][0]) * int(cam["height"][0]), np.uint64)
+    sel = np.ascontiguousarray(sel, dtype=np.uint32)
+    _load().orc_rasterize(_p(np.ascontiguousarray(nodes)), _p(sel), len(sel), _p(_pts(final_pts)), _p(cam), _p(fb))
+    return fb.reshape(int(cam["height"][0]), int(cam["width"][0]))
 
 
 def count(pts, cube, g):

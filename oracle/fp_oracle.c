@@ -8,6 +8,7 @@
  * Nothing here is shared with the CUDA library.
  */
 #include "fp_oracle.h"
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -22,6 +23,22 @@ uint64_t orc_splitmix64(uint64_t i)
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+/* Digest of a cloud (the key of the cache of built octrees): n plus the sum,
+ * modulo 2^64, of one mixed word per point built from its index and the two
+ * 64-bit halves of its record. */
+uint64_t orc_cloud_digest(const orc_point* pts, uint64_t n)
+{
+    uint64_t d = n;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t w[4];
+        memcpy(w, &pts[i], sizeof(w));
+        uint64_t a = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+        uint64_t b = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+        d += orc_splitmix64(orc_splitmix64(i) ^ orc_splitmix64(a) ^ orc_splitmix64(b ^ 0x5851F42D4C957F2Dull));
+    }
+    return d;
 }
 
 /* ----------------------------------------------------------------- bounds */
@@ -514,4 +531,118 @@ int orc_point_levels(const orc_point* pts, uint64_t n, const orc_cube* cube, con
     }
     tree_free(&t);
     return 0;
+}
+
+/* ----------------------------------------------------- headless rendering */
+/* Sec. 4.5: the renderer walks the octree, draws the nodes the camera needs
+ * and the points of those nodes.  Restated with fp32 arithmetic in the order
+ * the boundary documents: each clip row is fmaf(m0, x, fmaf(m1, y, fmaf(m2, z,
+ * m3))); screen x = fmaf(x / w, 0.5, 0.5) * width.  (C float arithmetic is
+ * IEEE single here; the library is built without contraction.) */
+typedef struct { float x, y, z, w; } orc_clip;
+
+static orc_clip clip_of(const orc_camera* c, float x, float y, float z)
+{
+    orc_clip r;
+    r.x = fmaf(c->m[0], x, fmaf(c->m[1], y, fmaf(c->m[2], z, c->m[3])));
+    r.y = fmaf(c->m[4], x, fmaf(c->m[5], y, fmaf(c->m[6], z, c->m[7])));
+    r.z = fmaf(c->m[8], x, fmaf(c->m[9], y, fmaf(c->m[10], z, c->m[11])));
+    r.w = fmaf(c->m[12], x, fmaf(c->m[13], y, fmaf(c->m[14], z, c->m[15])));
+    return r;
+}
+
+static float screen(float ndc, float size)
+{
+    float t = fmaf(ndc, 0.5f, 0.5f);
+    return t * size;
+}
+
+/* the integer range of the points node (L, key) can hold, per axis */
+static void node_box(const orc_node* nd, const orc_cube* cb, float lo[3], float hi[3])
+{
+    uint64_t c[3] = {0, 0, 0};
+    for (int b = 0; b < nd->level; ++b)
+        for (int a = 0; a < 3; ++a) c[a] |= ((nd->key >> (3 * b + (2 - a))) & 1u) << b;
+    uint64_t den = 1ull << nd->level;
+    for (int a = 0; a < 3; ++a) {
+        uint64_t first = (c[a] * cb->S + den - 1) / den;         /* ceil(c S / 2^L) */
+        uint64_t next = ((c[a] + 1) * cb->S + den - 1) / den;    /* ceil((c + 1) S / 2^L) */
+        lo[a] = (float)((int64_t)cb->o[a] + (int64_t)first);
+        hi[a] = (float)((int64_t)cb->o[a] + (int64_t)next - 1);
+    }
+}
+
+/* visible: not all corners beyond one clip plane; refine: visible, inner, and
+ * the screen extent of the corners above min_node_px (or a corner behind) */
+static void node_flags(const orc_node* nd, const orc_cube* cb, const orc_camera* cam, int* visible, int* refine)
+{
+    float lo[3], hi[3];
+    node_box(nd, cb, lo, hi);
+    int out[6] = {1, 1, 1, 1, 1, 1}, behind = 0, any = 0;
+    float x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    for (int k = 0; k < 8; ++k) {
+        orc_clip c = clip_of(cam, (k & 4) ? hi[0] : lo[0], (k & 2) ? hi[1] : lo[1], (k & 1) ? hi[2] : lo[2]);
+        out[0] &= c.x < -c.w;
+        out[1] &= c.x > c.w;
+        out[2] &= c.y < -c.w;
+        out[3] &= c.y > c.w;
+        out[4] &= c.z < 0.f;
+        out[5] &= c.z > c.w;
+        if (c.w <= 0.f) { behind = 1; continue; }
+        float sx = screen(c.x / c.w, (float)cam->width), sy = screen(c.y / c.w, (float)cam->height);
+        if (!any || sx < x0) x0 = sx;
+        if (!any || sx > x1) x1 = sx;
+        if (!any || sy < y0) y0 = sy;
+        if (!any || sy > y1) y1 = sy;
+        any = 1;
+    }
+    *visible = !(out[0] || out[1] || out[2] || out[3] || out[4] || out[5]);
+    float w = x1 - x0, h = y1 - y0;
+    float size = w > h ? w : h;
+    *refine = *visible && !nd->is_leaf && (behind || size > cam->min_node_px);
+}
+
+/* preorder walk: a node is drawn when visible and its parent refined */
+static void select_visit(const orc_node* nodes, uint32_t i, const orc_cube* cb, const orc_camera* cam,
+                         uint32_t* sel, uint32_t* ns)
+{
+    int visible, refine;
+    node_flags(&nodes[i], cb, cam, &visible, &refine);
+    if (visible) sel[(*ns)++] = i;
+    if (!refine) return;
+    for (uint32_t j = i + 1; j <= i + nodes[i].n_desc; j += nodes[j].n_desc + 1) select_visit(nodes, j, cb, cam, sel, ns);
+}
+
+uint32_t orc_render_select(const orc_node* nodes, uint32_t M, const orc_cube* cube, const orc_camera* cam,
+                           uint32_t* sel)
+{
+    uint32_t ns = 0;
+    if (M) select_visit(nodes, 0, cube, cam, sel, &ns);
+    return ns;
+}
+
+void orc_rasterize(const orc_node* nodes, const uint32_t* sel, uint32_t nsel, const orc_point* final_pts,
+                   const orc_camera* cam, uint64_t* fb)
+{
+    uint64_t npx = (uint64_t)cam->width * cam->height;
+    for (uint64_t q = 0; q < npx; ++q) fb[q] = ~0ull;
+    for (uint32_t k = 0; k < nsel; ++k) {
+        const orc_node* nd = &nodes[sel[k]];
+        for (uint64_t i = nd->first; i < nd->first + nd->n_own; ++i) {
+            const orc_point* p = &final_pts[i];
+            orc_clip c = clip_of(cam, (float)p->x, (float)p->y, (float)p->z);
+            if (!(c.w > 0.f) || c.x < -c.w || c.x > c.w || c.y < -c.w || c.y > c.w || c.z < 0.f || c.z > c.w) continue;
+            float sx = screen(c.x / c.w, (float)cam->width), sy = screen(c.y / c.w, (float)cam->height);
+            uint32_t px = (uint32_t)floorf(sx), py = (uint32_t)floorf(sy);
+            if (px > cam->width - 1) px = cam->width - 1;
+            if (py > cam->height - 1) py = cam->height - 1;
+            float depth = c.z / c.w + 0.0f;
+            uint32_t dbits, rgba;
+            memcpy(&dbits, &depth, 4);
+            memcpy(&rgba, &p->r, 4);
+            uint64_t v = ((uint64_t)dbits << 32) | rgba;
+            uint64_t at = (uint64_t)py * cam->width + px;
+            if (v < fb[at]) fb[at] = v;
+        }
+    }
 }

@@ -52,6 +52,9 @@ void orc_bounds(const orc_point* pts, uint64_t n, orc_cube* cube);
 uint64_t orc_decimate(const orc_point* pts, uint64_t n, uint64_t first_index, uint32_t modulus,
                       orc_point* out, uint64_t* out_idx);
 
+/* digest of a cloud: n + sum of one mixed word per point (mod 2^64) */
+uint64_t orc_cloud_digest(const orc_point* pts, uint64_t n);
+
 /* modulus of a preview of about `target` points: max(1, ceil(n / target)) */
 uint32_t orc_preview_modulus(uint64_t n, uint64_t target);
 
@@ -94,6 +97,23 @@ uint32_t orc_octree_lod(const orc_point* pts, uint64_t n, const orc_cube* cube, 
  * leaf_level[i], owner_level[i]; returns 0 on success */
 int orc_point_levels(const orc_point* pts, uint64_t n, const orc_cube* cube, const orc_params* prm,
                      uint8_t* lambda, uint8_t* leaf_level, uint8_t* owner_level);
+
+/* ---- headless rendering (Sec. 4.5) */
+typedef struct {
+    float m[16];               /* row-major view-projection */
+    uint32_t width, height;
+    float min_node_px;
+    uint32_t reserved;
+} orc_camera;
+
+/* drawn nodes (ids in preorder) to sel (capacity M); returns their number */
+uint32_t orc_render_select(const orc_node* nodes, uint32_t M, const orc_cube* cube, const orc_camera* cam,
+                           uint32_t* sel);
+
+/* the kept points of the drawn nodes rasterised: fb[width * height] = min over the
+ * pixel's points of (depth bits << 32 | rgba), all ones where none lands */
+void orc_rasterize(const orc_node* nodes, const uint32_t* sel, uint32_t nsel, const orc_point* final_pts,
+                   const orc_camera* cam, uint64_t* fb);
 
 #ifdef __cplusplus
 }

@@ -13,7 +13,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libfastpoints.so")
 OBJDIR = os.path.join(ROOT, "_build", "fastpoints")
 SOURCES = ["fp_core.cu", "fp_sort.cu", "fp_seg.cu", "fp_octree.cu", "fp_api.cu", "fp_static.cu", "fp_batch.cu",
-           "fp_ooc.cu"]
+           "fp_ooc.cu", "fp_io.cu", "fp_render.cu"]
 HEADERS = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_sort.cuh", "fp_seg.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -98,6 +98,7 @@ const char* fp_status_string(fp_status s)
     case FP_ERR_CUDA: return "CUDA error";
     case FP_ERR_UNSUPPORTED: return "unsupported parameters";
     case FP_ERR_CAPACITY: return "output capacity exceeded";
+    case FP_ERR_IO: return "file read or write failed";
     }
     return "unknown status";
 }
@@ -160,6 +161,46 @@ fp_status fp_bounds(const fp_point* d_pts, uint64_t n, fp_cube* d_cube, void* d_
     fp_status s = make_ws(d_ws, ws_bytes, fp_workspace_size(FP_STAGE_BOUNDS, n, nullptr), ws);
     if (s != FP_OK) return s;
     return cuda_status(launch_bounds_decimate(d_pts, n, d_cube, true, false, 0, 1, nullptr, 0, nullptr, ws, stream));
+}
+
+size_t fp_render_workspace_size(uint32_t node_cap) { return render_ws_bytes(node_cap); }
+
+static bool camera_ok(const fp_camera* c)
+{
+    return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384;
+}
+
+// Sec. 4.5: the traversal that picks the nodes to draw
+fp_status fp_select_nodes(const fp_node* d_nodes, const uint32_t* d_num_nodes, uint32_t node_cap,
+                          const fp_cube* d_cube, const fp_camera* h_cam, uint32_t* d_selected,
+                          uint32_t* d_num_selected, uint64_t* d_num_points, void* d_ws, size_t ws_bytes,
+                          cudaStream_t stream)
+{
+    if (!d_num_nodes || !d_cube || !d_num_selected || !d_num_points || !camera_ok(h_cam) ||
+        (node_cap && (!d_nodes || !d_selected)))
+        return FP_ERR_INVALID;
+    if (node_cap > (1u << 23)) return FP_ERR_UNSUPPORTED;
+    Workspace ws;
+    fp_status s = make_ws(d_ws, ws_bytes, render_ws_bytes(node_cap), ws);
+    if (s != FP_OK) return s;
+    return cuda_status(launch_select_nodes(d_nodes, d_num_nodes, node_cap, d_cube, *h_cam, d_selected,
+                                           d_num_selected, d_num_points, ws, stream));
+}
+
+// Sec. 4.5: the selected nodes' points drawn, nearest per pixel
+fp_status fp_rasterize(const fp_node* d_nodes, const uint32_t* d_selected, const uint32_t* d_num_selected,
+                       uint32_t node_cap, const fp_point* d_final, uint64_t n, const fp_camera* h_cam,
+                       uint64_t* d_framebuffer, void* d_ws, size_t ws_bytes, cudaStream_t stream)
+{
+    if (!d_num_selected || !d_framebuffer || !camera_ok(h_cam) || (node_cap && (!d_nodes || !d_selected || !d_final)))
+        return FP_ERR_INVALID;
+    if (node_cap > (1u << 23)) return FP_ERR_UNSUPPORTED;
+    if (d_final && !aligned16(d_final)) return FP_ERR_ALIGN;
+    Workspace ws;
+    fp_status s = make_ws(d_ws, ws_bytes, render_ws_bytes(node_cap), ws);
+    if (s != FP_OK) return s;
+    return cuda_status(launch_rasterize(d_nodes, d_selected, d_num_selected, node_cap, d_final, n, *h_cam,
+                                        reinterpret_cast<unsigned long long*>(d_framebuffer), ws, ws.num_sms, stream));
 }
 
 uint32_t fp_preview_modulus(uint64_t n, uint64_t target)

@@ -45,6 +45,15 @@ cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cub
                                    uint64_t first, uint32_t modulus, fp_point* out, uint64_t out_cap,
                                    uint64_t* out_count, const Workspace& ws, cudaStream_t st);
 size_t bounds_ws_bytes(uint64_t n, int num_sms);
+
+// fp_render.cu
+size_t render_ws_bytes(uint32_t cap);
+cudaError_t launch_select_nodes(const fp_node* nodes, const uint32_t* num_nodes, uint32_t cap, const fp_cube* cube,
+                                const fp_camera& cam, uint32_t* ids, uint32_t* num_sel, uint64_t* num_points,
+                                const Workspace& ws, cudaStream_t st);
+cudaError_t launch_rasterize(const fp_node* nodes, const uint32_t* ids, const uint32_t* num_sel, uint32_t cap,
+                             const fp_point* fin, uint64_t n, const fp_camera& cam, unsigned long long* fb,
+                             const Workspace& ws, int num_sms, cudaStream_t st);
 size_t spatial_ws_bytes(uint64_t n, int level, int num_sms);
 cudaError_t launch_preview_spatial(const fp_point* pts, uint64_t n, const fp_cube* cube, int level, uint64_t first,
                                    fp_point* out, uint64_t out_cap, uint64_t* out_count, const Workspace& ws,

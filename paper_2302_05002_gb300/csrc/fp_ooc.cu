@@ -223,9 +223,7 @@ HostStore host_carve(void* base, uint64_t n)
 }
 
 size_t host_bytes(uint64_t n)
-{
-    Workspace dry;
-    host_carve(nullptr, n);
+{   // the pieces host_carve takes, in its order
     const uint64_t N = n ? n : 1;
     return Workspace::bytes_for({16 * N, 4 * N, N, N, 4 * N, 8 * N, 4 * N});
 }

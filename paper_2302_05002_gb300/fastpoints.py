@@ -40,6 +40,24 @@ class fp_cloud_desc(ctypes.Structure):
                 ("d_final_perm", ctypes.c_void_p)]
 
 
+class fp_cube(ctypes.Structure):
+    _fields_ = [("o", ctypes.c_int32 * 3), ("mx", ctypes.c_int32 * 3), ("S", ctypes.c_uint64)]
+
+
+class fp_file_header(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_char * 8), ("version", ctypes.c_uint32), ("header_bytes", ctypes.c_uint32),
+                ("prm", fp_params), ("cube", fp_cube), ("n", ctypes.c_uint64), ("num_nodes", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("digest", ctypes.c_uint64), ("nodes_offset", ctypes.c_uint64),
+                ("points_offset", ctypes.c_uint64), ("perm_offset", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 4)]
+
+
+class fp_camera(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_float * 16), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("min_node_px", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+
+
+FILE_HAS_PERM = 1
 MAX_LANES = 32
 PREVIEW_DONE = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
 STAGE = dict(bounds=0, decimate=1, bounds_decimate=2, count=3, merge=4, distribute=5, octree=6, subsample=7,
@@ -79,6 +97,13 @@ def load():
         "fp_ooc_host_bytes": (sz, [u64, p]),
         "fp_build_ooc": (st, [p, u64, p, u64, u64, p, sz, p, sz, p, p, u64, p, p, u32, p, p, p, PREVIEW_DONE, p, p]),
         "fp_build_batched": (st, [p, u32, u32, p, sz, p]),
+        "fp_cloud_digest": (st, [p, u64, p, p]),
+        "fp_render_workspace_size": (sz, [u32]),
+        "fp_select_nodes": (st, [p, p, u32, p, p, p, p, p, p, sz, p]),
+        "fp_rasterize": (st, [p, p, p, u32, p, u64, p, p, p, sz, p]),
+        "fp_octree_save": (st, [ctypes.c_char_p, p, p, p, p, p, p, u64, u64, p, sz, p]),
+        "fp_octree_read_header": (st, [ctypes.c_char_p, p]),
+        "fp_octree_load": (st, [ctypes.c_char_p, p, u32, p, p, u64, u64, p, sz, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -454,3 +479,133 @@ def build_octree(pts, prm, stream=None):
     return dict(cube=cube, preview=prev, preview_count=prev_n, counts=counts, chunks=chunks, num_chunks=num_chunks,
                 lut=lut, offsets=offsets, dist=dist, perm=perm, nodes=nodes, num_nodes=num_nodes, leaf_pts=leaf_pts,
                 leaf_perm=leaf_perm, owner=owner, final=final, final_perm=final_perm)
+
+
+# ------------------------------------------------------- octree file, cache
+def fp_cloud_digest(pts, stream=None):
+    """64-bit digest of a cloud (every point and the order): the cache key."""
+    d = torch.zeros(1, dtype=torch.int64, device=_dev(pts))
+    _check(load().fp_cloud_digest(_ptr(pts), pts.shape[0], _ptr(d), _stream(stream)), "fp_cloud_digest")
+    return int(d.item()) & 0xFFFFFFFFFFFFFFFF
+
+
+def _staging(staging, nbytes=64 << 20):
+    return staging if staging is not None else torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+
+
+def octree_save(path, prm, out, digest=0, with_perm=True, staging=None, stream=None):
+    """Writes the octree of build_octree() (device outputs: cube, nodes,
+    num_nodes, final, final_perm) to one file."""
+    stg = _staging(staging)
+    n = out["final"].shape[0] if out.get("n") is None else out["n"]
+    _check(load().fp_octree_save(os.fsencode(path), ctypes.byref(prm), _ptr(out["cube"]), _ptr(out["nodes"]),
+                                 _ptr(out["num_nodes"]), _ptr(out["final"]),
+                                 _ptr(out["final_perm"]) if with_perm else None, n, digest & 0xFFFFFFFFFFFFFFFF,
+                                 _ptr(stg), stg.numel(), _stream(stream)), "fp_octree_save")
+
+
+def octree_header(path):
+    h = fp_file_header()
+    _check(load().fp_octree_read_header(os.fsencode(path), ctypes.byref(h)), "fp_octree_read_header")
+    return h
+
+
+def octree_load(path, nodes=True, first=0, count=None, perm=True, device=None, staging=None, stream=None):
+    """Node table and final points [first, first + count) (all by default) of an
+    octree file, as device tensors: dict(header, nodes, num_nodes, final, final_perm)."""
+    h = octree_header(path)
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    count = h.n - first if count is None else count
+    stg = _staging(staging)
+    d_nodes = torch.zeros((max(h.num_nodes, 1), NODE_BYTES // 8), dtype=torch.int64, device=dev) if nodes else None
+    pts = torch.empty((max(count, 1), 4), dtype=torch.int32, device=dev)
+    prm_ = torch.empty(max(count, 1), dtype=torch.int32, device=dev) if perm and (h.flags & FILE_HAS_PERM) else None
+    _check(load().fp_octree_load(os.fsencode(path), _ptr(d_nodes), h.num_nodes, _ptr(pts), _ptr(prm_), first, count,
+                                 _ptr(stg), stg.numel(), _stream(stream)), "fp_octree_load")
+    num = torch.tensor([h.num_nodes], dtype=torch.int32, device=dev)
+    return dict(header=h, nodes=d_nodes, num_nodes=num, final=pts[:count], final_perm=None if prm_ is None else prm_[:count])
+
+
+def cache_path(cache_dir, digest, prm):
+    key = "%016x_g%d_s%d_l%d_m%d_t%d_c%d" % (digest, prm.grid_log2, prm.sub_log2, prm.max_level, prm.decim_modulus,
+                                             prm.chunk_threshold, prm.node_capacity)
+    return os.path.join(cache_dir, key + ".fpo")
+
+
+def cached_build(pts, prm, cache_dir, stream=None, staging=None):
+    """The octree of a cloud, from the cache when this cloud was built before
+    with these parameters (same digest, same n), else built and saved.
+    Returns (outputs, hit): outputs hold nodes, num_nodes, final, final_perm."""
+    digest = fp_cloud_digest(pts, stream)
+    path = cache_path(cache_dir, digest, prm)
+    if os.path.exists(path):
+        try:
+            h = octree_header(path)
+            if h.n == pts.shape[0] and h.digest == digest:
+                return octree_load(path, device=pts.device, staging=staging, stream=stream), True
+        except FastPointsError:
+            pass   # unreadable entry: rebuilt and replaced below
+    out = build_octree(pts, prm, stream=stream)
+    os.makedirs(cache_dir, exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    octree_save(tmp, prm, out, digest=digest, staging=staging, stream=stream)
+    os.replace(tmp, path)
+    return out, False
+
+
+# ------------------------------------------------------ rendering, headless
+def view_projection(eye, target, up=(0.0, 0.0, 1.0), fovy_deg=60.0, aspect=16 / 9, near=1.0, far=1e7):
+    """Row-major 4x4 perspective view-projection (clip z in [0, w]) as 16 fp32 values."""
+    import numpy as np
+    eye, target, up = (np.asarray(v, dtype=np.float64) for v in (eye, target, up))
+    f = target - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    view = np.eye(4)
+    view[0, :3], view[1, :3], view[2, :3] = r, u, -f
+    view[:3, 3] = -view[:3, :3] @ eye
+    t = 1.0 / np.tan(np.radians(fovy_deg) / 2)
+    proj = np.zeros((4, 4))
+    proj[0, 0], proj[1, 1] = t / aspect, t
+    proj[2, 2], proj[2, 3] = far / (near - far), near * far / (near - far)
+    proj[3, 2] = -1.0
+    return (proj @ view).astype(np.float32).reshape(16)
+
+
+def camera(m, width, height, min_node_px):
+    c = fp_camera()
+    for i, v in enumerate(m):
+        c.m[i] = float(v)
+    c.width, c.height, c.min_node_px = width, height, min_node_px
+    return c
+
+
+def render_workspace_size(node_cap):
+    return int(load().fp_render_workspace_size(node_cap))
+
+
+def fp_select_nodes(nodes, num_nodes, cube, cam, ws=None, stream=None):
+    """(selected ids, count, total kept points) of the nodes the camera draws."""
+    cap = nodes.shape[0]
+    dev = nodes.device
+    ids = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    npts = torch.zeros(1, dtype=torch.int64, device=dev)
+    w = ws if ws is not None else torch.empty(max(render_workspace_size(cap), 1), dtype=torch.uint8, device=dev)
+    _check(load().fp_select_nodes(_ptr(nodes), _ptr(num_nodes), cap, _ptr(cube), ctypes.byref(cam), _ptr(ids),
+                                  _ptr(nsel), _ptr(npts), _ptr(w), w.numel(), _stream(stream)), "fp_select_nodes")
+    return ids, nsel, npts
+
+
+def fp_rasterize(nodes, ids, nsel, final, cam, fb=None, ws=None, stream=None):
+    """Framebuffer (height, width) int64: (depth bits << 32 | rgba) of the nearest point, -1 where empty."""
+    cap = nodes.shape[0]
+    dev = nodes.device
+    if fb is None:
+        fb = torch.empty((cam.height, cam.width), dtype=torch.int64, device=dev)
+    w = ws if ws is not None else torch.empty(max(render_workspace_size(cap), 1), dtype=torch.uint8, device=dev)
+    _check(load().fp_rasterize(_ptr(nodes), _ptr(ids), _ptr(nsel), cap, _ptr(final), final.shape[0],
+                               ctypes.byref(cam), _ptr(fb), _ptr(w), w.numel(), _stream(stream)), "fp_rasterize")
+    return fb

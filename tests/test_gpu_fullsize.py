@@ -144,6 +144,26 @@ def check_layout(fp, pts_dev, r, nodes, n, C, lmax):
         del seen
 
 
+def check_frame(fp, pts_np, r, nodes, cube):
+    lo = np.array([pts_np[a].min() for a in "xyz"], np.float64)
+    hi = np.array([pts_np[a].max() for a in "xyz"], np.float64)
+    c, size = (lo + hi) / 2, float((hi - lo).max())
+    m = fp.view_projection(c + np.array([0.45, -0.6, 0.25]) * size, c, fovy_deg=60, aspect=16 / 9,
+                           near=size * 1e-3, far=size * 10)
+    cam = fp.camera(m, 1920, 1080, 30.0)
+    M = len(nodes)
+    nd = r["nodes"][:M].contiguous()
+    ids, nsel, _ = fp.fp_select_nodes(nd, r["num_nodes"], r["cube"], cam)
+    fb = fp.fp_rasterize(nd, ids, nsel, r["final"], cam)
+    torch.cuda.synchronize()
+    ocam = oracle.camera(m, 1920, 1080, 30.0)
+    want_sel = oracle.render_select(nodes, cube, ocam)
+    k = int(nsel.item())
+    assert np.array_equal(ids[:k].cpu().numpy().view(np.uint32), want_sel)
+    fin = r["final"].cpu().numpy().view(np.uint8).reshape(-1, 16).copy().view(oracle.POINT).reshape(-1)
+    assert np.array_equal(fb.cpu().numpy().view(np.uint64), oracle.rasterize(nodes, want_sel, fin, ocam))
+
+
 @pytest.mark.parametrize("kind,n,seed,g,s,lmax,T,C", FULL)
 def test_full_size(gpu_lib, kind, n, seed, g, s, lmax, T, C):
     fp = gpu_lib
@@ -198,4 +218,7 @@ def test_full_size(gpu_lib, kind, n, seed, g, s, lmax, T, C):
     del perm_np
     # layout properties of the whole cloud
     check_layout(fp, pts, r, nodes, n, C, lmax)
+    # one headless frame of the whole octree (selection and framebuffer) against the oracle
+    if n <= 200_000_000:
+        check_frame(fp, pts_np, r, nodes, cube)
     assert fp.get_device_error() == 0

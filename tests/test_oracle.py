@@ -61,6 +61,23 @@ def test_preview_matches_independent_bigint_hash():
     assert len(oracle.decimate(pts[:100], 0, 7)[1]) == sum(brute.splitmix64(i) % 7 == 0 for i in range(100))
 
 
+def test_cloud_digest_bruteforce():
+    pts = synth.lidar(300, 9)
+    M = (1 << 64) - 1
+    want = len(pts)
+    for i, w in enumerate(pts.view(np.uint32).reshape(-1, 4).tolist()):
+        a, b = w[0] | (w[1] << 32), w[2] | (w[3] << 32)
+        want += brute.splitmix64(brute.splitmix64(i) ^ brute.splitmix64(a) ^ brute.splitmix64(b ^ 0x5851F42D4C957F2D))
+    assert oracle.cloud_digest(pts) == want & M
+    assert oracle.cloud_digest(pts[:0]) == 0
+    swapped = pts.copy()
+    swapped[[3, 4]] = swapped[[4, 3]]
+    assert oracle.cloud_digest(swapped) != oracle.cloud_digest(pts)   # order matters
+    moved = pts.copy()
+    moved["x"][7] += 1
+    assert oracle.cloud_digest(moved) != oracle.cloud_digest(pts)
+
+
 def test_preview_modulus_closed_forms():
     # ceil(n / target), at least 1; the 1B-point cloud at a 1M-point budget keeps every 1000th hash
     assert oracle.preview_modulus(10 ** 9, 10 ** 6) == 1000
@@ -400,3 +417,71 @@ def test_octree_independent_of_grid_and_threshold():
         if ref is None:
             ref = key
         assert key == ref, (g, T)
+
+
+# ------------------------------------------------------------------ rendering
+def _ortho(sx, ox, sy, oy, sz, oz):
+    """clip = (sx x + ox, sy y + oy, sz z + oz, 1): exact for power-of-two scales and integer inputs"""
+    m = np.zeros(16, np.float32)
+    m[0], m[3], m[5], m[7], m[10], m[11], m[15] = sx, ox, sy, oy, sz, oz, 1.0
+    return m
+
+
+def _cube_cloud(n, seed):
+    """points in [0, 1024)^3 with the two corners present, so the cube is exactly [0, 1024)"""
+    rnd = np.random.default_rng(seed)
+    xyz = rnd.integers(0, 1024, size=(n, 3))
+    xyz[0], xyz[1] = 0, 1023
+    rgba = rnd.integers(0, 256, size=(n, 4))
+    pts = make_pts(xyz.tolist())
+    pts["r"], pts["g"], pts["b"], pts["a"] = rgba.T
+    return pts
+
+
+def _tree(pts, s=3, lmax=6, C=60):
+    prm = oracle.params(2, s, lmax, 16, 10 ** 9, C)
+    cube = oracle.bounds(pts)
+    return cube, oracle.octree_lod(pts, cube, prm)
+
+
+def test_render_orthographic_closed_form():
+    pts = _cube_cloud(3000, 1)
+    cube, t = _tree(pts)
+    assert int(cube["S"][0]) == 1024
+    cam = oracle.camera(_ortho(1 / 512, -1, 1 / 512, -1, 1 / 1024, 0), 64, 64, 0.0)
+    sel = oracle.render_select(t["nodes"], cube, cam)
+    assert sel.tolist() == list(range(len(t["nodes"])))   # in view, refined down to the leaves
+    fb = oracle.rasterize(t["nodes"], sel, t["final_pts"], cam)
+    # pixel = (x // 16, y // 16), depth = z / 1024 exactly; the smallest (depth, rgba) wins
+    want = np.full((64, 64), np.uint64(0xFFFFFFFFFFFFFFFF))
+    d = (pts["z"].astype(np.float32) / np.float32(1024)).view(np.uint32).astype(np.uint64)
+    rgba = pts.view(np.uint32).reshape(-1, 4)[:, 3].astype(np.uint64)   # the record's fourth word
+    key = (d << np.uint64(32)) | rgba
+    for x, y, k in zip(pts["x"] // 16, pts["y"] // 16, key):
+        want[y, x] = min(want[y, x], k)
+    assert np.array_equal(fb, want)
+
+
+def test_render_selection_frustum_and_size():
+    pts = _cube_cloud(5000, 2)
+    cube, t = _tree(pts)
+    nodes = t["nodes"]
+    # half the cube in view (x in [0, 512] maps to [-1, 1]): a node is drawn iff its box starts at x <= 512
+    cam = oracle.camera(_ortho(1 / 256, -1, 1 / 512, -1, 1 / 1024, 0), 64, 64, 0.0)
+    sel = set(oracle.render_select(nodes, cube, cam).tolist())
+    for i, nd in enumerate(nodes):
+        L = int(nd["level"])
+        c = sum(((int(nd["key"]) >> (3 * b + 2)) & 1) << b for b in range(L))
+        lo_x = -(-(c * 1024) // (1 << L))   # ceil(c S / 2^L)
+        assert (i in sel) == (lo_x <= 512), (i, L, lo_x)
+    # size threshold: a level-L box spans 1024 / 2^L - 1 units = (64 / 2^L - 1/16) pixels
+    cam = oracle.camera(_ortho(1 / 512, -1, 1 / 512, -1, 1 / 1024, 0), 64, 64, 10.0)
+    sel = oracle.render_select(nodes, cube, cam)
+    assert sel.tolist() == [i for i, nd in enumerate(nodes) if nd["level"] <= 3]
+    # nothing in view: the camera looks away (w < 0 everywhere)
+    m = _ortho(1 / 512, -1, 1 / 512, -1, 1 / 1024, 0)
+    m[15] = -1.0
+    assert len(oracle.render_select(nodes, cube, oracle.camera(m, 64, 64, 0.0))) == 0
+    # a huge threshold draws the root only
+    assert oracle.render_select(nodes, cube, oracle.camera(_ortho(1 / 512, -1, 1 / 512, -1, 1 / 1024, 0), 64, 64,
+                                                           1e9)).tolist() == [0]
