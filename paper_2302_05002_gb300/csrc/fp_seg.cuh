@@ -56,6 +56,11 @@ struct SegArgs {
 
     const uint32_t* d_fail;
     uint32_t* err;
+
+    // distribution (DIST): the digit is the chunk of the point's level-g cell
+    const fp_cube* cube;
+    const uint32_t* lut;
+    int g;
 };
 
 template <bool CPT, int MAXB>
@@ -74,10 +79,16 @@ struct SegSmem {
     static constexpr size_t total = pt + gbase + val + cnt + off + pos + dig + whist + misc + tiles;
 };
 
-template <bool CPT, int MAXB>
+template <bool CPT, int MAXB, bool DIST = false>
 __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegArgs a)
 {
     if (*a.d_fail) return;
+    CubeDev cube;
+    float scale_g = 0.f;
+    if (DIST) {
+        cube = load_cube(a.cube);
+        scale_g = scale_at(cube, a.g);
+    }
     using SM = SegSmem<CPT, MAXB>;
     using dig_t = typename SM::dig_t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -123,7 +134,23 @@ __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegAr
 #pragma unroll
         for (int r = 0; r < kSortIPT; ++r) {
             const int p = warp * (kSortIPT * 32) + r * 32 + lane;
-            dg[r] = p < tn ? a.id_in[base + p] - lo : 0xFFFFFFFFu;
+            if (DIST) {
+                uint32_t cell = 0;
+                if (p < tn) {
+                    const int4 q = __ldg(a.pt_in + base + p);
+                    cell = key_small(q.x, q.y, q.z, cube, scale_g, a.g);
+                }
+                dg[r] = cell;
+            } else {
+                dg[r] = p < tn ? a.id_in[base + p] - lo : 0xFFFFFFFFu;
+            }
+        }
+        if (DIST) {   // cell -> chunk, all gathers in flight together
+#pragma unroll
+            for (int r = 0; r < kSortIPT; ++r) {
+                const int p = warp * (kSortIPT * 32) + r * 32 + lane;
+                dg[r] = p < tn ? a.lut[dg[r]] - lo : 0xFFFFFFFFu;
+            }
         }
         uint32_t pack[kSortIPT];
 #pragma unroll
@@ -183,7 +210,7 @@ __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegAr
                 const uint32_t lp = s_off[d] + s_whist[warp * nb + d] + (pack[r] >> 16);
                 const uint64_t i = base + p;
                 if (CPT) s_pt[lp] = __ldg(a.pt_in + i);
-                s_val[lp] = a.val_in[i];
+                s_val[lp] = DIST ? (uint32_t)i : a.val_in[i];
                 s_pos[lp] = (uint16_t)p;
                 s_dig[lp] = (dig_t)d;
             }
@@ -251,6 +278,15 @@ struct SegCall {
     // owner layout: staging
     uint64_t* st_key; uint32_t* st_src; uint32_t* st_count; int st_shift;
 };
+
+// Distribution of n points into 257..2048 chunks in one sweep: one segment
+// (the whole array), digit = chunk of the point's cell, bucket bases = the
+// chunk offsets.  Runs only when *d_num_chunks lies in that range; *run_sort
+// is set to 1 otherwise (the radix passes run instead), 0 when it ran.
+size_t dist_wide_bytes(uint64_t n);
+cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
+                      const uint64_t* offsets, const uint32_t* num_chunks, int4* out, uint32_t* perm,
+                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st);
 
 // Setup (chunk node ids, digits, tiles), status reset, both pass variants.
 // Afterwards cnt[2] != 0 means a chunk did not fit (the caller's whole-array

@@ -6,7 +6,7 @@
 // (lut); the bucket bases are the chunk offsets, so with at most 1024 chunks a
 // single pass reads each point once and writes it once.  More chunks take two
 // or three least-significant-digit-first passes, chosen on the device.
-#include "fp_sort.cuh"
+#include "fp_seg.cuh"
 
 namespace fp {
 
@@ -247,7 +247,8 @@ cudaError_t sort_plan_keys(const SortScratch& sc, const uint64_t* keys, uint64_t
 size_t distribute_ws_bytes(uint64_t n, int g)
 {
     (void)g;
-    return sort_scratch_bytes(n) + Workspace::bytes_for({16 * (size_t)n, 4 * (size_t)n});
+    return sort_scratch_bytes(n) + Workspace::bytes_for({16 * (size_t)n, 4 * (size_t)n, sizeof(uint32_t)}) +
+           dist_wide_bytes(n);
 }
 
 cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
@@ -258,9 +259,15 @@ cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cu
     SortScratch sc = take_sort_scratch(ws, n);
     int4* pt_tmp = ws.take<int4>(n);
     uint32_t* val_tmp = ws.take<uint32_t>(n);
-    // bucket weights = chunk counts (offsets[c+1] - offsets[c])
-    cudaError_t e = sort_plan_weights(sc, nullptr, offsets, num_chunks, 1ull << (3 * g), 0, st);
+    uint32_t* run_sort = ws.take<uint32_t>(1);
+    Workspace rest = ws;
+    // 257..2048 chunks: one sweep with chunk digits (no plan, bases = offsets);
+    // otherwise the radix passes below (one pass up to 256 chunks)
+    cudaError_t e = dist_wide(reinterpret_cast<const int4*>(pts), n, cube, g, lut, offsets, num_chunks,
+                              reinterpret_cast<int4*>(out), perm, run_sort, rest, st);
     if (e) return e;
+    // bucket weights = chunk counts (offsets[c+1] - offsets[c])
+    if ((e = sort_plan_weights(sc, nullptr, offsets, num_chunks, 1ull << (3 * g), 0, st))) return e;
     SortArgs a{};
     a.b.pt_src = reinterpret_cast<const int4*>(pts);
     a.b.pt_tmp = pt_tmp;
@@ -273,6 +280,7 @@ cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cu
     a.lut = lut;
     a.g = g;
     a.err = ws.err;
+    a.run_if = run_sort;
     for (int slot = 0; slot < kSortMaxPass; ++slot) {
         e = sort_run_pass<DIG_CHUNK, true, false, false>(sc, a, slot, ws.num_sms, st);
         if (e) return e;

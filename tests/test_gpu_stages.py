@@ -29,8 +29,9 @@ def cloud(kind, n, seed):
 
 CASES = [
     ("uniform", 1_000_000, 1, 7, 100_000),     # the 1M-point uniform workload
-    ("uniform", 300_001, 5, 7, 2_000),         # ragged tail, ~150 chunks
-    ("lidar", 400_000, 2, 7, 1_000),           # > 1024 chunks: multi-digit scatter
+    ("uniform", 300_001, 5, 7, 2_000),         # ragged tail, 512 chunks: one sweep with chunk digits
+    ("lidar", 400_000, 2, 7, 1_000),           # 1409 chunks: one sweep with chunk digits
+    ("uniform", 2_000_003, 12, 7, 1_000),      # 4096 chunks: two radix passes
     ("lidar", 50_000, 3, 7, 1),                # every cell its own chunk
     ("dups", 40_000, 4, 3, 50),
     ("extremes", 8_193, 6, 7, 100),
