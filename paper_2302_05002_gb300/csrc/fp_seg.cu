@@ -122,6 +122,8 @@ static cudaError_t seg_launch(SegArgs a, const SegScratch& sc, int v, int num_sm
 // ------------------------------------------------ distribution in one sweep
 // one segment [0, n) with K digits when 256 < K <= 2048: its tiles, the
 // segment bounds, and the flag that gates the radix passes
+constexpr int kDistMidBits = 9;   // up to 512 chunks: two CTAs per SM
+
 __global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint64_t* seg_off, uint32_t* seg_lo,
                              uint32_t* seg_nb, SegTile* tiles, uint32_t* cnt, uint32_t* run_sort)
 {
@@ -132,13 +134,15 @@ __global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint64_t* s
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += stride)
         tiles[t] = SegTile{0u, (uint32_t)t};
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const bool mid = K <= (1u << kDistMidBits);
         seg_off[0] = 0;
         seg_off[1] = n;
         seg_lo[0] = 0;
         seg_nb[0] = wide ? K : 1u;
-        cnt[0] = (uint32_t)ntl;   // tiles of the pass
-        cnt[1] = 0;               // tile counter
-        cnt[2] = 0;               // fail word (never set here)
+        cnt[0] = mid ? (uint32_t)ntl : 0u;   // tiles of the 9-bit pass
+        cnt[3] = mid ? 0u : (uint32_t)ntl;   // tiles of the 11-bit pass
+        cnt[1] = cnt[4] = 0;                 // tile counters
+        cnt[2] = 0;                          // fail word (never set here)
         *run_sort = wide ? 0u : 1u;
     }
 }
@@ -158,10 +162,25 @@ static DistScratch dist_carve(const Workspace& ws, uint64_t n)
     d.seg_off = ws.take<uint64_t>(2);
     d.lo = ws.take<uint32_t>(1);
     d.nb = ws.take<uint32_t>(1);
-    d.cnt = ws.take<uint32_t>(4);
+    d.cnt = ws.take<uint32_t>(8);
     d.tiles = ws.take<SegTile>(T);
     d.status = ws.take<uint32_t>(T << kSegMaxBits);
     return d;
+}
+
+template <int MAXB>
+static cudaError_t dist_launch(const SegArgs& a, uint64_t ntiles, int num_sms, cudaStream_t st)
+{
+    using SM = SegSmem<true, MAXB, true>;
+    auto kern = k_seg_pass<true, MAXB, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::total);
+    if (e) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSortNT, SM::total))) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, (uint64_t)num_sms * per_sm));
+    kern<<<grid, kSortNT, SM::total, st>>>(a);
+    return cudaGetLastError();
 }
 
 size_t dist_wide_bytes(uint64_t n)
@@ -179,7 +198,8 @@ cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, c
     const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((d.ntiles + 255) / 256, (uint64_t)ws.num_sms * 4));
     k_dist_setup<<<gs, 256, 0, st>>>(num_chunks, n, d.seg_off, d.lo, d.nb, d.tiles, d.cnt, run_sort);
     const int gz = std::max(1, ws.num_sms * 8);
-    k_seg_zero<kSegMaxBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
+    k_seg_zero<kDistMidBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
+    k_seg_zero<kSegMaxBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt + 3, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
     SegArgs a{};
     a.pt_in = pts; a.pt_out = out;
     a.val_in = nullptr; a.val_out = perm;
@@ -193,16 +213,11 @@ cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, c
     a.d_fail = d.cnt + 2;
     a.err = ws.err;
     a.cube = cube; a.lut = lut; a.g = g;
-    using SM = SegSmem<true, kSegMaxBits>;
-    auto kern = k_seg_pass<true, kSegMaxBits, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::total);
-    if (e) return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSortNT, SM::total))) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(d.ntiles, (uint64_t)ws.num_sms * per_sm));
-    kern<<<grid, kSortNT, SM::total, st>>>(a);
-    return cudaGetLastError();
+    cudaError_t e;
+    a.d_ntiles = d.cnt; a.counter = d.cnt + 1;
+    if ((e = dist_launch<kDistMidBits>(a, d.ntiles, ws.num_sms, st))) return e;
+    a.d_ntiles = d.cnt + 3; a.counter = d.cnt + 4;
+    return dist_launch<kSegMaxBits>(a, d.ntiles, ws.num_sms, st);
 }
 
 cudaError_t seg_scatter(const SegScratch& sc, const SegCall& c, const Workspace& ws, cudaStream_t st)

@@ -63,7 +63,7 @@ struct SegArgs {
     int g;
 };
 
-template <bool CPT, int MAXB>
+template <bool CPT, int MAXB, bool DIST = false>
 struct SegSmem {
     using dig_t = typename std::conditional<(MAXB <= 8), uint8_t, uint16_t>::type;
     static constexpr size_t pt = CPT ? sizeof(int4) * kSortTile : 0;
@@ -71,7 +71,7 @@ struct SegSmem {
     static constexpr size_t val = sizeof(uint32_t) * kSortTile;
     static constexpr size_t cnt = sizeof(uint32_t) * (1 << MAXB);
     static constexpr size_t off = sizeof(uint32_t) * (1 << MAXB);
-    static constexpr size_t pos = sizeof(uint16_t) * kSortTile;   // tile position of a staged record
+    static constexpr size_t pos = DIST ? 0 : sizeof(uint16_t) * kSortTile;   // tile position of a staged record
     static constexpr size_t dig = sizeof(dig_t) * kSortTile;
     static constexpr size_t whist = sizeof(uint16_t) * kSortWarps * (1 << MAXB);
     static constexpr size_t misc = 4 * (1 + kSortWarps + 15);
@@ -79,8 +79,13 @@ struct SegSmem {
     static constexpr size_t total = pt + gbase + val + cnt + off + pos + dig + whist + misc + tiles;
 };
 
+// two CTAs per SM while the shared memory allows it (8-bit digits; 9-bit
+// digits without the staging positions, i.e. in the distribution)
+template <bool CPT, int MAXB, bool DIST>
+constexpr int seg_ctas() { return SegSmem<CPT, MAXB, DIST>::total <= 113 * 1024 ? 2 : 1; }
+
 template <bool CPT, int MAXB, bool DIST = false>
-__global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegArgs a)
+__global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_pass(SegArgs a)
 {
     if (*a.d_fail) return;
     CubeDev cube;
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegAr
         cube = load_cube(a.cube);
         scale_g = scale_at(cube, a.g);
     }
-    using SM = SegSmem<CPT, MAXB>;
+    using SM = SegSmem<CPT, MAXB, DIST>;
     using dig_t = typename SM::dig_t;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* sp = smem;
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(kSortNT, (MAXB <= 8 ? 2 : 1)) k_seg_pass(SegAr
                 const uint64_t i = base + p;
                 if (CPT) s_pt[lp] = __ldg(a.pt_in + i);
                 s_val[lp] = DIST ? (uint32_t)i : a.val_in[i];
-                s_pos[lp] = (uint16_t)p;
+                if (!DIST) s_pos[lp] = (uint16_t)p;
                 s_dig[lp] = (dig_t)d;
             }
         }
