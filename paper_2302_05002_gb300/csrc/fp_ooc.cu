@@ -14,10 +14,13 @@
 // Passes over the host points (pieces of piece_points, double-buffered copies
 // on a side stream): bounds + preview, counts, and the distribution into the
 // host store (each piece scattered by chunk at per-chunk cursors); then the
-// groups are read back from the store.  The pinned
-// host scratch is the out-of-core store between passes: the distributed points
-// and original indices of every group, the two levels and the owner of every
-// point, and the staged records.
+// groups are read back from the store -- unless the arena holds the whole
+// distributed cloud next to a group as large as the largest chunk, in which
+// case pass 3 also writes it to the device and the group passes read it there
+// (a cloud up to about half the arena in size crosses the link three times
+// fewer).  The pinned host scratch is the out-of-core store between passes:
+// the distributed points and original indices of every group, the two levels
+// and the owner of every point, and the staged records.
 #include <algorithm>
 #include <vector>
 #include "fp_sort.cuh"
@@ -86,10 +89,12 @@ __global__ void k_piece_hist(const fp_point* pts, uint64_t n, const fp_cube* cub
 }
 
 // a piece scattered stably by chunk: its run of chunk c lands at the chunk's cursor
-// in the whole cloud's distributed order (host store)
+// in the whole cloud's distributed order (the host store, or the device when the
+// cloud stays resident)
 __global__ void k_piece_scatter(const int4* dpts, const uint32_t* dperm, uint64_t n, const fp_cube* cube, int g,
                                 const uint32_t* lut, const uint64_t* poff, const uint64_t* ccur, uint64_t base,
-                                int4* h_pts, uint32_t* h_perm, uint64_t n_all, uint32_t* err)
+                                int4* h_pts, uint32_t* h_perm, int4* d_pts, uint32_t* d_perm, uint64_t n_all,
+                                uint32_t* err)
 {
     const CubeDev c = load_cube(cube);
     const float sg = scale_at(c, g);
@@ -98,8 +103,14 @@ __global__ void k_piece_scatter(const int4* dpts, const uint32_t* dperm, uint64_
         const uint32_t ch = __ldg(lut + key_small(p.x, p.y, p.z, c, sg, g));
         const uint64_t dest = ccur[ch] + (q - poff[ch]);
         if (dest >= n_all) { raise(err, FP_ERR_CAPACITY); continue; }
-        h_pts[dest] = p;
-        h_perm[dest] = (uint32_t)(base + dperm[q]);
+        if (h_pts) {
+            h_pts[dest] = p;
+            h_perm[dest] = (uint32_t)(base + dperm[q]);
+        }
+        if (d_pts) {   // the resident copy on the device
+            d_pts[dest] = p;
+            d_perm[dest] = (uint32_t)(base + dperm[q]);
+        }
     }
 }
 
@@ -157,7 +168,7 @@ __global__ void k_group_place(const uint64_t* key, const uint32_t* src, uint64_t
                               const fp_node* nodes, uint32_t M, uint64_t T, int g, const uint64_t* first,
                               const int4* pts, const uint32_t* perm, uint64_t group_base, int4* h_final,
                               uint32_t* h_final_perm, uint64_t n_all, uint64_t* h_st_key, uint32_t* h_st_src,
-                              uint64_t* st_run, uint64_t st_cap, int pbits, uint32_t* err)
+                              int4* h_st_pt, uint64_t* st_run, uint64_t st_cap, int pbits, uint32_t* err)
 {
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t X = (uint32_t)key[t];
@@ -174,24 +185,28 @@ __global__ void k_group_place(const uint64_t* key, const uint32_t* src, uint64_t
             if (o >= st_cap) { raise(err, FP_ERR_CAPACITY); continue; }
             h_st_key[o] = ((uint64_t)X << pbits) | perm[j];
             h_st_src[o] = (uint32_t)(group_base + j);
+            if (h_st_pt) h_st_pt[o] = pts[j];   // the point itself (no host store of the cloud)
         }
     }
 }
 
-// staged records sorted by (owner, index): position first[owner] + rank
+// staged records sorted by (owner, index): position first[owner] + rank.  The
+// point comes from the host store, or (staged_pts) from its staged copy, the
+// index from the key.
 __global__ void k_stitch_final(const uint64_t* key, const uint32_t* val, uint64_t S, int pbits, const uint32_t* soff,
                                const uint64_t* first, const uint32_t* h_st_src, const int4* h_pts,
-                               const uint32_t* h_perm, int4* h_final, uint32_t* h_final_perm, uint64_t n_all,
-                               uint32_t M, uint32_t* err)
+                               const uint32_t* h_perm, int staged_pts, int4* h_final, uint32_t* h_final_perm,
+                               uint64_t n_all, uint32_t M, uint32_t* err)
 {
+    const uint64_t imask = (1ull << pbits) - 1;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < S; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t X = key[t] >> pbits;
         if (X >= M) { raise(err, FP_ERR_CAPACITY); continue; }
         const uint64_t f = first[X] + (t - soff[X]);
-        const uint32_t j = h_st_src[val[t]];
+        const uint32_t j = staged_pts ? val[t] : h_st_src[val[t]];
         if (f >= n_all || j >= n_all) { raise(err, FP_ERR_CAPACITY); continue; }
         h_final[f] = h_pts[j];
-        h_final_perm[f] = h_perm[j];
+        h_final_perm[f] = staged_pts ? (uint32_t)(key[t] & imask) : h_perm[j];
     }
 }
 
@@ -301,7 +316,8 @@ Fixed fixed_carve(const Workspace& w, uint64_t P, const fp_params& p, uint64_t n
 }
 
 struct Group {   // device buffers of one chunk group (G points), reused group after group
-    int4* pts;      // first: the start of the group region
+    char* region;   // the start of the group region
+    int4* pts;
     uint32_t *perm, *owner;
     uint8_t *own, *leaf;
     uint64_t *key, *key2, *key3;
@@ -320,12 +336,16 @@ size_t stage_ws(uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, i
     return w;
 }
 
-Group group_carve(const Workspace& w, uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+// resident: the group's points and indices are a slice of the resident
+// distributed cloud (set per group), not carved here
+Group group_carve(const Workspace& w, uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms,
+                  bool resident = false)
 {
     Group g;
     const uint64_t N = G ? G : 1;
-    g.pts = w.take<int4>(N);
-    g.perm = w.take<uint32_t>(N);
+    g.region = w.base + w.used;
+    g.pts = resident ? nullptr : w.take<int4>(N);
+    g.perm = resident ? nullptr : w.take<uint32_t>(N);
     g.owner = w.take<uint32_t>(N);
     g.own = w.take<uint8_t>(N);
     g.leaf = w.take<uint8_t>(N);
@@ -346,22 +366,27 @@ size_t fixed_bytes(uint64_t P, const fp_params& p, uint64_t node_cap)
     return dry.used;
 }
 
-size_t group_bytes(uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+size_t group_bytes(uint64_t G, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms, bool resident = false)
 {
     Workspace dry;
-    group_carve(dry, G, P, p, node_cap, num_sms);
+    group_carve(dry, G, P, p, node_cap, num_sms, resident);
     return dry.used;
 }
 
-// the largest group (points) that fits next to the fixed buffers
-uint64_t group_cap_for(size_t arena, uint64_t n, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms)
+// the distributed cloud and its original indices kept in the arena
+size_t resident_bytes(uint64_t n) { return Workspace::bytes_for({16 * (n ? n : 1), 4 * (n ? n : 1)}); }
+
+// the largest group (points) that fits next to the fixed buffers (and the
+// resident cloud)
+uint64_t group_cap_for(size_t arena, uint64_t n, uint64_t P, const fp_params& p, uint64_t node_cap, int num_sms,
+                       bool resident = false)
 {
-    const size_t fixed = fixed_bytes(P, p, node_cap);
+    const size_t fixed = fixed_bytes(P, p, node_cap) + (resident ? resident_bytes(n) : 0);
     if (arena <= fixed) return 0;
     uint64_t lo = 0, hi = std::max<uint64_t>(n, 1);
     while (lo < hi) {
         const uint64_t mid = (lo + hi + 1) / 2;
-        if (fixed + group_bytes(mid, P, p, node_cap, num_sms) <= arena) lo = mid;
+        if (fixed + group_bytes(mid, P, p, node_cap, num_sms, resident) <= arena) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -444,7 +469,8 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     if (G == 0) return FP_ERR_WORKSPACE;
     Workspace w = base;
     const Fixed F = fixed_carve(w, P, prm, node_cap, base.num_sms);
-    const Group B = group_carve(w, G, P, prm, node_cap, base.num_sms);
+    const size_t after_fixed = w.used;
+    Group B = group_carve(w, G, P, prm, node_cap, base.num_sms);
     Workspace ws = base;   // stage workspace view
     ws.base = B.ws;
     ws.bytes = B.ws_bytes;
@@ -490,6 +516,31 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         return cu(e);
     if ((e = cudaStreamSynchronize(st))) return cu(e);
     if (off[K] != n) return FP_ERR_INVALID;
+    // When the arena holds the distributed cloud (points and indices) next to the
+    // fixed buffers and a group as large as the largest chunk, the cloud stays
+    // on the device after pass 3: the group passes read it in place instead of
+    // copying it back from the host store three times.
+    uint64_t biggest = 0;
+    for (uint32_t c = 0; c < K; ++c) biggest = std::max(biggest, off[c + 1] - off[c]);
+    int4* res_pts = nullptr;
+    uint32_t* res_perm = nullptr;
+    {
+        uint64_t Gr = group_cap_for(arena_bytes, n, P, prm, node_cap, base.num_sms, true);
+        if (group_points) Gr = std::min(Gr, group_points);
+        if (Gr >= biggest && Gr > 0) {
+            Workspace wr = base;
+            wr.used = after_fixed;
+            res_pts = wr.take<int4>(n ? n : 1);
+            res_perm = wr.take<uint32_t>(n ? n : 1);
+            G = Gr;
+            B = group_carve(wr, G, P, prm, node_cap, base.num_sms, true);
+            ws.base = B.ws;
+            ws.bytes = B.ws_bytes;
+            ws.used = 0;
+        }
+    }
+    const bool resident = res_pts != nullptr;
+
     // consecutive chunks while they fit a group
     std::vector<std::pair<uint32_t, uint32_t>> groups;
     for (uint32_t c0 = 0; c0 < K;) {
@@ -517,7 +568,9 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
                                    F.dperm, ws, st)))
             return x;
         k_piece_scatter<<<grid_for(np, base.num_sms), 256, 0, st>>>(F.dpiece, F.dperm, np, F.cube, g, F.lut, F.poff,
-                                                                    F.ccur, k * P, H.pts, H.perm, n, base.err);
+                                                                    F.ccur, k * P, resident ? nullptr : H.pts,
+                                                                    resident ? nullptr : H.perm, res_pts, res_perm, n,
+                                                                    base.err);
         k_cursor_advance<<<gK, 256, 0, st>>>(F.ccur, F.pcnt, K);
         return cudaGetLastError();
     });
@@ -530,8 +583,13 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
         k_group_tables<<<gc, 256, 0, st>>>(F.counts, F.lut, cells, c0, c1, F.rcounts, F.lut_local);
         k_group_offsets<<<gc, 256, 0, st>>>(F.offsets, c0, c1 - c0, F.off_local, F.kdev);
-        if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
-        if ((e = cudaMemcpyAsync(B.perm, H.perm + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
+        if (resident) {
+            B.pts = res_pts + b0;
+            B.perm = res_perm + b0;
+        } else {
+            if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
+            if ((e = cudaMemcpyAsync(B.perm, H.perm + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
+        }
         OctGroup grp{F.rcounts, (uint32_t)b0, B.own, B.leaf, F.recs, node_cap, F.num_deep};
         ws.used = 0;
         if ((e = launch_octree_impl(reinterpret_cast<const fp_point*>(B.pts), B.perm, ng, F.cube, F.chunks + c0,
@@ -551,7 +609,8 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     // ---- pass 4 per group: owner ids, owned counts
     for (auto [c0, c1] : groups) {
         const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
-        if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
+        if (resident) B.pts = res_pts + b0;
+        else if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
         if ((e = cudaMemcpyAsync(B.own, H.own + b0, ng, cudaMemcpyHostToDevice, st))) return cu(e);
         if ((e = cudaMemcpyAsync(B.leaf, H.leaf + b0, ng, cudaMemcpyHostToDevice, st))) return cu(e);
         if ((e = launch_octree_resolve(reinterpret_cast<const fp_point*>(B.pts), ng, F.cube, B.own, B.leaf, F.T, prm,
@@ -576,8 +635,13 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     const size_t ws_after_sc = ws.used;
     for (auto [c0, c1] : groups) {
         const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
-        if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
-        if ((e = cudaMemcpyAsync(B.perm, H.perm + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
+        if (resident) {
+            B.pts = res_pts + b0;
+            B.perm = res_perm + b0;
+        } else {
+            if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
+            if ((e = cudaMemcpyAsync(B.perm, H.perm + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
+        }
         if ((e = cudaMemcpyAsync(B.owner, H.owner + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
         k_owner_keys<<<grid_for(ng, base.num_sms), 256, 0, st>>>(B.owner, ng, B.key);
         ws.used = ws_after_sc;
@@ -591,7 +655,8 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         k_run_starts<<<grid_for(ng, base.num_sms), 256, 0, st>>>(B.key3, ng, 0, F.soff, M);
         k_group_place<<<grid_for(ng, base.num_sms), 256, 0, st>>>(
             B.key3, B.val3, ng, F.soff, F.nodes, M, prm.chunk_threshold, g, F.first, B.pts, B.perm, b0,
-            reinterpret_cast<int4*>(h_final), h_final_perm, n, H.st_key, H.st_src, F.st_run, n, pbits, base.err);
+            reinterpret_cast<int4*>(h_final), h_final_perm, n, H.st_key, H.st_src, resident ? H.pts : nullptr,
+            F.st_run, n, pbits, base.err);
         if ((e = cudaGetLastError())) return cu(e);
     }
 
@@ -601,8 +666,9 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     if ((e = cudaStreamSynchronize(st))) return cu(e);
     if (S) {   // the sort of the staged records reuses the whole group region
         Workspace wf = base;
-        wf.base = reinterpret_cast<char*>(B.pts);
-        wf.bytes = group_bytes(G, P, prm, node_cap, base.num_sms);
+        // (the resident cloud is dead by now: the staged points were copied out with their records)
+        wf.base = resident ? reinterpret_cast<char*>(res_pts) : B.region;
+        wf.bytes = group_bytes(G, P, prm, node_cap, base.num_sms, resident) + (resident ? resident_bytes(n) : 0);
         wf.used = 0;
         uint64_t* k1 = wf.take<uint64_t>(S);
         uint64_t* k2 = wf.take<uint64_t>(S);
@@ -621,7 +687,8 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
             if ((e = sort_run_pass<DIG_K64, false, true, false>(sf, a, slot, base.num_sms, st))) return cu(e);
         k_run_starts<<<grid_for(S, base.num_sms), 256, 0, st>>>(k3, S, pbits, F.soff, M);
         k_stitch_final<<<grid_for(S, base.num_sms), 256, 0, st>>>(k3, v3, S, pbits, F.soff, F.first, H.st_src, H.pts,
-                                                                  H.perm, reinterpret_cast<int4*>(h_final),
+                                                                  H.perm, resident ? 1 : 0,
+                                                                  reinterpret_cast<int4*>(h_final),
                                                                   h_final_perm, n, M, base.err);
         if ((e = cudaGetLastError())) return cu(e);
     }

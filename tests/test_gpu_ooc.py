@@ -28,6 +28,10 @@ CASES = [
     ("dups", 50_000, 43, 3, 3, 9, 1_000, 40, 8_192, 10_000),
     ("lidar", 120_000, 44, 6, 7, 14, 30_000, 3_000, 1 << 20, 0),        # one piece, one group
     ("uniform", 100_000, 45, 4, 4, 10, 2_000, 2_000, 25_000, 2_000),    # groups of about one chunk
+    # the minimum arena (about 300 MB) cannot also hold the 16M-point distributed cloud (320 MB):
+    # the groups come back from the host store (the cases above keep the cloud on the device);
+    # 64 chunks of level 2, few points kept above them
+    ("uniform", 16_000_000, 46, 5, 5, 12, 300_000, 20_000, 1 << 21, 0),
 ]
 
 
