@@ -36,6 +36,7 @@
 namespace fp {
 
 constexpr int kPieceMax = 1024;                 // largest piece handled in shared memory
+constexpr int kRoundLevels = 3;                 // levels a split round groups the open nodes' records by
 constexpr int kWindow = 1024;                   // pieces starting in one window form a unit
 constexpr int kUnitCap = kPieceMax + kWindow;   // records of one unit
 constexpr int kUnitNT = 512;
@@ -79,8 +80,6 @@ struct OctCtx {   // device pointers of one fp_build_chunk_octree call
     uint32_t piece_cap;
     uint32_t* dups;       // pieces of more than kPieceMax points (equal keys to the deepest level)
     uint32_t* ndups;
-    const uint32_t* deep; // nonzero: the cell grouping sorted every record down to level g + r1
-    int r1;
     NodeRec* nrec;
     uint32_t* nnode;
     uint32_t node_cap_ws;
@@ -156,20 +155,16 @@ FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, u
 // count grid was not the grid of these points (reported by k_cell_check).
 FP_DEV uint32_t cursor_slot(uint32_t m, int g) { return __brev(m) >> (32 - 3 * g); }
 
-__global__ void k_cell_cursor_init(const uint32_t* __restrict__ cstart, uint64_t cells, uint32_t* cursor, int g,
-                                   const uint32_t* run_if)
+__global__ void k_cell_cursor_init(const uint32_t* __restrict__ cstart, uint64_t cells, uint32_t* cursor, int g)
 {
-    if (!*run_if) return;
     for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x)
         cursor[cursor_slot((uint32_t)m, g)] = cstart[m];
 }
 
 __global__ void __launch_bounds__(256) k_cell_scatter(const int4* __restrict__ pts, uint64_t n, const fp_cube* cube_p,
                                                       uint32_t* cursor, uint64_t* __restrict__ gk,
-                                                      uint32_t* __restrict__ gj, int g, const uint32_t* run_if,
-                                                      uint32_t* err)
+                                                      uint32_t* __restrict__ gj, int g, uint32_t* err)
 {
-    if (!*run_if) return;
     const CubeDev cube = load_cube(cube_p);
     const int lane = threadIdx.x & 31;
     const int sh = 3 * (kKeyLevels - g);
@@ -197,9 +192,8 @@ __global__ void __launch_bounds__(256) k_cell_scatter(const int4* __restrict__ p
 }
 
 __global__ void k_cell_check(const uint32_t* __restrict__ cstart, uint64_t cells, const uint32_t* cursor, int g,
-                             const uint32_t* run_if, uint32_t* err)
+                             uint32_t* err)
 {
-    if (!*run_if) return;
     for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x)
         if (cursor[cursor_slot((uint32_t)m, g)] != cstart[m + 1]) raise(err, FP_ERR_CAPACITY);
 }
@@ -221,7 +215,7 @@ __global__ void k_cell_setup(OctCtx c, OpenNode* open0, uint32_t* nopen0)
     }
     c.cell_leaf[m] = hier;
     if (cnt <= (uint32_t)kPieceMax) {
-        emit_piece(c, c.cstart[m], cnt, c.g, hier, (uint8_t)c.g, *c.deep ? c.g + c.r1 : c.g);
+        emit_piece(c, c.cstart[m], cnt, c.g, hier, (uint8_t)c.g, c.g);
     } else {
         uint32_t id = atomicAdd(nopen0, 1u);
         if (id >= c.open_cap) { raise(c.err, FP_ERR_CAPACITY); return; }
@@ -256,8 +250,8 @@ __global__ void k_nodes_upper(OctCtx c)
     emit_node(c, k, L, cnt, c.cstart[k << (3 * (c.g - L))], leaf);
 }
 
-// ------------------------------------------------------- big cells: gather
-// big cell of a position of the gathered array (bigstart: exclusive prefix of the big cells' counts)
+// ------------------------------------------------------- big cells: rounds
+// position p of the records of the open nodes, copied out one node after another
 FP_DEV uint32_t big_of(const uint32_t* bigstart, uint32_t nb, uint32_t p)
 {
     uint32_t a = 0, b = nb;
@@ -265,45 +259,7 @@ FP_DEV uint32_t big_of(const uint32_t* bigstart, uint32_t nb, uint32_t p)
     return a - 1;
 }
 
-// Records of the open nodes at level q (more than kPieceMax points each), one
-// thread per record.  Key = (rank of the open node << 3 (21 - q)) | the key
-// bits below level q: sorting by the rank and the next levels' digits groups
-// the records by node and orders them by those levels, and the key stays
-// whole (the rank needs at most 21 bits, the rest 3 (21 - q) <= 42).
-__global__ void k_big_gather(const OpenNode* open, const uint32_t* nopen, const uint32_t* bigstart,
-                             const uint32_t* total, const uint64_t* gk, const uint32_t* gj, uint64_t* bk, uint32_t* bj,
-                             int q)
-{
-    const uint32_t nb = *nopen, T = *total;
-    const int low = 3 * (kKeyLevels - q);
-    const uint64_t low_mask = (1ull << low) - 1;
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
-        const uint32_t b = big_of(bigstart, nb, p);
-        const uint32_t src = open[b].begin + (p - bigstart[b]);
-        bk[p] = ((uint64_t)b << low) | (gk[src] & low_mask);
-        bj[p] = gj[src];
-    }
-}
-
-// write the sorted records back into their nodes' ranges, with their full keys
-__global__ void k_big_scatter(const OpenNode* open, const uint32_t* nopen, const uint32_t* bigstart,
-                              const uint32_t* total, const uint64_t* bk, const uint32_t* bj, uint64_t* gk,
-                              uint32_t* gj, int q)
-{
-    const uint32_t nb = *nopen, T = *total;
-    const int low = 3 * (kKeyLevels - q);
-    const uint64_t low_mask = (1ull << low) - 1;
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < T; p += gridDim.x * blockDim.x) {
-        const uint32_t b = big_of(bigstart, nb, p);
-        const uint32_t dst = open[b].begin + (p - bigstart[b]);
-        const uint64_t k = bk[p];
-        gk[dst] = (open[b].key << low) | (k & low_mask);
-        gj[dst] = bj[p];
-    }
-}
-
-// records of each open node to gather for a sort round; none when *d_skip > skip_min
-// (the records are already sorted deep enough)
+// records of each open node; a round's records are copied out compactly (bigstart)
 __global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uint32_t* cnt_out, uint32_t cap,
                               const uint64_t* d_skip, uint64_t skip_min)
 {
@@ -313,29 +269,97 @@ __global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uin
     cnt_out[i] = i < *nopen0 && !skip ? open0[i].count : 0;
 }
 
-// a one-pass plan: the deeper grouping's passes (selected over it when it runs) or none
-__global__ void k_plan_one(SortPlan* p)
+// Counting slots of a round are digit-major (slot = d * cap + node): the cells
+// of one node, used together, lie far apart in the array (and in L2 slices).
+__global__ void k_round_zero(const uint32_t* nopen, uint32_t cap, int nd, uint32_t* cnt)
 {
-    p->npass = 1;
-    p->bits = kSortMaxBits;
-    p->shift0 = 0;
-    p->pad = 0;
+    const uint32_t nb = min(*nopen, cap);
+    const uint64_t tot = (uint64_t)nb * nd;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < tot; x += (uint64_t)gridDim.x * blockDim.x)
+        cnt[(x / nb) * cap + x % nb] = 0;
 }
 
-__global__ void k_deep_flag(const uint64_t* bigsum, uint64_t min_sum, uint32_t* flag)
+// copy of the open nodes' records (key, j) and their slot (node, cell of the
+// round's depth), counted per slot with one atomic per slot and warp
+__global__ void k_round_copy(const OpenNode* open, const uint32_t* nopen, uint32_t cap, const uint32_t* bigstart,
+                             const uint32_t* total, const uint64_t* __restrict__ gk, const uint32_t* __restrict__ gj,
+                             uint64_t* __restrict__ tk, uint32_t* __restrict__ tj, uint32_t* __restrict__ ts, int sh,
+                             uint32_t dmask, uint32_t* cnt)
 {
-    flag[0] = *bigsum > min_sum ? 1u : 0u;
-    flag[1] = 1u - flag[0];
+    const uint32_t nb = min(*nopen, cap), T = *total;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); p0 < T; p0 += stride) {   // warp-uniform
+        const uint32_t p = p0 + lane;
+        uint32_t slot = kNone;
+        if (p < T) {
+            const uint32_t b = big_of(bigstart, nb, p);
+            const uint32_t src = open[b].begin + (p - bigstart[b]);
+            const uint64_t k = gk[src];
+            tk[p] = k;
+            tj[p] = gj[src];
+            slot = (uint32_t)((k >> sh) & dmask) * cap + b;
+            ts[p] = slot;
+        }
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
+        if (slot != kNone && lane == __ffs(peers) - 1) atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
+    }
 }
 
-// points in cells of more than kPieceMax points (the records the split tree sorts)
-__global__ void k_big_sum(const uint32_t* counts, uint64_t cells, uint64_t* sum)
+// counts -> absolute starts: node b's cells in digit order from open[b].begin (one warp per node)
+__global__ void k_round_bases(const OpenNode* open, const uint32_t* nopen, uint32_t cap, int nd, uint32_t* cnt)
 {
-    uint64_t s = 0;
-    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x)
-        if (counts[m] > (uint32_t)kPieceMax) s += counts[m];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd((unsigned long long*)sum, (unsigned long long)s);
+    const uint32_t nb = min(*nopen, cap);
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int per = (nd + 31) / 32;   // <= 16
+    for (uint32_t b = warp; b < nb; b += nwarps) {
+        uint32_t v[16];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int d = lane * per + q;
+            v[q] = q < per && d < nd ? cnt[(uint64_t)d * cap + b] : 0u;
+            sum += v[q];
+        }
+        uint32_t x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t run = open[b].begin + (x - sum);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int d = lane * per + q;
+            if (q < per && d < nd) {
+                cnt[(uint64_t)d * cap + b] = run;
+                run += v[q];
+            }
+        }
+    }
+}
+
+// the copied records back into their nodes' ranges, grouped by slot (any order inside a slot)
+__global__ void k_round_scatter(const uint32_t* total, const uint64_t* __restrict__ tk,
+                                const uint32_t* __restrict__ tj, const uint32_t* __restrict__ ts, uint32_t* cnt,
+                                uint64_t* __restrict__ gk, uint32_t* __restrict__ gj, uint64_t n, uint32_t* err)
+{
+    const uint32_t T = *total;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); p0 < T; p0 += stride) {   // warp-uniform
+        const uint32_t p = p0 + lane;
+        const uint32_t slot = p < T ? ts[p] : kNone;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
+        const int leader = __ffs(peers) - 1;
+        uint32_t at = 0;
+        if (slot != kNone && lane == leader) at = atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
+        at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
+        if (slot == kNone) continue;
+        if (at >= n) { raise(err, FP_ERR_CAPACITY); continue; }
+        gk[at] = tk[p];
+        gj[at] = tj[p];
+    }
 }
 
 // --------------------------------------------------- big cells: split tree
@@ -1231,11 +1255,9 @@ uint64_t node_capacity_bound(uint64_t n, const fp_params& p) { return oct_layout
 
 struct OctBufs {
     SortScratch sc;
-    SortScratch sc_deep;   // plan, bases and histograms of the deeper cell grouping
-    uint64_t* bigsum;
-    uint32_t* deep;        // [0]: the deeper grouping runs, [1]: it does not
-    uint64_t *t_k1, *t_k2, *t_k3;
-    uint32_t *t_j1, *t_j2, *t_j3;
+    uint32_t* rcnt;        // counting slots of a split round: 8^3 per open node
+    uint64_t* t_k1;
+    uint32_t *t_j1, *t_j2;
     int4* lt_pt;
     uint32_t *lt_val, *lt_k32;
     uint32_t *pyr, *cstart, *cursor;
@@ -1267,14 +1289,11 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     OctBufs B;
     const uint64_t N = n ? n : 1;
     B.sc = take_sort_scratch(ws, std::max<uint64_t>(N, std::max(Ly.node_cap, Ly.piece_cap)));
-    B.sc_deep = take_sort_scratch(ws, 1);
-    B.bigsum = ws.take<uint64_t>(1);
-    B.deep = ws.take<uint32_t>(2);
+    B.rcnt = ws.take<uint32_t>(Ly.open_cap << (3 * kRoundLevels));
     // aliased phase region: grouping temporaries, later the leaf scatter temporaries
     const size_t phase_base = ws.used;
     B.t_k1 = ws.take<uint64_t>(N); B.t_j1 = ws.take<uint32_t>(N);
-    B.t_k2 = ws.take<uint64_t>(N); B.t_j2 = ws.take<uint32_t>(N);
-    B.t_k3 = ws.take<uint64_t>(N); B.t_j3 = ws.take<uint32_t>(N);
+    B.t_j2 = ws.take<uint32_t>(N);
     const size_t phase_end = ws.used;
     ws.used = phase_base;
     B.lt_pt = ws.take<int4>(N); B.lt_val = ws.take<uint32_t>(N); B.lt_k32 = ws.take<uint32_t>(N);
@@ -1421,91 +1440,58 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     if ((e = scan_exclusive<uint32_t, uint32_t>(rcounts, B.cstart, Ly.cells, nullptr, B.leafw, B.cstart + Ly.cells,
                                                 (uint32_t*)nullptr, st)))
         return e;
-    // depth of the first split round: the rank of an open node and the digits of
-    // R levels within 32 bits (four sort passes at most)
-    int rank_bits = 1;
-    while ((1ull << rank_bits) < std::min<uint64_t>(Ly.open_cap, Ly.cells)) ++rank_bits;
-    const int R = std::max(1, (32 - rank_bits) / 3);
-    const int r1 = std::min(R, dl - g);
     OctCtx c;
     c.counts = counts; c.rcounts = rcounts; c.leaf_base = grp ? grp->leaf_base : 0u;
     c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
     c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
     c.dups = B.dups; c.ndups = B.counters + 1;
-    c.deep = B.deep; c.r1 = r1;
     c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
     c.own_code = grp ? grp->own_code : B.own_code;
     c.leaf_code = grp ? grp->leaf_code : B.leaf_code;
     c.open_cap = (uint32_t)Ly.open_cap;
     c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
 
-    // 2. group by level-g cell: (key21, j) scattered by cell id.  When more
-    // than a third of the points lie in cells of more than kPieceMax points,
-    // sorting all records down to level g + r1 instead (stable key passes)
-    // is cheaper than the first split round's gather, sort and scatter of
-    // them, and that round then has nothing to do.
+    // 2. group by level-g cell: (key21, j) scattered by cell id
     {
-        if ((e = cudaMemsetAsync(B.bigsum, 0, sizeof(uint64_t), st))) return e;
-        k_big_sum<<<std::max(1, std::min(ws.num_sms * 4, (int)((Ly.cells + 255) / 256))), 256, 0, st>>>(
-            rcounts, Ly.cells, B.bigsum);
-        k_deep_flag<<<1, 1, 0, st>>>(B.bigsum, r1 > 0 ? N / 3 : ~0ull, B.deep);
-        k_plan_one<<<1, 1, 0, st>>>(sc.plan);
-        // deeper grouping: every key computed once into t_k2, read by the first pass
-        if ((e = sort_plan_cells_deep(sc, B.sc_deep, reinterpret_cast<const int4*>(sorted), N, cube, rcounts, Ly.cells,
-                                      (uint32_t)(3 * (kKeyLevels - g - r1)), (uint32_t)(3 * (g + r1)),
-                                      (uint32_t)(3 * r1), B.t_k2, B.deep, st)))
-            return e;
         const int gcell = (int)std::max<uint64_t>(1, std::min<uint64_t>((Ly.cells + 255) / 256, ws.num_sms * 8ull));
-        k_cell_cursor_init<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g, B.deep + 1);
+        k_cell_cursor_init<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g);
         const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 8));
         k_cell_scatter<<<gs, 256, 0, st>>>(reinterpret_cast<const int4*>(sorted), N, cube, B.cursor, B.gk, B.gj, g,
-                                           B.deep + 1, ws.err);
-        k_cell_check<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g, B.deep + 1, ws.err);
-        SortArgs a{};
-        a.b.k64_src = B.t_k2; a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.gk;
-        a.b.val_src = nullptr; a.b.val_tmp = B.t_j1; a.b.val_dst = B.gj;
-        a.n = N; a.cube = cube; a.g = g; a.err = ws.err;
-        a.run_if = B.deep;
-        for (int slot = 0; slot < kSortMaxPass; ++slot)
-            if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a, slot, ws.num_sms, st))) return e;
+                                           ws.err);
+        k_cell_check<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g, ws.err);
     }
     // 3. cells: pieces, leaf levels, open big cells
     k_cell_setup<<<(unsigned)((Ly.cells + 255) / 256), 256, 0, st>>>(c, B.open[0], B.ocount);
-    // 4. big cells: split tree.  The records of the open nodes are key-sorted
-    // (stable: records equal down to the sorted depth stay in index order) in
-    // two rounds, the first down to level g + R, the second down to dl for the
-    // nodes still open there; each round is followed by the splits it allows.
+    // 4. big cells: split tree.  Rounds of up to three levels: the records of
+    // the open nodes are grouped by their cell three levels down (one counting
+    // scatter: copy out with per-(node, cell) counts, starts, scatter back),
+    // which puts them in key order down to that depth; then the splits of
+    // those levels, whose children still too large stay open for the next round.
     {
         const uint32_t cap = (uint32_t)Ly.open_cap;
         int gw = std::max(1, std::min(ws.num_sms * 16, (int)(((uint64_t)cap * 32 + 255) / 256)));
         const int gr = std::max(1, std::min(ws.num_sms * 8, (int)((N + 255) / 256)));
         int cur = 0;
         for (int q = g; q < dl;) {
-            const int r = q == g ? r1 : dl - q;
-            k_open_counts<<<(cap + 255) / 256, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, cap,
-                                                             q == g ? B.bigsum : nullptr, N / 3);
+            const int k = std::min(kRoundLevels, dl - q);
+            const int nd = 1 << (3 * k);
+            k_open_counts<<<(cap + 255) / 256, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, cap, nullptr, 0);
             if ((e = scan_exclusive<uint32_t, uint32_t>(B.bigstart, B.bigstart, cap, nullptr, B.leafw, B.ocount + 3,
                                                         (uint32_t*)nullptr, st)))
                 return e;
-            k_big_gather<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, B.ocount + 3, B.gk, B.gj,
-                                             B.t_k2, B.t_j2, q);
-            if ((e = sort_plan_keys(sc, B.t_k2, N, B.ocount + 3, (uint32_t)(3 * (kKeyLevels - q - r)),
-                                    (uint32_t)(3 * r), st, B.ocount + cur)))
-                return e;
-            SortArgs a{};
-            a.b.k64_src = B.t_k2; a.b.k64_tmp = B.t_k1; a.b.k64_dst = B.t_k3;
-            a.b.val_src = B.t_j2; a.b.val_tmp = B.t_j1; a.b.val_dst = B.t_j3;
-            a.n = N; a.d_n = B.ocount + 3; a.err = ws.err;
-            if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
-            k_big_scatter<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, B.bigstart, B.ocount + 3, B.t_k3,
-                                              B.t_j3, B.gk, B.gj, q);
-            for (int l = q; l < q + r; ++l) {
+            k_round_zero<<<gr, 256, 0, st>>>(B.ocount + cur, cap, nd, B.rcnt);
+            k_round_copy<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, cap, B.bigstart, B.ocount + 3, B.gk, B.gj,
+                                             B.t_k1, B.t_j1, B.t_j2, 3 * (kKeyLevels - q - k), (uint32_t)(nd - 1),
+                                             B.rcnt);
+            k_round_bases<<<gw, 256, 0, st>>>(B.open[cur], B.ocount + cur, cap, nd, B.rcnt);
+            k_round_scatter<<<gr, 256, 0, st>>>(B.ocount + 3, B.t_k1, B.t_j1, B.t_j2, B.rcnt, B.gk, B.gj, N, ws.err);
+            for (int l = q; l < q + k; ++l) {
                 k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
                 k_split<<<gw, 256, 0, st>>>(c, B.open[cur], B.ocount + cur, B.open[1 - cur], B.ocount + (1 - cur),
-                                            cap, q + r);
+                                            cap, q + k);
                 cur = 1 - cur;
             }
-            q += r;
+            q += k;
         }
     }
     // 5. nodes at levels <= g (a chunk group leaves them to the whole-cloud node table)

@@ -123,83 +123,6 @@ __global__ void __launch_bounds__(1024) k_plan_finalize(const uint32_t* d_nw, ui
     }
 }
 
-// Deeper cell grouping (used when *flag != 0): a key sort of key21(point) over
-// bits [shift0, shift0 + total_bits).  The bits from shift0 + lsh up are cell
-// bits (lsh = 3 (21 - g) - shift0): a pass whose digit lies entirely among them
-// gets its histogram from the count grid, the others from the points, whose
-// keys are written to keys_out for the first pass.
-__global__ void k_keys_hist(const int4* pts, uint64_t n, const fp_cube* cube, uint32_t shift0, uint32_t total_bits,
-                            uint32_t lsh, uint32_t* hist, uint64_t* keys_out, const uint32_t* flag)
-{
-    if (!*flag) return;
-    const CubeDev cb = load_cube(cube);
-    __shared__ uint32_t sh[kSortMaxPass << kSortMaxBits];
-    uint32_t npass, bits;
-    plan_shape(0, total_bits, npass, bits);
-    const uint32_t mask = (1u << bits) - 1;
-    uint32_t np_pts = 0;   // passes whose digit includes bits below the cell bits
-    while (np_pts < npass && np_pts * bits < lsh) ++np_pts;
-    for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x) sh[q] = 0;
-    __syncthreads();
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int4 q = __ldg(pts + i);
-        const uint64_t key = key21(q.x, q.y, q.z, cb);
-        keys_out[i] = key;
-        const uint64_t k = key >> shift0;
-        for (uint32_t p = 0; p < np_pts; ++p) atomicAdd(&sh[(p << kSortMaxBits) + ((k >> (p * bits)) & mask)], 1u);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x)
-        if (sh[q]) atomicAdd(&hist[q], sh[q]);
-}
-
-__global__ void k_cells_hist(const uint32_t* counts, uint64_t cells, uint32_t total_bits, uint32_t lsh, uint32_t* hist,
-                             const uint32_t* flag)
-{
-    if (!*flag) return;
-    __shared__ uint32_t sh[kSortMaxPass << kSortMaxBits];
-    uint32_t npass, bits;
-    plan_shape(0, total_bits, npass, bits);
-    const uint32_t mask = (1u << bits) - 1;
-    uint32_t p0 = 0;
-    while (p0 < npass && p0 * bits < lsh) ++p0;
-    for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x) sh[q] = 0;
-    __syncthreads();
-    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t w = counts[m];
-        if (!w) continue;
-        const uint64_t k = m << lsh;
-        for (uint32_t p = p0; p < npass; ++p) atomicAdd(&sh[(p << kSortMaxBits) + ((k >> (p * bits)) & mask)], w);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < (kSortMaxPass << kSortMaxBits); q += blockDim.x)
-        if (sh[q]) atomicAdd(&hist[q], sh[q]);
-}
-
-__global__ void k_plan_select(const uint32_t* flag, const SortPlan* p2, const uint64_t* b2, SortPlan* p, uint64_t* b)
-{
-    if (!*flag) return;
-    for (int i = threadIdx.x; i < (kSortMaxPass << kSortMaxBits); i += blockDim.x) b[i] = b2[i];
-    if (threadIdx.x == 0) *p = *p2;
-}
-
-cudaError_t sort_plan_cells_deep(const SortScratch& target, const SortScratch& alt, const int4* pts, uint64_t n,
-                                 const fp_cube* cube, const uint32_t* counts, uint64_t cells, uint32_t shift0,
-                                 uint32_t total_bits, uint32_t lsh, uint64_t* keys_out, const uint32_t* flag,
-                                 cudaStream_t st)
-{
-    cudaError_t e = cudaMemsetAsync(alt.hist, 0, sizeof(uint32_t) * (kSortMaxPass << kSortMaxBits), st);
-    if (e) return e;
-    int grid = (int)std::min<uint64_t>((n + 1023) / 1024 ? (n + 1023) / 1024 : 1, 1024);
-    k_keys_hist<<<grid, 1024, 0, st>>>(pts, n, cube, shift0, total_bits, lsh, alt.hist, keys_out, flag);
-    int gc = (int)std::min<uint64_t>((cells + 1023) / 1024 ? (cells + 1023) / 1024 : 1, 256);
-    k_cells_hist<<<gc, 1024, 0, st>>>(counts, cells, total_bits, lsh, alt.hist, flag);
-    k_plan_finalize<<<1, 1024, 0, st>>>(nullptr, 0, total_bits, shift0, alt.hist, alt.plan, alt.bases, nullptr);
-    k_plan_select<<<1, 256, 0, st>>>(flag, alt.plan, alt.bases, target.plan, target.bases);
-    return cudaGetLastError();
-}
-
 size_t sort_scratch_bytes(uint64_t n)
 {
     uint64_t ntiles = (n + kSortTile - 1) / kSortTile;

@@ -375,15 +375,6 @@ struct SortScratch {
 size_t sort_scratch_bytes(uint64_t n);
 SortScratch take_sort_scratch(const Workspace& ws, uint64_t n);
 
-// When *flag != 0: replace target's plan by that of a key sort of key21(point)
-// over bits [shift0, shift0 + total_bits), whose bits from shift0 + lsh up are
-// the cell bits of the count grid `counts`, and write every point's key21 to
-// keys_out (alt: plan, bases and histogram scratch).
-cudaError_t sort_plan_cells_deep(const SortScratch& target, const SortScratch& alt, const int4* pts, uint64_t n,
-                                 const fp_cube* cube, const uint32_t* counts, uint64_t cells, uint32_t shift0,
-                                 uint32_t total_bits, uint32_t lsh, uint64_t* keys_out, const uint32_t* flag,
-                                 cudaStream_t st);
-
 // plan from weights of ids; then run the passes of the given kind
 cudaError_t sort_plan_weights(const SortScratch& sc, const uint32_t* weights, const uint64_t* offsets,
                               const uint32_t* d_nw, uint64_t nw_max, uint32_t shift0, cudaStream_t st);
