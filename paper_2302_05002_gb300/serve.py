@@ -15,7 +15,9 @@ memory budget:
   - an in-core request's octree (node table, final points and perm) stays on
     the device; an out-of-core one is written to pinned host memory (at most
     `ooc_slots` such requests at a time, each in its own host buffers,
-    allocated when the server starts);
+    allocated when the server starts; one by default: an out-of-core build is
+    bound by the host link, so a second one only shares the link while its
+    arena keeps the other half of the budget from in-core requests);
   - per request: time to preview and time to the full octree (from arrival),
     both taken on the host when the device work is done.
 Results do not depend on the mix: every request runs the same calls on its own
@@ -67,7 +69,7 @@ def preview_slots_shape(n, piece, m):
 
 class Server:
     def __init__(self, budget_bytes=24 << 30, piece_points=1 << 23, device=0, ooc_max_points=0, ooc_prm=None,
-                 ooc_slots=2):
+                 ooc_slots=1):
         self.budget = budget_bytes
         self.free = budget_bytes
         self.piece = piece_points
