@@ -311,8 +311,11 @@ fp_status fp_build_batched(const fp_cloud_desc* h_clouds, uint32_t ncloud, uint3
  * counts, chunks, then groups of consecutive chunks that fit the arena: each
  * group's local octrees (levels and nodes below the count grid), the node table
  * of the whole cloud, owners, and the final layout (points kept above the
- * chunks merged across groups by a device sort).  The outputs equal the
- * in-core calls' (cube, preview, node table, final points and perm).
+ * chunks merged across groups by a device sort).  When the arena also holds
+ * the distributed cloud (20 bytes per point) next to a group as large as the
+ * largest chunk, the cloud stays on the device after the distribution pass and
+ * is not read back from h_scratch.  The outputs equal the in-core calls'
+ * (cube, preview, node table, final points and perm).
  * This call blocks the calling host thread until the build is done (it reads
  * the chunk list between passes); h_* outputs are pinned host memory. */
 size_t fp_ooc_arena_min(uint64_t n, const fp_params* prm, uint64_t piece_points);
