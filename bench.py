@@ -70,6 +70,19 @@ def ncu_traffic(workload, stage):
         return None
 
 
+def replica_rate(ms, n, world, device):
+    """Replicas only (every rank builds its own cloud of n points, nothing is
+    exchanged): the step time of the job is the slowest rank's, and the job
+    processed n * world points in it.  Returns (max ms over ranks, Gpts/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, n * world / (ms * 1e-3) / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1090,11 +1103,7 @@ def main():
         st.synchronize()
         for k, name in enumerate(STAGES):
             stage_ms[name].append(ev[k].elapsed_time(ev[k + 1]))
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = n * world / (ms * 1e-3) / 1e9
+    ms, value = replica_rate(ms, n, world, dev)
 
     # end to end: pinned host input copied in, node table read back, every step
     nodes_host = torch.empty_like(O["nodes"], device="cpu").pin_memory()
