@@ -229,10 +229,20 @@ __global__ void k_zero_count(uint64_t* out_count) { *out_count = 0; }
 __global__ void k_put_at(uint64_t* a, const uint32_t* idx, const uint64_t* val) { a[*idx] = *val; }
 
 // ----------------------------------------------------------------- count
+// Each block also keeps a small direct-mapped table of cells in shared memory:
+// the first cell to reach a slot owns it for the block's lifetime and its hits
+// are added there, flushed to the grid at the end.  Clouds with dense spots
+// (scanner surroundings) send most of their hits to a few cells; those end up
+// in the tables and stop contending for the same global counters.
+constexpr int kCountSlots = 1024;
+
 template <bool AGG>
 __global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts, uint64_t n,
                                                const fp_cube* __restrict__ cube, int g, uint32_t* __restrict__ counts)
 {
+    __shared__ uint32_t s_tag[kCountSlots], s_cnt[kCountSlots];
+    for (int q = threadIdx.x; q < kCountSlots; q += blockDim.x) { s_tag[q] = kNone; s_cnt[q] = 0; }
+    __syncthreads();
     const CubeDev c = load_cube(cube);
     const float sg = scale_at(c, g);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -252,12 +262,21 @@ __global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts,
         for (int u = 0; u < 4; ++u) {
             if (AGG) {
                 uint32_t peers = __match_any_sync(0xFFFFFFFFu, key[u]);
-                if (key[u] != kNone && lane == __ffs(peers) - 1) atomicAdd(&counts[key[u]], (uint32_t)__popc(peers));
+                if (key[u] != kNone && lane == __ffs(peers) - 1) {
+                    const uint32_t slot = (key[u] * 2654435761u) >> 22;   // 10-bit multiplicative hash
+                    uint32_t t = s_tag[slot];
+                    if (t == kNone) t = atomicCAS(&s_tag[slot], kNone, key[u]) == kNone ? key[u] : s_tag[slot];
+                    if (t == key[u]) atomicAdd(&s_cnt[slot], (uint32_t)__popc(peers));
+                    else atomicAdd(&counts[key[u]], (uint32_t)__popc(peers));
+                }
             } else if (key[u] != kNone) {
                 atomicAdd(&counts[key[u]], 1u);
             }
         }
     }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kCountSlots; q += blockDim.x)
+        if (s_cnt[q]) atomicAdd(&counts[s_tag[q]], s_cnt[q]);
 }
 
 // ----------------------------------------------------------------- merge
