@@ -18,7 +18,8 @@
 // distributed cloud next to a group as large as the largest chunk, in which
 // case pass 3 also writes it to the device and the group passes read it there
 // (a cloud up to about half the arena in size crosses the link three times
-// fewer).  The pinned host scratch is the out-of-core store between passes:
+// fewer); when the arena also holds a raw copy of the cloud, pass 1 leaves it
+// there and passes 2 and 3 read it on the device.  The pinned host scratch is the out-of-core store between passes:
 // the distributed points and original indices of every group, the two levels
 // and the owner of every point, and the staged records.
 #include <algorithm>
@@ -398,6 +399,7 @@ struct Piecer {   // double-buffered host -> device copies of the pieces on a si
     const fp_point* h = nullptr;
     uint64_t n = 0, P = 0;
     int4* buf[2] = {nullptr, nullptr};
+    int4* raw = nullptr;   // set: piece k lands at raw + k P (a device copy of the whole cloud)
 
     cudaError_t init(cudaStream_t stream, const fp_point* hp, uint64_t nn, uint64_t pp, int4* b0, int4* b1)
     {
@@ -411,6 +413,7 @@ struct Piecer {   // double-buffered host -> device copies of the pieces on a si
         return e;
     }
     uint64_t pieces() const { return (n + P - 1) / P; }
+    int4* dst(uint64_t k) const { return raw ? raw + k * P : buf[k & 1]; }
     uint64_t size(uint64_t k) const { return std::min(P, n - k * P); }
     // enqueue the copy of piece k (after the work that read its buffer), compute stream waits for it
     cudaError_t fetch(uint64_t k)
@@ -418,11 +421,20 @@ struct Piecer {   // double-buffered host -> device copies of the pieces on a si
         const int b = (int)(k & 1);
         cudaError_t e;
         if ((e = cudaStreamWaitEvent(cs, consumed[b], 0))) return e;
-        if ((e = cudaMemcpyAsync(buf[b], h + k * P, size(k) * sizeof(fp_point), cudaMemcpyHostToDevice, cs))) return e;
+        if ((e = cudaMemcpyAsync(dst(k), h + k * P, size(k) * sizeof(fp_point), cudaMemcpyHostToDevice, cs))) return e;
         if ((e = cudaEventRecord(copied[b], cs))) return e;
         return cudaStreamWaitEvent(st, copied[b], 0);
     }
     cudaError_t done(uint64_t k) { return cudaEventRecord(consumed[k & 1], st); }
+    // a pass over the device copy made by an earlier pass (raw set): no copies
+    template <typename F>
+    cudaError_t pass_raw(F body)
+    {
+        cudaError_t e;
+        for (uint64_t k = 0; k < pieces(); ++k)
+            if ((e = body(k, reinterpret_cast<const fp_point*>(raw + k * P), size(k)))) return e;
+        return cudaSuccess;
+    }
     // pass over all pieces: body(k, device pointer, size) enqueues the work on st
     template <typename F>
     cudaError_t pass(F body)
@@ -432,7 +444,7 @@ struct Piecer {   // double-buffered host -> device copies of the pieces on a si
         if (np && (e = fetch(0))) return e;
         for (uint64_t k = 0; k < np; ++k) {
             if (k + 1 < np && (e = fetch(k + 1))) return e;   // the next copy overlaps this piece's work
-            if ((e = body(k, reinterpret_cast<const fp_point*>(buf[k & 1]), size(k)))) return e;
+            if ((e = body(k, reinterpret_cast<const fp_point*>(dst(k)), size(k)))) return e;
             if ((e = done(k))) return e;
         }
         return cudaSuccess;
@@ -478,6 +490,25 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     const HostStore H = host_carve(h_scratch, n);
     cudaError_t e;
     if ((e = io.init(st, h_pts, n, P, F.piece[0], F.piece[1]))) return FP_ERR_CUDA;
+    // When the arena also holds a copy of the raw cloud behind the space of the
+    // resident distributed cloud (16 + 20 bytes per point, and the passes'
+    // stage workspace after them), pass 1 copies every piece there and passes 2
+    // and 3 read it on the device instead of crossing the link again.
+    int4* raw = nullptr;
+    {
+        const size_t ws13 = std::max({bounds_ws_bytes(P, base.num_sms), merge_ws_bytes(g),
+                                      distribute_ws_bytes(P, g)});
+        const size_t raw_bytes = Workspace::bytes_for({16 * (n ? n : 1)});
+        if (after_fixed + resident_bytes(n) + raw_bytes + ws13 <= arena_bytes) {
+            Workspace wr = base;
+            wr.used = after_fixed + resident_bytes(n);
+            raw = wr.take<int4>(n ? n : 1);
+            ws.base = base.base + wr.used;
+            ws.bytes = ws13;
+            ws.used = 0;
+            io.raw = raw;
+        }
+    }
 
     // ---- pass 1: bounds and preview
     if ((e = cudaMemsetAsync(F.prev_run, 0, sizeof(uint64_t), st))) return cu(e);
@@ -500,10 +531,11 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     if (preview_done && (e = cudaLaunchHostFunc(st, preview_done, user))) return cu(e);
 
     // ---- pass 2: counts; chunks
-    e = io.pass([&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
+    auto count_piece = [&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
         ws.used = 0;
         return launch_count(p, np, F.cube, g, F.counts, k > 0, ws, st);
-    });
+    };
+    e = raw ? io.pass_raw(count_piece) : io.pass(count_piece);
     if (e) return cu(e);
     ws.used = 0;
     if ((e = launch_merge(F.counts, g, prm.chunk_threshold, F.chunks, F.num_chunks, F.lut, F.offsets, ws, st)))
@@ -534,12 +566,18 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
             res_perm = wr.take<uint32_t>(n ? n : 1);
             G = Gr;
             B = group_carve(wr, G, P, prm, node_cap, base.num_sms, true);
-            ws.base = B.ws;
-            ws.bytes = B.ws_bytes;
-            ws.used = 0;
         }
     }
     const bool resident = res_pts != nullptr;
+    if (raw && !resident) {   // the non-resident group region covers the raw copy: pass 3 streams again
+        raw = nullptr;
+        io.raw = nullptr;
+    }
+    if (!raw) {   // pass 3's stage workspace: the group's (the raw copy keeps its own until pass 3 is done)
+        ws.base = B.ws;
+        ws.bytes = B.ws_bytes;
+        ws.used = 0;
+    }
 
     // consecutive chunks while they fit a group
     std::vector<std::pair<uint32_t, uint32_t>> groups;
@@ -556,7 +594,7 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     // lands after the earlier pieces' points of that chunk (a cursor per chunk).
     const unsigned gK = grid_for(K, base.num_sms);
     k_cursor_init<<<gK, 256, 0, st>>>(F.offsets, K, F.ccur);
-    e = io.pass([&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
+    auto distribute_piece = [&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
         cudaError_t x;
         if ((x = cudaMemsetAsync(F.pcnt, 0, (size_t)K * sizeof(uint32_t), st))) return x;
         k_piece_hist<<<grid_for(np, base.num_sms), 256, 0, st>>>(p, np, F.cube, g, F.lut, F.pcnt);
@@ -573,8 +611,12 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
                                                                     base.err);
         k_cursor_advance<<<gK, 256, 0, st>>>(F.ccur, F.pcnt, K);
         return cudaGetLastError();
-    });
+    };
+    e = raw ? io.pass_raw(distribute_piece) : io.pass(distribute_piece);
     if (e) return cu(e);
+    ws.base = B.ws;   // the raw copy is dead from here on
+    ws.bytes = B.ws_bytes;
+    ws.used = 0;
 
     // ---- per group: its points from the store; levels and nodes below level g
     if ((e = cudaMemsetAsync(F.num_deep, 0, sizeof(uint32_t), st))) return cu(e);

@@ -33,10 +33,14 @@ CASES = [
     # 64 chunks of level 2, few points kept above them
     ("uniform", 16_000_000, 46, 5, 5, 12, 300_000, 20_000, 1 << 21, 0),
 ]
+# the same cloud with a 500 MB arena: room for the resident distributed cloud (320 MB) but not
+# also for a raw copy (another 256 MB), so passes 2 and 3 stream from the host
+ARENA = {("uniform", 16_000_000): 500 << 20}
 
 
-@pytest.mark.parametrize("kind,n,seed,g,s,lmax,T,C,piece,group", CASES)
-def test_ooc_equals_in_core(gpu_lib, kind, n, seed, g, s, lmax, T, C, piece, group):
+@pytest.mark.parametrize("kind,n,seed,g,s,lmax,T,C,piece,group,arena_bytes",
+                         [c + (0,) for c in CASES] + [c + (ARENA[c[:2]],) for c in CASES if c[:2] in ARENA])
+def test_ooc_equals_in_core(gpu_lib, kind, n, seed, g, s, lmax, T, C, piece, group, arena_bytes):
     fp = gpu_lib
     prm = fp.params(grid_log2=g, sub_log2=s, max_level=lmax, decim_modulus=16, chunk_threshold=T, node_capacity=C)
     pts_np = cloud(kind, n, seed)
@@ -44,7 +48,8 @@ def test_ooc_equals_in_core(gpu_lib, kind, n, seed, g, s, lmax, T, C, piece, gro
     ref = fp.build_octree(dev, prm)
     torch.cuda.synchronize()
     host = dev.cpu().pin_memory()
-    arena = torch.empty(max(fp.ooc_arena_min(n, prm, piece), 64 << 20), dtype=torch.uint8, device="cuda")
+    arena = torch.empty(arena_bytes or max(fp.ooc_arena_min(n, prm, piece), 64 << 20), dtype=torch.uint8,
+                        device="cuda")
     seen = []
     out = fp.build_ooc(host, prm, arena, piece_points=piece, group_points=group, on_preview=lambda: seen.append(1))
     assert fp.get_device_error() == 0
