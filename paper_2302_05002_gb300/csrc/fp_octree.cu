@@ -1794,12 +1794,28 @@ static SubBufs sub_carve(const Workspace& ws, uint64_t n, uint64_t M)
     B.nown = ws.take<uint32_t>(M); B.first = ws.take<uint64_t>(M + 1);
     B.mark = ws.take<uint32_t>(M); B.mrank = ws.take<uint32_t>(M); B.mlist = ws.take<uint32_t>(M);
     B.mown = ws.take<uint32_t>(M); B.soff = ws.take<uint32_t>(M + 1); B.cnt = ws.take<uint32_t>(4);
+    // One region serves three sets of per-point buffers that are never live
+    // together: the whole-array path's sort temporaries and owner copy (dead
+    // once its unsorted segments are marked), the stitch records and their
+    // sort buffers, and the stitch's gathered points (written over the sort's
+    // source and temporary, both dead after the sort).
+    const size_t region = ws.used;
     B.t_pt = ws.take<int4>(N); B.t_val = ws.take<uint32_t>(N); B.t_k32 = ws.take<uint32_t>(N);
     B.fown = ws.take<uint32_t>(N);
+    const size_t end_t = ws.used;
+    ws.used = region;
     B.s_key = ws.take<uint64_t>(N); B.s_val = ws.take<uint32_t>(N);
     B.s_key2 = ws.take<uint64_t>(N); B.s_val2 = ws.take<uint32_t>(N);
+    const size_t end_src = ws.used;
     B.s_key3 = ws.take<uint64_t>(N); B.s_val3 = ws.take<uint32_t>(N);
+    const size_t end_s = ws.used;
+    ws.used = region;
     B.s_pt = ws.take<int4>(N); B.s_perm = ws.take<uint32_t>(N);
+    if (ws.used > end_src) {   // (20 bytes per point fit in 24 unless rounding says otherwise: then after)
+        ws.used = end_s;
+        B.s_pt = ws.take<int4>(N); B.s_perm = ws.take<uint32_t>(N);
+    }
+    ws.used = std::max(std::max(end_t, end_s), ws.used);
     B.tiles64 = ws.take<uint64_t>(kScanMaxTiles); B.tiles32 = ws.take<uint32_t>(kScanMaxTiles);
     B.scnt = ws.take<uint32_t>(M + 1);
     B.seg = take_seg_scratch(ws, N, chunk_bound(n), M);

@@ -4,9 +4,13 @@ The paper's converter shows a preview at once and builds the octree behind it
 (Sec. 3, Sec. 4.2).  Here many such requests share one GPU under a device
 memory budget:
   - admission: a request is admitted as soon as its device need fits in the
-    free budget (first fit in arrival order), so requests that arrive while
-    others run are built alongside them (each on its own CUDA stream; their
-    kernels overlap on the device);
+    free budget (first fit in arrival order, an out-of-core request before
+    in-core ones: it is long and bound by the host link, so in-core builds
+    overlap it), so requests that arrive while others run are built alongside
+    them (each on its own CUDA stream; their kernels overlap on the device).
+    In-core builds of `big_points` or more fill the GPU alone and run one at a
+    time (two at once only compete for bandwidth and L2); smaller ones overlap
+    freely;
   - a cloud whose in-core need exceeds three quarters of the budget is built
     out of core (fp_build_ooc) in an arena of half the budget;
   - in-core requests stream their points in pieces with cudaMemcpyAsync on a
@@ -69,8 +73,10 @@ def preview_slots_shape(n, piece, m):
 
 class Server:
     def __init__(self, budget_bytes=24 << 30, piece_points=1 << 23, device=0, ooc_max_points=0, ooc_prm=None,
-                 ooc_slots=1):
+                 ooc_slots=1, big_points=1 << 24):
         self.budget = budget_bytes
+        self.big_points = big_points   # in-core builds this large fill the GPU alone: one at a time
+        self.big_active = 0
         self.free = budget_bytes
         self.piece = piece_points
         self.ooc_slots = ooc_slots
@@ -107,8 +113,12 @@ class Server:
                 while True:
                     if self._stop and not self.queue:
                         return
-                    pick = next((r for r in self.queue if r.need <= self.free and
-                                 (r.mode == "in-core" or self.ooc_free)), None)
+                    fits = [r for r in self.queue if r.need <= self.free and
+                            (self.ooc_free if r.mode == "out-of-core" else
+                             (r.n < self.big_points or self.big_active == 0))]
+                    # an out-of-core build is long and bound by the host link: start it
+                    # first, then fill the rest of the budget with in-core requests
+                    pick = next((r for r in fits if r.mode == "out-of-core"), fits[0] if fits else None)
                     if pick is not None:
                         break
                     self.cv.wait()
@@ -116,6 +126,8 @@ class Server:
                 self.free -= pick.need
                 if pick.mode == "out-of-core":
                     pick.slot = self.ooc_free.pop()
+                elif pick.n >= self.big_points:
+                    self.big_active += 1
                 self.active += 1
                 self.peak_active = max(self.peak_active, self.active)
             pick.t_admit = time.perf_counter()
@@ -128,6 +140,8 @@ class Server:
             self.free += req.need
             if req.mode == "out-of-core":
                 self.ooc_free.append(req.slot)
+            elif req.n >= self.big_points:
+                self.big_active -= 1
             self.active -= 1
             self.done.append(req)
             self.cv.notify_all()
