@@ -39,7 +39,10 @@ WORKLOADS = {
 }
 RENDER_W, RENDER_H, RENDER_MIN_PX = 1920, 1080, 30.0
 STAGES = ["bounds_decimate", "count", "merge", "distribute", "octree", "subsample"]
-# algorithmic HBM bytes per point of each stage (mandatory reads + writes), see the design doc
+# algorithmic HBM bytes per point of each stage: the mandatory reads and writes of
+# its definition (bounds + preview: read 16, a 16-byte record for 1 point in 16;
+# count: read 16; distribute: read 16, write 16 + 4 perm; octree: read 16 + 4 perm,
+# write 16 + 4 leaf-grouped and 4 owner; subsample: read 16 + 4 + 4, write 16 + 4)
 ALG_BYTES = {"bounds_decimate": 17, "count": 16, "merge": 0, "distribute": 36, "octree": 44, "subsample": 44}
 FIXED_BYTES = {"merge": 3 * 4 * (1 << 21)}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a

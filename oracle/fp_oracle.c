@@ -2,8 +2,9 @@
  * fp_oracle.c -- plain single-threaded CPU oracle (TEST INFRASTRUCTURE ONLY).
  *
  * Every function restates one definition of the octree-construction hot path
- * (paper Sec. 3, Sec. 4.2, Sec. 4.4 and Fig. "octree"; the exact readings are
- * listed in the design doc) in the most direct form: loops, qsort, per-level work.
+ * (paper Sec. 3, Sec. 4.2, Sec. 4.4 and Fig. "octree", in the exact-integer
+ * readings listed in fp_oracle.h) in the most direct form: loops, qsort,
+ * per-level work.
  * There is no blocking, fusion or reordering beyond what the definitions say.
  * Nothing here is shared with the CUDA library.
  */
@@ -417,7 +418,7 @@ static int compute_lambda(const orc_point* pts, uint64_t n, const orc_cube* cube
 }
 
 /* owner level = min(max(0, lambda - s), leaf level); the owner is the node on the
- * point's path at that level.  Derivation (DESIGN.md): a node at level K on the
+ * point's path at that level.  Derivation: a node at level K on the
  * path takes p iff K < leaf level and p is the minimum of its level-(K+s) cell,
  * and being a minimum at level l implies being one at every deeper level. */
 static int lod_closed(tree_ctx* t, uint64_t n)

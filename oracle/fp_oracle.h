@@ -10,7 +10,7 @@
  *
  * The paper (Sec. 3, Sec. 4.4, Fig. "octree") delegates octree construction to a
  * chunk -> index -> stitch converter and gives no constants; every definition
- * implemented here is the exact-integer reading recorded in the design doc:
+ * implemented here is one exact-integer reading of it:
  *   cube      o_a = min p_a, S = max_a(max p_a - o_a) + 1                  (Sec. 4.4)
  *   cell      c_a(l) = floor((p_a - o_a) * 2^l / S), Morton x-major        (Sec. 4.4)
  *   preview   keep i  <=>  splitmix64(i) mod m == 0, ascending i            (Sec. 3, 4.2)
