@@ -28,6 +28,8 @@ WORKLOADS = {
     "uniform-1M": ("uniform", 1_000_000, 1, 7, 7, 15, 100_000, 20_000),
     "uniform-1B": ("uniform", 1_000_000_000, 3, 7, 7, 8, 5_000_000, 50_000),
     "lidar-10M": ("lidar", 10_000_000, 2, 7, 7, 15, 100_000, 20_000),
+    # the 1B parameters at 100M points: 512 chunks (the one-sweep distribution), 1.6 GB resident
+    "uniform-100M": ("uniform", 100_000_000, 3, 7, 7, 8, 500_000, 50_000),
     # 256 clouds, sizes log-uniform in [1e4, 2e7], uniform or LiDAR generator per cloud (seed 1000 + i)
     "batched-256": ("batch", 256, 1000, 7, 7, 15, 100_000, 20_000),
     # 32 LiDAR requests, sizes log-uniform in [1e6, 5e8], Poisson arrivals 4/s, 24 GB device budget (seed 5000 + i)

@@ -586,112 +586,123 @@ __global__ void k_unit_ranges(const uint64_t* piece_begin_sorted, const uint32_t
     unit_p0[u] = a;
 }
 
-__global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint32_t* unit_p0,
-                                                      const uint32_t* piece_order, uint64_t n)
+// Per-window piece descriptors, one warp per window, ahead of k_units (which
+// then reads them with one load per piece instead of waiting, every warp of a
+// CTA, on the piece loads and two block scans).  Pieces in window order:
+//   kind 0: one point; 1: 2..32 points, not inner; 2: general path (larger, or
+//   inner); 3: more than kPieceMax equal keys (k_dup_pieces); 4: table path --
+//   a kind-2 piece, not inner, whose lambda is decided within kTabLevels levels,
+//   while the tables of the candidates up to it fit in kTabCap entries.
+// pdesc[p] = {begin, pn | psrt << 16, pcnt | pfst << 16, ptab | q << 16 | hier << 24},
+// pdesc2[p] = A | kind << 8 | D << 16 (p = window's first piece + index);
+// uhead[u] = {first piece, pieces, general records | table records << 16,
+//             table entries | deepest needed level << 16 | smallest sorted level << 24}.
+__global__ void __launch_bounds__(256) k_unit_desc(OctCtx c, const uint32_t* unit_p0, const uint32_t* piece_order,
+                                                   uint64_t nunits, uint4* pdesc, uint32_t* pdesc2, uint4* uhead)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr uint32_t kSat = (uint32_t)kTabCap + 1u;   // table prefixes saturate here (past it nothing fits)
+    for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
+        const uint32_t p0 = unit_p0[u], np = unit_p0[u + 1] - p0;
+        uint32_t tcarry = 0, rcarry = 0, dmax = 0, smin = 255;
+        for (uint32_t b0 = 0; b0 < np; b0 += 32) {   // warp-uniform
+            const uint32_t pi = b0 + lane;
+            const bool valid = pi < np;
+            Piece p{};
+            if (valid) p = c.pieces[piece_order[p0 + pi]];
+            uint32_t kind = 0, tz = 0, D = 0;
+            bool cand = false;
+            if (valid) {
+                const bool large = !p.dup && (p.count > 32 || p.hier == kInner);
+                kind = p.dup ? 3u : (large ? 2u : (p.count == 1 ? 0u : 1u));
+                if (large && p.hier != kInner) {
+                    const int Dv = min(kKeyLevels, c.s + (int)p.hier - 1) - (int)p.q;
+                    if (Dv <= kTabLevels) { cand = true; tz = tab_size(Dv); D = (uint32_t)max(Dv, 0); }
+                }
+            }
+            uint32_t inc = tz;   // saturating inclusive scan of the candidates' table sizes
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc = min(inc + y, kSat);
+            }
+            uint32_t tex = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
+            tex = min(tcarry + (lane ? tex : 0u), kSat);
+            uint32_t cn = 0, fn = 0, ptab = 0;
+            if (valid && kind == 2) {
+                if (cand && tex + tz <= (uint32_t)kTabCap) {
+                    kind = 4;
+                    ptab = tex;
+                    fn = p.count;
+                } else {
+                    cn = p.count;
+                    const uint32_t d = p.hier == kInner ? (uint32_t)c.dl
+                                                        : (uint32_t)min(kKeyLevels, c.s + (int)p.hier - 1);
+                    dmax = max(dmax, d);
+                    smin = min(smin, (uint32_t)p.srt);
+                }
+            }
+            uint32_t inc2 = cn | (fn << 16);   // records of both paths, in window order
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc2, o);
+                if (lane >= o) inc2 += y;
+            }
+            uint32_t ex = __shfl_up_sync(0xFFFFFFFFu, inc2, 1);
+            ex = rcarry + (lane ? ex : 0u);
+            if (valid) {
+                const uint32_t pn = p.dup ? 0u : p.count;
+                pdesc[p0 + pi] = make_uint4(p.begin, pn | (ex << 16), cn | ((ex >> 16) << 16),
+                                            ptab | ((uint32_t)p.q << 16) | ((uint32_t)p.hier << 24));
+                pdesc2[p0 + pi] = (uint32_t)p.A | (kind << 8) | (D << 16);
+            }
+            tcarry = min(tcarry + __shfl_sync(0xFFFFFFFFu, inc, 31), kSat);
+            rcarry += __shfl_sync(0xFFFFFFFFu, inc2, 31);
+        }
+        dmax = __reduce_max_sync(0xFFFFFFFFu, dmax);
+        smin = __reduce_min_sync(0xFFFFFFFFu, smin);
+        if (lane == 0)
+            uhead[u] = make_uint4(p0, np, rcarry, min(tcarry, (uint32_t)kTabCap) | (dmax << 16) | (smin << 24));
+    }
+}
+
+__global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhead, const uint4* pdesc,
+                                                      const uint32_t* pdesc2, uint64_t n)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     UnitSmem& S = *reinterpret_cast<UnitSmem*>(smem_raw);
     const uint64_t nunits = (n + kWindow - 1) / kWindow;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-        if (threadIdx.x == 0) {
-            const uint32_t p0 = unit_p0[u];
-            S.p0 = p0;
-            S.np = unit_p0[u + 1] - p0;
-            S.dl = 0;
-            S.smin = 255;
+        // piece descriptors of the window (k_unit_desc)
+        {
+            const uint4 h = uhead[u];
+            if (threadIdx.x == 0) {
+                S.p0 = h.x;
+                S.np = h.y;
+                S.cnt = h.z & 0xFFFFu;
+                S.fcnt = h.z >> 16;
+                S.tabn = h.w & 0xFFFFu;
+                S.dl = (h.w >> 16) & 0xFFu;
+                S.smin = h.w >> 24;
+            }
+            for (int pi = threadIdx.x; pi < (int)h.y; pi += kUnitNT) {
+                const uint4 d = pdesc[h.x + pi];
+                const uint32_t d2 = pdesc2[h.x + pi];
+                S.pbeg[pi] = d.x;
+                S.pn[pi] = (uint16_t)(d.y & 0xFFFFu);
+                S.psrt[pi] = (uint16_t)(d.y >> 16);
+                S.pcnt[pi] = (uint16_t)(d.z & 0xFFFFu);
+                S.pfst[pi] = (uint16_t)(d.z >> 16);
+                S.ptab[pi] = (uint16_t)(d.w & 0xFFFFu);
+                S.pq[pi] = (uint8_t)(d.w >> 16);
+                S.phier[pi] = (uint8_t)(d.w >> 24);
+                S.pA[pi] = (uint8_t)d2;
+                S.pkind[pi] = (uint8_t)(d2 >> 8);
+                S.pD[pi] = (uint8_t)(d2 >> 16);
+            }
         }
         __syncthreads();
         const int np = (int)S.np;
-        // piece descriptors.  Pieces of one point need nothing but their minimum
-        // rule; pieces of at most 32 points are handled by one warp with
-        // shuffles; pieces whose lambda is decided within kTabLevels levels
-        // take the table path while the tables fit; the other pieces (and
-        // pieces whose node is still inner) go through the shared-memory sort.
-        // Block scans place the tables and the records of both paths.
-        {
-            constexpr int per = (kWindow + kUnitNT - 1) / kUnitNT;
-            uint32_t po[per], tz[per];
-            uint32_t tsum = 0;
-#pragma unroll
-            for (int q = 0; q < per; ++q) {   // both levels of loads issued before use
-                const int pi = threadIdx.x * per + q;
-                po[q] = pi < np ? piece_order[S.p0 + pi] : 0u;
-            }
-            Piece pr[per];
-#pragma unroll
-            for (int q = 0; q < per; ++q)
-                if ((int)threadIdx.x * per + q < np) pr[q] = c.pieces[po[q]];
-#pragma unroll
-            for (int q = 0; q < per; ++q) {
-                const int pi = threadIdx.x * per + q;
-                tz[q] = 0xFFFFFFFFu;   // not a table candidate
-                if (pi < np) {
-                    const Piece p = pr[q];
-                    S.pbeg[pi] = p.begin;
-                    S.pq[pi] = p.q;
-                    S.phier[pi] = p.hier;
-                    S.pA[pi] = p.A;
-                    S.pn[pi] = (uint16_t)(p.dup ? 0 : p.count);
-                    const bool large = !p.dup && (p.count > 32 || p.hier == kInner);
-                    S.pkind[pi] = p.dup ? 3 : (large ? 2 : (p.count == 1 ? 0 : 1));
-                    if (large && p.hier != kInner) {
-                        const int D = min(kKeyLevels, c.s + (int)p.hier - 1) - (int)p.q;
-                        if (D <= kTabLevels) {
-                            tz[q] = tab_size(D);
-                            S.pD[pi] = (uint8_t)max(D, 0);
-                            tsum += tz[q];
-                        }
-                    }
-                }
-            }
-            uint32_t ttot;
-            uint32_t tex = block_exclusive_scan<kUnitNT, uint32_t>(min(tsum, (uint32_t)kTabCap + 1u), S.scan, ttot);
-            uint32_t cn[per], fn[per];
-            uint32_t sum = 0, dmax = 0, smin = 255;
-#pragma unroll
-            for (int q = 0; q < per; ++q) {
-                const int pi = threadIdx.x * per + q;
-                cn[q] = fn[q] = 0;
-                if (pi < np && S.pkind[pi] == 2) {
-                    const Piece p = pr[q];
-                    if (tz[q] != 0xFFFFFFFFu && tex + tz[q] <= (uint32_t)kTabCap) {
-                        S.pkind[pi] = 4;
-                        S.ptab[pi] = (uint16_t)tex;
-                        fn[q] = p.count;
-                    } else {
-                        cn[q] = p.count;
-                        uint32_t d = p.hier == kInner ? (uint32_t)c.dl
-                                                      : (uint32_t)min(kKeyLevels, c.s + (int)p.hier - 1);
-                        dmax = max(dmax, d);
-                        smin = min(smin, (uint32_t)p.srt);
-                    }
-                }
-                if (tz[q] != 0xFFFFFFFFu) tex += tz[q];
-                sum += cn[q] | (fn[q] << 16);
-            }
-            dmax = __reduce_max_sync(0xFFFFFFFFu, dmax);
-            smin = __reduce_min_sync(0xFFFFFFFFu, smin);
-            if (lane == 0 && dmax) atomicMax(&S.dl, dmax);
-            if (lane == 0 && smin < 255) atomicMin(&S.smin, smin);
-            uint32_t tot;
-            uint32_t ex = block_exclusive_scan<kUnitNT, uint32_t>(sum, S.scan, tot);
-            for (int q = 0; q < per; ++q) {
-                int pi = threadIdx.x * per + q;
-                if (pi < np) {
-                    S.psrt[pi] = (uint16_t)(ex & 0xFFFFu);
-                    S.pcnt[pi] = (uint16_t)cn[q];
-                    S.pfst[pi] = (uint16_t)(ex >> 16);
-                }
-                ex += cn[q] | (fn[q] << 16);
-            }
-            if (threadIdx.x == 0) {
-                S.cnt = tot & 0xFFFFu;
-                S.fcnt = tot >> 16;
-                S.tabn = min(ttot, (uint32_t)kTabCap);
-            }
-        }
-        __syncthreads();
         // ---- pieces of one point: the point is its piece's minimum
         for (int pi = threadIdx.x; pi < np; pi += kUnitNT) {
             if (S.pkind[pi] != 0) continue;
@@ -1279,6 +1290,8 @@ struct OctBufs {
     uint8_t *own_code, *leaf_code;
     uint32_t* leafid;
     uint32_t* unit_p0;
+    uint4 *pdesc, *uhead;   // window descriptors (k_unit_desc)
+    uint32_t* pdesc2;
     uint32_t* ndesc;
     SegScratch seg;
 };
@@ -1324,6 +1337,9 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.own_code = ws.take<uint8_t>(N); B.leaf_code = ws.take<uint8_t>(N);
     B.leafid = ws.take<uint32_t>(N);
     B.unit_p0 = ws.take<uint32_t>((N + kWindow - 1) / kWindow + 2);
+    B.pdesc = ws.take<uint4>(Ly.piece_cap);
+    B.pdesc2 = ws.take<uint32_t>(Ly.piece_cap);
+    B.uhead = ws.take<uint4>((N + kWindow - 1) / kWindow + 1);
     B.ndesc = ws.take<uint32_t>(Ly.node_cap);
     B.seg = take_seg_scratch(ws, N, Ly.cells, 1);
     return B;
@@ -1516,8 +1532,11 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
         if ((e = cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         const uint64_t nunits = (N + kWindow - 1) / kWindow;
         k_unit_ranges<<<(unsigned)((nunits + 1 + 255) / 256), 256, 0, st>>>(B.pk3, npieces, pcap, nunits, B.unit_p0);
+        const int gd =
+            (int)std::max<uint64_t>(1, std::min<uint64_t>((nunits * 32 + 255) / 256, (uint64_t)ws.num_sms * 8));
+        k_unit_desc<<<gd, 256, 0, st>>>(c, B.unit_p0, B.pv, nunits, B.pdesc, B.pdesc2, B.uhead);
         int grid = (int)std::min<uint64_t>(nunits, (uint64_t)ws.num_sms * 2);
-        k_units<<<grid, kUnitNT, smem, st>>>(c, B.unit_p0, B.pv, N);
+        k_units<<<grid, kUnitNT, smem, st>>>(c, B.uhead, B.pdesc, B.pdesc2, N);
         k_dup_pieces<<<ws.num_sms, 256, 0, st>>>(c);
     }
     if (grp) {   // a chunk group: its nodes below level g are appended to the caller's list
