@@ -672,10 +672,13 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
     UnitSmem& S = *reinterpret_cast<UnitSmem*>(smem_raw);
     const uint64_t nunits = (n + kWindow - 1) / kWindow;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 hn = blockIdx.x < nunits ? uhead[blockIdx.x] : make_uint4(0, 0, 0, 0);
     for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-        // piece descriptors of the window (k_unit_desc)
+        // piece descriptors of the window (k_unit_desc); the next window's
+        // header is in flight while this one is worked on
         {
-            const uint4 h = uhead[u];
+            const uint4 h = hn;
+            if (u + gridDim.x < nunits) hn = uhead[u + gridDim.x];
             if (threadIdx.x == 0) {
                 S.p0 = h.x;
                 S.np = h.y;
@@ -714,28 +717,43 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
             c.leaf_code[jj] = (uint8_t)leafl;
         }
         // ---- pieces of 2..32 points: lambda from the deepest level shared with any
-        // point of smaller index in the piece (all pairs, by shuffles)
-        for (int pi = warp; pi < np; pi += kUnitWarps) {
-            if (S.pkind[pi] != 1) continue;
-            const int cnum = S.pn[pi];
-            const uint32_t b = S.pbeg[pi];
-            uint64_t k = 0;
-            uint32_t jj = 0xFFFFFFFFu;
-            if (lane < cnum) { k = c.gk[b + lane]; jj = c.gj[b + lane]; }
-            int lm = -1;
-            for (int t = 0; t < cnum; ++t) {
-                const uint64_t kt = __shfl_sync(0xFFFFFFFFu, k, t);
-                const uint32_t jt = __shfl_sync(0xFFFFFFFFu, jj, t);
-                if (jt < jj) lm = max(lm, common_level(k, kt));
+        // point of smaller index in the piece (all pairs, by shuffles); a warp
+        // loads the records of kSmallB of its pieces before working on them
+        constexpr int kSmallB = 4;
+        for (int pb = warp; pb < np; pb += kUnitWarps * kSmallB) {
+            uint64_t kb[kSmallB];
+            uint32_t jb[kSmallB];
+            int nb[kSmallB];
+#pragma unroll
+            for (int t = 0; t < kSmallB; ++t) {
+                const int pi = pb + t * kUnitWarps;
+                nb[t] = pi < np && S.pkind[pi] == 1 ? (int)S.pn[pi] : 0;
+                kb[t] = 0;
+                jb[t] = 0xFFFFFFFFu;
+                if (lane < nb[t]) { kb[t] = c.gk[S.pbeg[pi] + lane]; jb[t] = c.gj[S.pbeg[pi] + lane]; }
             }
-            if (lane < cnum) {
-                const int q = S.pq[pi];
-                const int lambda = lm < q ? (int)S.pA[pi] : lm + 1;
-                const int leafl = S.phier[pi];
-                int K = lambda - c.s;
-                K = K < 0 ? 0 : (K > leafl ? leafl : K);
-                c.own_code[jj] = (uint8_t)K;
-                c.leaf_code[jj] = (uint8_t)leafl;
+#pragma unroll
+            for (int t = 0; t < kSmallB; ++t) {
+                const int cnum = nb[t];   // warp-uniform
+                if (cnum == 0) continue;
+                const int pi = pb + t * kUnitWarps;
+                const uint64_t k = kb[t];
+                const uint32_t jj = jb[t];
+                int lm = -1;
+                for (int q = 0; q < cnum; ++q) {
+                    const uint64_t kt = __shfl_sync(0xFFFFFFFFu, k, q);
+                    const uint32_t jt = __shfl_sync(0xFFFFFFFFu, jj, q);
+                    if (jt < jj) lm = max(lm, common_level(k, kt));
+                }
+                if (lane < cnum) {
+                    const int q0 = S.pq[pi];
+                    const int lambda = lm < q0 ? (int)S.pA[pi] : lm + 1;
+                    const int leafl = S.phier[pi];
+                    int K = lambda - c.s;
+                    K = K < 0 ? 0 : (K > leafl ? leafl : K);
+                    c.own_code[jj] = (uint8_t)K;
+                    c.leaf_code[jj] = (uint8_t)leafl;
+                }
             }
         }
         // ---- table pieces: per-level smallest index of every occupied cell
