@@ -85,8 +85,7 @@ constexpr size_t kNodeRecBytes = 24;
 struct OctGroup {
     const uint32_t* rec_counts;      // the group's points per level-g cell (0 outside the group)
     uint32_t leaf_base;              // position of the group's first point in the whole distributed array
-    uint8_t* own_code;               // per group point: LOD owner level
-    uint8_t* leaf_code;              // per group point: leaf level
+    uint16_t* codes;                 // per group point: LOD owner level | leaf level << 8
     NodeRec* deep;                   // nodes below level g, appended at *num_deep
     uint32_t deep_cap;
     uint32_t* num_deep;
@@ -109,8 +108,8 @@ uint64_t upper_node_bound(const fp_params& p);
 cudaError_t launch_octree_nodes(const uint32_t* counts, const fp_params& prm, NodeRec* recs, uint64_t rec_cap,
                                 const uint32_t* num_deep, fp_node* nodes, uint32_t node_cap, uint32_t* num_nodes,
                                 const NodeTables& T, const Workspace& ws, cudaStream_t st);
-cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint8_t* own_code,
-                                  const uint8_t* leaf_code, const NodeTables& T, const fp_params& prm,
+cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint16_t* codes,
+                                  const NodeTables& T, const fp_params& prm,
                                   uint32_t* owner, const Workspace& ws, cudaStream_t st);
 cudaError_t launch_node_first(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const uint32_t* nown,
                               uint64_t* first, uint32_t* nm, uint64_t* tiles64, cudaStream_t st);

@@ -83,8 +83,7 @@ struct OctCtx {   // device pointers of one fp_build_chunk_octree call
     NodeRec* nrec;
     uint32_t* nnode;
     uint32_t node_cap_ws;
-    uint8_t* own_code;
-    uint8_t* leaf_code;
+    uint16_t* codes;      // per record position j: LOD owner level | leaf level << 8
     uint32_t open_cap;
     int g, s, lmax, dl;
     uint64_t C;
@@ -713,8 +712,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
             const int leafl = S.phier[pi];
             int K = (int)S.pA[pi] - c.s;
             K = K < 0 ? 0 : (K > leafl ? leafl : K);
-            c.own_code[jj] = (uint8_t)K;
-            c.leaf_code[jj] = (uint8_t)leafl;
+            c.codes[jj] = (uint16_t)(K | (leafl << 8));
         }
         // ---- pieces of 2..32 points: lambda from the deepest level shared with any
         // point of smaller index in the piece (all pairs, by shuffles); a warp
@@ -751,8 +749,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
                     const int leafl = S.phier[pi];
                     int K = lambda - c.s;
                     K = K < 0 ? 0 : (K > leafl ? leafl : K);
-                    c.own_code[jj] = (uint8_t)K;
-                    c.leaf_code[jj] = (uint8_t)leafl;
+                    c.codes[jj] = (uint16_t)(K | (leafl << 8));
                 }
             }
         }
@@ -815,8 +812,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
                 const int leafl = S.phier[pi];
                 int K = lambda - c.s;
                 K = K < 0 ? 0 : (K > leafl ? leafl : K);
-                c.own_code[jq[q]] = (uint8_t)K;
-                c.leaf_code[jq[q]] = (uint8_t)leafl;
+                c.codes[jq[q]] = (uint16_t)(K | (leafl << 8));
             }
             __syncthreads();   // the tables overlay the general path's arrays
         }
@@ -1045,8 +1041,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
             if (K < 0) K = 0;
             if (K > leafl) K = leafl;
             const uint32_t jj = S.j[vv];
-            c.own_code[jj] = (uint8_t)K;
-            c.leaf_code[jj] = (uint8_t)leafl;
+            c.codes[jj] = (uint16_t)(K | (leafl << 8));
         }
         __syncthreads();
     }
@@ -1077,8 +1072,7 @@ __global__ void __launch_bounds__(256) k_dup_pieces(OctCtx c)
                 if (K < 0) K = 0;
                 if (K > leafl) K = leafl;
             }
-            c.own_code[jj] = (uint8_t)K;
-            c.leaf_code[jj] = (uint8_t)leafl;
+            c.codes[jj] = (uint16_t)(K | (leafl << 8));
         }
         __syncthreads();
     }
@@ -1191,7 +1185,7 @@ __global__ void k_node_children(const uint32_t* nnode, const uint64_t* sorted_st
 // A node deeper than g lies in the subtree of its level-g ancestor, whose ids
 // are consecutive in preorder: the search runs over that subtree only.
 __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp_cube* cube,
-                          const uint8_t* own_code, const uint8_t* leaf_code, const uint32_t* idxtab,
+                          const uint16_t* codes, const uint32_t* idxtab,
                           const uint64_t* sorted_start, const uint8_t* sorted_level, const uint32_t* ndesc,
                           const uint32_t* nnode, uint32_t* owner, uint32_t* leafid, uint32_t* n_own, int g, int lmax,
                           uint32_t* err)
@@ -1206,7 +1200,8 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
         if (j < n) {
             int4 p = ld_point(pts, j);
             uint64_t k21 = key21(p.x, p.y, p.z, cb);
-            int ks[2] = {own_code[j], leaf_code[j]};
+            const uint32_t cw = codes[j];
+            int ks[2] = {(int)(cw & 0xFFu), (int)(cw >> 8)};
             uint32_t ids[2];
             const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + (k21 >> (3 * (kKeyLevels - g)))];
             for (int t = 0; t < 2; ++t) {
@@ -1305,7 +1300,7 @@ struct OctBufs {
     uint32_t *nl, *nv2, *nv3;
     uint8_t* slevel;
     uint32_t *idxtab, *leafw, *nown;
-    uint8_t *own_code, *leaf_code;
+    uint16_t* codes;
     uint32_t* leafid;
     uint32_t* unit_p0;
     uint4 *pdesc, *uhead;   // window descriptors (k_unit_desc)
@@ -1352,7 +1347,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.idxtab = ws.take<uint32_t>(Ly.cells * 8 / 7 + 8);
     B.leafw = ws.take<uint32_t>(std::max<uint64_t>(Ly.node_cap, kScanMaxTiles));
     B.nown = ws.take<uint32_t>(Ly.node_cap);
-    B.own_code = ws.take<uint8_t>(N); B.leaf_code = ws.take<uint8_t>(N);
+    B.codes = ws.take<uint16_t>(N);
     B.leafid = ws.take<uint32_t>(N);
     B.unit_p0 = ws.take<uint32_t>((N + kWindow - 1) / kWindow + 2);
     B.pdesc = ws.take<uint4>(Ly.piece_cap);
@@ -1480,8 +1475,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
     c.dups = B.dups; c.ndups = B.counters + 1;
     c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
-    c.own_code = grp ? grp->own_code : B.own_code;
-    c.leaf_code = grp ? grp->leaf_code : B.leaf_code;
+    c.codes = grp ? grp->codes : B.codes;
     c.open_cap = (uint32_t)Ly.open_cap;
     c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
 
@@ -1574,7 +1568,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     // 8. owner and leaf ids per distributed point, owned counts
     {
         int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
-        k_resolve<<<grid, 256, 0, st>>>(sorted, N, cube, B.own_code, B.leaf_code, B.idxtab, B.nk, B.slevel, B.ndesc,
+        k_resolve<<<grid, 256, 0, st>>>(sorted, N, cube, B.codes, B.idxtab, B.nk, B.slevel, B.ndesc,
                                         nnode, owner, B.leafid, B.nown, g, lmax, ws.err);
         k_write_nown<<<(unsigned)((Ly.node_cap + 255) / 256), 256, 0, st>>>(nodes, nnode, node_cap, B.nown);
     }
@@ -1670,13 +1664,13 @@ cudaError_t launch_octree_nodes(const uint32_t* counts, const fp_params& prm, No
     return cudaMemsetAsync(T.nown, 0, rec_cap * sizeof(uint32_t), st);
 }
 
-cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint8_t* own_code,
-                                  const uint8_t* leaf_code, const NodeTables& T, const fp_params& prm,
+cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint16_t* codes,
+                                  const NodeTables& T, const fp_params& prm,
                                   uint32_t* owner, const Workspace& ws, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
     int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ws.num_sms * 16);
-    k_resolve<<<grid, 256, 0, st>>>(pts, n, cube, own_code, leaf_code, T.idxtab, T.starts, T.slevel, T.ndesc, T.nnode,
+    k_resolve<<<grid, 256, 0, st>>>(pts, n, cube, codes, T.idxtab, T.starts, T.slevel, T.ndesc, T.nnode,
                                     owner, nullptr, T.nown, (int)prm.grid_log2, (int)prm.max_level, ws.err);
     return cudaGetLastError();
 }

@@ -215,8 +215,7 @@ __global__ void k_stitch_final(const uint64_t* key, const uint32_t* val, uint64_
 struct HostStore {
     int4* pts;          // n: the distributed points, group after group
     uint32_t* perm;     // n: their original indices
-    uint8_t* own;       // n: LOD owner level
-    uint8_t* leaf;      // n: leaf level
+    uint16_t* codes;    // n: LOD owner level | leaf level << 8
     uint32_t* owner;    // n: owner id
     uint64_t* st_key;   // n: staged (owner, index)
     uint32_t* st_src;   // n: staged record's position in pts
@@ -230,8 +229,7 @@ HostStore host_carve(void* base, uint64_t n)
     HostStore h;
     h.pts = w.take<int4>(N);
     h.perm = w.take<uint32_t>(N);
-    h.own = w.take<uint8_t>(N);
-    h.leaf = w.take<uint8_t>(N);
+    h.codes = w.take<uint16_t>(N);
     h.owner = w.take<uint32_t>(N);
     h.st_key = w.take<uint64_t>(N);
     h.st_src = w.take<uint32_t>(N);
@@ -320,7 +318,7 @@ struct Group {   // device buffers of one chunk group (G points), reused group a
     char* region;   // the start of the group region
     int4* pts;
     uint32_t *perm, *owner;
-    uint8_t *own, *leaf;
+    uint16_t* codes;
     uint64_t *key, *key2, *key3;
     uint32_t *val2, *val3;
     char* ws;      // stage workspace
@@ -348,8 +346,7 @@ Group group_carve(const Workspace& w, uint64_t G, uint64_t P, const fp_params& p
     g.pts = resident ? nullptr : w.take<int4>(N);
     g.perm = resident ? nullptr : w.take<uint32_t>(N);
     g.owner = w.take<uint32_t>(N);
-    g.own = w.take<uint8_t>(N);
-    g.leaf = w.take<uint8_t>(N);
+    g.codes = w.take<uint16_t>(N);
     g.key = w.take<uint64_t>(N);
     g.key2 = w.take<uint64_t>(N);
     g.key3 = w.take<uint64_t>(N);
@@ -632,14 +629,13 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
             if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
             if ((e = cudaMemcpyAsync(B.perm, H.perm + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
         }
-        OctGroup grp{F.rcounts, (uint32_t)b0, B.own, B.leaf, F.recs, node_cap, F.num_deep};
+        OctGroup grp{F.rcounts, (uint32_t)b0, B.codes, F.recs, node_cap, F.num_deep};
         ws.used = 0;
         if ((e = launch_octree_impl(reinterpret_cast<const fp_point*>(B.pts), B.perm, ng, F.cube, F.chunks + c0,
                                     F.kdev, F.off_local, F.counts, prm, nullptr, 0, nullptr, nullptr, nullptr,
                                     nullptr, &grp, ws, st)))
             return cu(e);
-        if ((e = cudaMemcpyAsync(H.own + b0, B.own, ng, cudaMemcpyDeviceToHost, st))) return cu(e);
-        if ((e = cudaMemcpyAsync(H.leaf + b0, B.leaf, ng, cudaMemcpyDeviceToHost, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(H.codes + b0, B.codes, ng * 2, cudaMemcpyDeviceToHost, st))) return cu(e);
     }
 
     // ---- node table of the whole cloud
@@ -653,9 +649,8 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
         if (resident) B.pts = res_pts + b0;
         else if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
-        if ((e = cudaMemcpyAsync(B.own, H.own + b0, ng, cudaMemcpyHostToDevice, st))) return cu(e);
-        if ((e = cudaMemcpyAsync(B.leaf, H.leaf + b0, ng, cudaMemcpyHostToDevice, st))) return cu(e);
-        if ((e = launch_octree_resolve(reinterpret_cast<const fp_point*>(B.pts), ng, F.cube, B.own, B.leaf, F.T, prm,
+        if ((e = cudaMemcpyAsync(B.codes, H.codes + b0, ng * 2, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = launch_octree_resolve(reinterpret_cast<const fp_point*>(B.pts), ng, F.cube, B.codes, F.T, prm,
                                        B.owner, ws, st)))
             return cu(e);
         if ((e = cudaMemcpyAsync(H.owner + b0, B.owner, ng * 4, cudaMemcpyDeviceToHost, st))) return cu(e);
