@@ -780,17 +780,22 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
             for (int q = 0; q < kPer; ++q)   // all loads in flight together
                 if (pp[q] >= 0) { kq[q] = c.gk[gi[q]]; jq[q] = c.gj[gi[q]]; }
             __syncthreads();   // tables cleared
+            // deepest level first: a record that finds a smaller index in its cell
+            // stops (that index lies in every coarser cell too); a cell's minimum
+            // never does, so every cell ends with its minimum
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 if (pp[q] < 0) continue;
                 const int pi = pp[q], D = S.pD[pi], q0 = S.pq[pi];
-                atomicMin(&S.pmin[pi], jq[q]);
-                uint32_t off = S.ptab[pi];
-                for (int d = 1; d <= D; ++d) {
+                const uint32_t jv = jq[q];
+                bool least = true;
+                for (int d = D; d >= 1 && least; --d) {
                     const uint32_t idx = (uint32_t)(kq[q] >> (3 * (kKeyLevels - q0 - d))) & ((1u << (3 * d)) - 1u);
-                    atomicMin(&tab[off + idx], jq[q]);
-                    off += 1u << (3 * d);
+                    uint32_t* t = &tab[S.ptab[pi] + tab_size(d - 1) + idx];
+                    if (*t < jv) least = false;
+                    else atomicMin(t, jv);
                 }
+                if (least && S.pmin[pi] > jv) atomicMin(&S.pmin[pi], jv);
             }
             __syncthreads();
 #pragma unroll
