@@ -66,6 +66,18 @@ struct OpenNode {
 };
 static_assert(sizeof(OpenNode) == 24, "OpenNode layout");
 
+// A record of the cell-grouped arrays in one 16-byte word, so that a record is
+// moved by one load and one store: Morton key (level 21) in x | y << 32, its
+// position j in the chunk array in z; w is the counting slot in the split
+// rounds' copy and 0 elsewhere.
+FP_DEV uint4 rec_make(uint64_t key, uint32_t j, uint32_t w)
+{
+    return make_uint4((uint32_t)key, (uint32_t)(key >> 32), j, w);
+}
+FP_DEV uint64_t rec_key(const uint4& r) { return (uint64_t)r.x | ((uint64_t)r.y << 32); }
+FP_DEV uint64_t rec_key_at(const uint4* rec, uint64_t i) { return *reinterpret_cast<const uint64_t*>(rec + i); }
+FP_DEV uint32_t rec_j_at(const uint4* rec, uint64_t i) { return reinterpret_cast<const uint32_t*>(rec + i)[2]; }
+
 struct OctCtx {   // device pointers of one fp_build_chunk_octree call
     const uint32_t* counts;    // points per level-g cell: the hierarchy
     const uint32_t* rcounts;   // records per level-g cell: the points at hand (a chunk group's, or all)
@@ -73,8 +85,7 @@ struct OctCtx {   // device pointers of one fp_build_chunk_octree call
     const uint32_t* pyr;
     const uint32_t* cstart;
     uint8_t* cell_leaf;
-    uint64_t* gk;
-    uint32_t* gj;
+    uint4* rec;           // cell-grouped records (rec_key, rec_j)
     Piece* pieces;
     uint32_t* npieces;
     uint32_t piece_cap;
@@ -161,8 +172,8 @@ __global__ void k_cell_cursor_init(const uint32_t* __restrict__ cstart, uint64_t
 }
 
 __global__ void __launch_bounds__(256) k_cell_scatter(const int4* __restrict__ pts, uint64_t n, const fp_cube* cube_p,
-                                                      uint32_t* cursor, uint64_t* __restrict__ gk,
-                                                      uint32_t* __restrict__ gj, int g, uint32_t* err)
+                                                      uint32_t* cursor, uint4* __restrict__ rec, int g,
+                                                      uint32_t* err)
 {
     const CubeDev cube = load_cube(cube_p);
     const int lane = threadIdx.x & 31;
@@ -184,8 +195,7 @@ __global__ void __launch_bounds__(256) k_cell_scatter(const int4* __restrict__ p
         at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
         if (m != kNone) {
             if (at >= n) { raise(err, FP_ERR_CAPACITY); continue; }   // a count grid of other points
-            gk[at] = k;
-            gj[at] = (uint32_t)i;
+            rec[at] = rec_make(k, (uint32_t)i, 0u);
         }
     }
 }
@@ -281,8 +291,7 @@ __global__ void k_round_zero(const uint32_t* nopen, uint32_t cap, int nd, uint32
 // copy of the open nodes' records (key, j) and their slot (node, cell of the
 // round's depth), counted per slot with one atomic per slot and warp
 __global__ void k_round_copy(const OpenNode* open, const uint32_t* nopen, uint32_t cap, const uint32_t* bigstart,
-                             const uint32_t* total, const uint64_t* __restrict__ gk, const uint32_t* __restrict__ gj,
-                             uint64_t* __restrict__ tk, uint32_t* __restrict__ tj, uint32_t* __restrict__ ts, int sh,
+                             const uint32_t* total, const uint4* __restrict__ rec, uint4* __restrict__ trec, int sh,
                              uint32_t dmask, uint32_t* cnt)
 {
     const uint32_t nb = min(*nopen, cap), T = *total;
@@ -294,11 +303,9 @@ __global__ void k_round_copy(const OpenNode* open, const uint32_t* nopen, uint32
         if (p < T) {
             const uint32_t b = big_of(bigstart, nb, p);
             const uint32_t src = open[b].begin + (p - bigstart[b]);
-            const uint64_t k = gk[src];
-            tk[p] = k;
-            tj[p] = gj[src];
-            slot = (uint32_t)((k >> sh) & dmask) * cap + b;
-            ts[p] = slot;
+            const uint4 r = rec[src];
+            slot = (uint32_t)((rec_key(r) >> sh) & dmask) * cap + b;
+            trec[p] = make_uint4(r.x, r.y, r.z, slot);
         }
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
         if (slot != kNone && lane == __ffs(peers) - 1) atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
@@ -339,16 +346,16 @@ __global__ void k_round_bases(const OpenNode* open, const uint32_t* nopen, uint3
 }
 
 // the copied records back into their nodes' ranges, grouped by slot (any order inside a slot)
-__global__ void k_round_scatter(const uint32_t* total, const uint64_t* __restrict__ tk,
-                                const uint32_t* __restrict__ tj, const uint32_t* __restrict__ ts, uint32_t* cnt,
-                                uint64_t* __restrict__ gk, uint32_t* __restrict__ gj, uint64_t n, uint32_t* err)
+__global__ void k_round_scatter(const uint32_t* total, const uint4* __restrict__ trec, uint32_t* cnt,
+                                uint4* __restrict__ rec, uint64_t n, uint32_t* err)
 {
     const uint32_t T = *total;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); p0 < T; p0 += stride) {   // warp-uniform
         const uint32_t p = p0 + lane;
-        const uint32_t slot = p < T ? ts[p] : kNone;
+        const uint4 r = p < T ? trec[p] : make_uint4(0u, 0u, 0u, kNone);
+        const uint32_t slot = r.w;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
         const int leader = __ffs(peers) - 1;
         uint32_t at = 0;
@@ -356,8 +363,7 @@ __global__ void k_round_scatter(const uint32_t* total, const uint64_t* __restric
         at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
         if (slot == kNone) continue;
         if (at >= n) { raise(err, FP_ERR_CAPACITY); continue; }
-        gk[at] = tk[p];
-        gj[at] = tj[p];
+        rec[at] = make_uint4(r.x, r.y, r.z, 0u);
     }
 }
 
@@ -381,7 +387,7 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
             uint32_t a = o.begin, b = o.begin + o.count;
             while (a < b) {
                 uint32_t mid = (a + b) >> 1;
-                if ((int)((c.gk[mid] >> sh) & 7) < lane) a = mid + 1;
+                if ((int)((rec_key_at(c.rec, mid) >> sh) & 7) < lane) a = mid + 1;
                 else b = mid;
             }
             lo = a;
@@ -396,10 +402,11 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
             uint32_t mj = 0xFFFFFFFFu;
             uint32_t r = cb + lane;
             for (; r + 96 < ce; r += 128) {   // four independent loads in flight per lane
-                const uint32_t v0 = c.gj[r], v1 = c.gj[r + 32], v2 = c.gj[r + 64], v3 = c.gj[r + 96];
+                const uint32_t v0 = rec_j_at(c.rec, r), v1 = rec_j_at(c.rec, r + 32), v2 = rec_j_at(c.rec, r + 64),
+                               v3 = rec_j_at(c.rec, r + 96);
                 mj = min(mj, min(min(v0, v1), min(v2, v3)));
             }
-            for (; r < ce; r += 32) mj = min(mj, c.gj[r]);
+            for (; r < ce; r += 32) mj = min(mj, rec_j_at(c.rec, r));
             for (int off = 16; off > 0; off >>= 1) mj = min(mj, __shfl_xor_sync(0xFFFFFFFFu, mj, off));
             mjd[d] = mj;
             pmin = min(pmin, mj);
@@ -708,7 +715,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
         // ---- pieces of one point: the point is its piece's minimum
         for (int pi = threadIdx.x; pi < np; pi += kUnitNT) {
             if (S.pkind[pi] != 0) continue;
-            const uint32_t jj = c.gj[S.pbeg[pi]];
+            const uint32_t jj = rec_j_at(c.rec, S.pbeg[pi]);
             const int leafl = S.phier[pi];
             int K = (int)S.pA[pi] - c.s;
             K = K < 0 ? 0 : (K > leafl ? leafl : K);
@@ -728,7 +735,11 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
                 nb[t] = pi < np && S.pkind[pi] == 1 ? (int)S.pn[pi] : 0;
                 kb[t] = 0;
                 jb[t] = 0xFFFFFFFFu;
-                if (lane < nb[t]) { kb[t] = c.gk[S.pbeg[pi] + lane]; jb[t] = c.gj[S.pbeg[pi] + lane]; }
+                if (lane < nb[t]) {
+                    const uint4 r = c.rec[S.pbeg[pi] + lane];
+                    kb[t] = rec_key(r);
+                    jb[t] = r.z;
+                }
             }
 #pragma unroll
             for (int t = 0; t < kSmallB; ++t) {
@@ -778,7 +789,11 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
             }
 #pragma unroll
             for (int q = 0; q < kPer; ++q)   // all loads in flight together
-                if (pp[q] >= 0) { kq[q] = c.gk[gi[q]]; jq[q] = c.gj[gi[q]]; }
+                if (pp[q] >= 0) {
+                    const uint4 r = c.rec[gi[q]];
+                    kq[q] = rec_key(r);
+                    jq[q] = r.z;
+                }
             __syncthreads();   // tables cleared
             // deepest level first: a record that finds a smaller index in its cell
             // stops (that index lies in every coarser cell too); a cell's minimum
@@ -843,7 +858,11 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
             uint32_t jq[kPer];
 #pragma unroll
             for (int q = 0; q < kPer; ++q)   // all loads in flight together
-                if ((int)threadIdx.x + q * kUnitNT < cnt) { kq[q] = c.gk[gi[q]]; jq[q] = c.gj[gi[q]]; }
+                if ((int)threadIdx.x + q * kUnitNT < cnt) {
+                    const uint4 r = c.rec[gi[q]];
+                    kq[q] = rec_key(r);
+                    jq[q] = r.z;
+                }
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 const int r = threadIdx.x + q * kUnitNT;
@@ -1063,14 +1082,14 @@ __global__ void __launch_bounds__(256) k_dup_pieces(OctCtx c)
         const Piece p = c.pieces[c.dups[k]];
         const int leafl = p.hier == kInner ? c.lmax : (int)p.hier;
         uint32_t mn = kNone;
-        for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) mn = min(mn, c.gj[p.begin + r]);
+        for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) mn = min(mn, rec_j_at(c.rec, p.begin + r));
         mn = __reduce_min_sync(0xFFFFFFFFu, mn);
         if (lane == 0) s_min[warp] = mn;
         __syncthreads();
         mn = s_min[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mn = min(mn, s_min[w]);
         for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) {
-            uint32_t jj = c.gj[p.begin + r];
+            uint32_t jj = rec_j_at(c.rec, p.begin + r);
             int K = leafl;
             if (jj == mn) {
                 K = (int)p.A - c.s;
@@ -1285,14 +1304,12 @@ uint64_t node_capacity_bound(uint64_t n, const fp_params& p) { return oct_layout
 struct OctBufs {
     SortScratch sc;
     uint32_t* rcnt;        // counting slots of a split round: 8^3 per open node
-    uint64_t* t_k1;
-    uint32_t *t_j1, *t_j2;
+    uint4* trec;   // split rounds: the copied records with their slots
     int4* lt_pt;
     uint32_t *lt_val, *lt_k32;
     uint32_t *pyr, *cstart, *cursor;
     uint8_t* cell_leaf;
-    uint64_t* gk;
-    uint32_t* gj;
+    uint4* rec;           // cell-grouped records (rec_key, rec_j)
     Piece* pieces;
     uint32_t* counters;   // [0] pieces, [1] pieces of equal keys, [3] node records
     uint32_t* dups;
@@ -1323,8 +1340,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.rcnt = ws.take<uint32_t>(Ly.open_cap << (3 * kRoundLevels));
     // aliased phase region: grouping temporaries, later the leaf scatter temporaries
     const size_t phase_base = ws.used;
-    B.t_k1 = ws.take<uint64_t>(N); B.t_j1 = ws.take<uint32_t>(N);
-    B.t_j2 = ws.take<uint32_t>(N);
+    B.trec = ws.take<uint4>(N);
     const size_t phase_end = ws.used;
     ws.used = phase_base;
     B.lt_pt = ws.take<int4>(N); B.lt_val = ws.take<uint32_t>(N); B.lt_k32 = ws.take<uint32_t>(N);
@@ -1333,7 +1349,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.cstart = ws.take<uint32_t>(Ly.cells + 1);
     B.cursor = ws.take<uint32_t>(Ly.cells);
     B.cell_leaf = ws.take<uint8_t>(Ly.cells);
-    B.gk = ws.take<uint64_t>(N); B.gj = ws.take<uint32_t>(N);
+    B.rec = ws.take<uint4>(N);
     B.pieces = ws.take<Piece>(Ly.piece_cap);
     B.counters = ws.take<uint32_t>(4);
     B.dups = ws.take<uint32_t>(Ly.piece_cap);
@@ -1477,7 +1493,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     OctCtx c;
     c.counts = counts; c.rcounts = rcounts; c.leaf_base = grp ? grp->leaf_base : 0u;
     c.pyr = B.pyr; c.cstart = B.cstart; c.cell_leaf = B.cell_leaf;
-    c.gk = B.gk; c.gj = B.gj; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
+    c.rec = B.rec; c.pieces = B.pieces; c.npieces = npieces; c.piece_cap = (uint32_t)Ly.piece_cap;
     c.dups = B.dups; c.ndups = B.counters + 1;
     c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
     c.codes = grp ? grp->codes : B.codes;
@@ -1489,7 +1505,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
         const int gcell = (int)std::max<uint64_t>(1, std::min<uint64_t>((Ly.cells + 255) / 256, ws.num_sms * 8ull));
         k_cell_cursor_init<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g);
         const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 8));
-        k_cell_scatter<<<gs, 256, 0, st>>>(reinterpret_cast<const int4*>(sorted), N, cube, B.cursor, B.gk, B.gj, g,
+        k_cell_scatter<<<gs, 256, 0, st>>>(reinterpret_cast<const int4*>(sorted), N, cube, B.cursor, B.rec, g,
                                            ws.err);
         k_cell_check<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g, ws.err);
     }
@@ -1513,11 +1529,10 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
                                                         (uint32_t*)nullptr, st)))
                 return e;
             k_round_zero<<<gr, 256, 0, st>>>(B.ocount + cur, cap, nd, B.rcnt);
-            k_round_copy<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, cap, B.bigstart, B.ocount + 3, B.gk, B.gj,
-                                             B.t_k1, B.t_j1, B.t_j2, 3 * (kKeyLevels - q - k), (uint32_t)(nd - 1),
-                                             B.rcnt);
+            k_round_copy<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, cap, B.bigstart, B.ocount + 3, B.rec,
+                                             B.trec, 3 * (kKeyLevels - q - k), (uint32_t)(nd - 1), B.rcnt);
             k_round_bases<<<gw, 256, 0, st>>>(B.open[cur], B.ocount + cur, cap, nd, B.rcnt);
-            k_round_scatter<<<gr, 256, 0, st>>>(B.ocount + 3, B.t_k1, B.t_j1, B.t_j2, B.rcnt, B.gk, B.gj, N, ws.err);
+            k_round_scatter<<<gr, 256, 0, st>>>(B.ocount + 3, B.trec, B.rcnt, B.rec, N, ws.err);
             for (int l = q; l < q + k; ++l) {
                 k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
                 k_split<<<gw, 256, 0, st>>>(c, B.open[cur], B.ocount + cur, B.open[1 - cur], B.ocount + (1 - cur),
