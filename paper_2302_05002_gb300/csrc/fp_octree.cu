@@ -1207,7 +1207,9 @@ __global__ void k_node_children(const uint32_t* nnode, const uint64_t* sorted_st
 
 // owner and leaf ids of every distributed point; owned counts per node
 // A node deeper than g lies in the subtree of its level-g ancestor, whose ids
-// are consecutive in preorder: the search runs over that subtree only.
+// are consecutive in preorder: the search runs over that subtree only.  Keys
+// are taken at max_level (no node is deeper): 32-bit for max_level <= 10.
+template <bool SMALL>
 __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp_cube* cube,
                           const uint16_t* codes, const uint32_t* idxtab,
                           const uint64_t* sorted_start, const uint8_t* sorted_level, const uint32_t* ndesc,
@@ -1215,6 +1217,7 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
                           uint32_t* err)
 {
     const CubeDev cb = load_cube(cube);
+    const float scale_l = SMALL ? scale_at(cb, lmax) : 0.f;
     const uint32_t M = *nnode;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -1222,15 +1225,17 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
         uint64_t j = i0 + threadIdx.x;
         uint32_t oid = kNone;
         if (j < n) {
-            int4 p = ld_point(pts, j);
-            uint64_t k21 = key21(p.x, p.y, p.z, cb);
+            const int4 p = ld_point(pts, j);
+            const uint64_t kl = SMALL ? (uint64_t)key_small(p.x, p.y, p.z, cb, scale_l, lmax)
+                                      : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
             const uint32_t cw = codes[j];
             int ks[2] = {(int)(cw & 0xFFu), (int)(cw >> 8)};
             uint32_t ids[2];
-            const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + (k21 >> (3 * (kKeyLevels - g)))];
+            const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + (kl >> (3 * (lmax - g)))];
             for (int t = 0; t < 2; ++t) {
-                int L = ks[t];
-                uint64_t k = k21 >> (3 * (kKeyLevels - L));
+                const int L = ks[t];
+                if (L > lmax) { ids[t] = kNone; continue; }
+                const uint64_t k = kl >> (3 * (lmax - L));
                 if (L <= g) {
                     ids[t] = idxtab[((1ull << (3 * L)) - 1) / 7 + k];
                 } else {
@@ -1241,7 +1246,6 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
                         if (r != kNone) ids[t] = c0 + r;
                     }
                 }
-                if (L > lmax) ids[t] = kNone;
             }
             if (ids[0] >= M || ids[1] >= M) {   // never for a consistent tree
                 raise(err, FP_ERR_CAPACITY);
@@ -1588,8 +1592,9 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     // 8. owner and leaf ids per distributed point, owned counts
     {
         int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
-        k_resolve<<<grid, 256, 0, st>>>(sorted, N, cube, B.codes, B.idxtab, B.nk, B.slevel, B.ndesc,
-                                        nnode, owner, B.leafid, B.nown, g, lmax, ws.err);
+        auto kres = lmax <= 10 ? k_resolve<true> : k_resolve<false>;
+        kres<<<grid, 256, 0, st>>>(sorted, N, cube, B.codes, B.idxtab, B.nk, B.slevel, B.ndesc, nnode, owner, B.leafid,
+                                   B.nown, g, lmax, ws.err);
         k_write_nown<<<(unsigned)((Ly.node_cap + 255) / 256), 256, 0, st>>>(nodes, nnode, node_cap, B.nown);
     }
     // 9. leaf-grouped points: stable scatter by leaf id, chunk by chunk (every
@@ -1690,8 +1695,9 @@ cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube
 {
     if (n == 0) return cudaSuccess;
     int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ws.num_sms * 16);
-    k_resolve<<<grid, 256, 0, st>>>(pts, n, cube, codes, T.idxtab, T.starts, T.slevel, T.ndesc, T.nnode,
-                                    owner, nullptr, T.nown, (int)prm.grid_log2, (int)prm.max_level, ws.err);
+    auto kres = prm.max_level <= 10 ? k_resolve<true> : k_resolve<false>;
+    kres<<<grid, 256, 0, st>>>(pts, n, cube, codes, T.idxtab, T.starts, T.slevel, T.ndesc, T.nnode, owner, nullptr,
+                               T.nown, (int)prm.grid_log2, (int)prm.max_level, ws.err);
     return cudaGetLastError();
 }
 
