@@ -1391,9 +1391,9 @@ size_t octree_ws_bytes(uint64_t n, const fp_params& p)
 }
 
 template <int DIG, bool CPT, bool CK64, bool CK32>
-static cudaError_t run_sort(const SortScratch& sc, SortArgs a, const Workspace& ws, cudaStream_t st)
+static cudaError_t run_sort(const SortScratch& sc, SortArgs a, int npass, const Workspace& ws, cudaStream_t st)
 {
-    for (int slot = 0; slot < kSortMaxPass; ++slot) {
+    for (int slot = 0; slot < npass; ++slot) {
         cudaError_t e = sort_run_pass<DIG, CPT, CK64, CK32>(sc, a, slot, ws.num_sms, st);
         if (e) return e;
     }
@@ -1423,14 +1423,14 @@ static cudaError_t node_table(const SortScratch& sc, const NodeRec* nrec, uint32
     a.b.k64_src = B.nk3; a.b.k64_tmp = B.nk2; a.b.k64_dst = B.nk4;
     a.b.val_src = nullptr; a.b.val_tmp = B.nv2; a.b.val_dst = B.nv3;
     a.n = ncap; a.d_n = nnode; a.err = ws.err;
-    if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
+    if ((e = run_sort<DIG_K64, false, true, false>(sc, a, sort_passes(5), ws, st))) return e;
     k_gather_u64<<<gn, 256, 0, st>>>(B.nk, B.nv3, nnode, B.nk3);
     if ((e = sort_plan_keys(sc, B.nk3, ncap, nnode, 0, (uint32_t)std::max(1, 3 * lmax), st))) return e;
     SortArgs b2{};
     b2.b.k64_src = B.nk3; b2.b.k64_tmp = B.nk2; b2.b.k64_dst = B.nk;   // nk <- sorted starts
     b2.b.val_src = B.nv3; b2.b.val_tmp = B.nv2; b2.b.val_dst = B.nl;   // nl <- record of preorder position
     b2.n = ncap; b2.d_n = nnode; b2.err = ws.err;
-    if ((e = run_sort<DIG_K64, false, true, false>(sc, b2, ws, st))) return e;
+    if ((e = run_sort<DIG_K64, false, true, false>(sc, b2, sort_passes(3 * lmax), ws, st))) return e;
     k_node_write<<<gn, 256, 0, st>>>(nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, num_nodes, B.idxtab, B.leafw,
                                      g, lmax, ws.err);
     k_node_fill<<<gn, 256, 0, st>>>(nrec, nnode, B.nl, B.nk, B.slevel, nodes, node_cap, B.ndesc, lmax);
@@ -1563,7 +1563,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
         a.b.k64_src = B.pk; a.b.k64_tmp = B.pk2; a.b.k64_dst = B.pk3;
         a.b.val_src = nullptr; a.b.val_tmp = B.pv2; a.b.val_dst = B.pv;
         a.n = pcap; a.d_n = npieces; a.err = ws.err;
-        if ((e = run_sort<DIG_K64, false, true, false>(sc, a, ws, st))) return e;
+        if ((e = run_sort<DIG_K64, false, true, false>(sc, a, sort_passes(bits), ws, st))) return e;
         const size_t smem = sizeof(UnitSmem);
         if ((e = cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         const uint64_t nunits = (N + kWindow - 1) / kWindow;
@@ -1621,8 +1621,9 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
         a.b.val_src = perm; a.b.val_tmp = B.lt_val; a.b.val_dst = leaf_perm;
         a.b.k32_src = B.leafid; a.b.k32_tmp = B.lt_k32; a.b.k32_dst = nullptr;
         a.n = N; a.d_n = B.seg.cnt + 5; a.err = ws.err;
-        if (leaf_pts) e = run_sort<DIG_K32, true, false, true>(sc, a, ws, st);
-        else e = run_sort<DIG_K32, false, false, true>(sc, a, ws, st);
+        const int np = sort_passes(count_bits(Ly.node_cap));   // leaf ids below node_cap
+        if (leaf_pts) e = run_sort<DIG_K32, true, false, true>(sc, a, np, ws, st);
+        else e = run_sort<DIG_K32, false, false, true>(sc, a, np, ws, st);
         if (e) return e;
     }
     return cudaGetLastError();
@@ -1938,7 +1939,8 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
         b.b.k64_src = B.s_key; b.b.k64_tmp = B.s_key2; b.b.k64_dst = B.s_key3;
         b.b.val_src = B.s_val; b.b.val_tmp = B.s_val2; b.b.val_dst = B.s_val3;
         b.n = N; b.d_n = nstaged; b.err = ws.err;
-        for (int slot = 0; slot < kSortMaxPass; ++slot)
+        const int np = sort_passes(pbits + count_bits(M));   // node ids below M above the index bits
+        for (int slot = 0; slot < np; ++slot)
             if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, b, slot, ws.num_sms, st))) return e;
     }
     k_stitch_place<<<gN, 256, 0, st>>>(nstaged, B.s_key3, B.s_val3, pbits, nm, soff, first,
@@ -1955,7 +1957,7 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     a.b.val_src = perm; a.b.val_tmp = B.t_val; a.b.val_dst = final_perm;
     a.b.k32_src = owner; a.b.k32_tmp = B.t_k32; a.b.k32_dst = B.fown;
     a.n = N; a.d_n = gate; a.err = ws.err;
-    for (int slot = 0; slot < kSortMaxPass; ++slot)
+    for (int slot = 0; slot < sort_passes(count_bits(M)); ++slot)
         if ((e = sort_run_pass<DIG_K32, true, false, true>(sc, a, slot, ws.num_sms, st))) return e;
     if ((e = cudaMemsetAsync(mark, 0, (size_t)M * 4, st))) return e;
     if ((e = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), st))) return e;
@@ -1973,7 +1975,7 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     b.b.k64_src = B.s_key; b.b.k64_tmp = B.s_key2; b.b.k64_dst = B.s_key3;
     b.b.val_src = B.s_val; b.b.val_tmp = B.s_val2; b.b.val_dst = B.s_val3;
     b.n = N; b.d_n = cnt + 1; b.err = ws.err;
-    for (int slot = 0; slot < kSortMaxPass; ++slot)
+    for (int slot = 0; slot < sort_passes(32 + rank_bits); ++slot)
         if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, b, slot, ws.num_sms, st))) return e;
     k_stitch_gather<<<gN, 256, 0, st>>>(cnt + 1, B.s_val3,
                                                                   reinterpret_cast<const int4*>(final_pts),

@@ -687,7 +687,7 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         a.b.k64_src = B.key; a.b.k64_tmp = B.key2; a.b.k64_dst = B.key3;
         a.b.val_src = nullptr; a.b.val_tmp = B.val2; a.b.val_dst = B.val3;
         a.n = ng; a.err = base.err;
-        for (int slot = 0; slot < kSortMaxPass; ++slot)
+        for (int slot = 0; slot < sort_passes(mbits); ++slot)
             if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, a, slot, base.num_sms, st))) return cu(e);
         k_run_starts<<<grid_for(ng, base.num_sms), 256, 0, st>>>(B.key3, ng, 0, F.soff, M);
         k_group_place<<<grid_for(ng, base.num_sms), 256, 0, st>>>(
@@ -720,7 +720,7 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         a.b.k64_src = k1; a.b.k64_tmp = k2; a.b.k64_dst = k3;
         a.b.val_src = nullptr; a.b.val_tmp = v2; a.b.val_dst = v3;
         a.n = S; a.err = base.err;
-        for (int slot = 0; slot < kSortMaxPass; ++slot)
+        for (int slot = 0; slot < sort_passes(pbits + mbits); ++slot)
             if ((e = sort_run_pass<DIG_K64, false, true, false>(sf, a, slot, base.num_sms, st))) return cu(e);
         k_run_starts<<<grid_for(S, base.num_sms), 256, 0, st>>>(k3, S, pbits, F.soff, M);
         k_stitch_final<<<grid_for(S, base.num_sms), 256, 0, st>>>(k3, v3, S, pbits, F.soff, F.first, H.st_src, H.pts,

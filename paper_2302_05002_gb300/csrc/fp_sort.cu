@@ -204,7 +204,8 @@ cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cu
     a.g = g;
     a.err = ws.err;
     a.run_if = run_sort;
-    for (int slot = 0; slot < kSortMaxPass; ++slot) {
+    const int npass = sort_passes(count_bits(1ull << (3 * g)));   // chunk ids below 8^g
+    for (int slot = 0; slot < npass; ++slot) {
         e = sort_run_pass<DIG_CHUNK, true, false, false>(sc, a, slot, ws.num_sms, st);
         if (e) return e;
     }

@@ -365,6 +365,20 @@ __global__ void k_plan_hist_keys(const uint64_t* keys, uint64_t n, const uint32_
                                  uint32_t total_bits, uint32_t* hist, const uint32_t* d_rank_n);
 
 // host helpers
+// Launch bound of a sort: the device plan of keys with `bits` significant bits
+// takes ceil(bits / kSortMaxBits) passes (ids below nw: count_bits(nw) bits);
+// the passes past the plan exit at once, so launching this many suffices.
+inline int sort_passes(uint64_t bits)
+{
+    bits = bits < 1 ? 1 : (bits > 64 ? 64 : bits);
+    return (int)((bits + kSortMaxBits - 1) / kSortMaxBits);
+}
+inline uint32_t count_bits(uint64_t v)   // bits of v - 1, at least 1, as the device plan counts them
+{
+    uint32_t b = 1;
+    while (b < 64 && ((v ? v - 1 : 0) >> b)) ++b;
+    return b;
+}
 struct SortScratch {
     SortPlan* plan;
     uint64_t* bases;
