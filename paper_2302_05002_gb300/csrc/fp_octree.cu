@@ -1794,14 +1794,17 @@ __global__ void k_stitch_counts(const uint8_t* inside, const uint32_t* nown, con
     scnt[i] = i < *nm && !inside[i] ? nown[i] : 0u;
 }
 
-// sorted staging record t = (node X, original index): final position first[X] + rank inside X
+// sorted staging record t = (rank of node X, original index): final position
+// first[X] + rank inside X
 __global__ void k_stitch_place(const uint32_t* nstaged, const uint64_t* key, const uint32_t* src, int shift,
-                               const uint32_t* nm, const uint32_t* soff, const uint64_t* first, const int4* pts,
-                               const uint32_t* perm, uint64_t n, int4* fin, uint32_t* fperm, uint32_t* err)
+                               const uint32_t* list, const uint32_t* nlist, const uint32_t* nm, const uint32_t* soff,
+                               const uint64_t* first, const int4* pts, const uint32_t* perm, uint64_t n, int4* fin,
+                               uint32_t* fperm, uint32_t* err)
 {
-    const uint32_t S = *nstaged, M = *nm;
+    const uint32_t S = *nstaged, M = *nm, R = *nlist;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < S; t += gridDim.x * blockDim.x) {
-        const uint32_t X = (uint32_t)(key[t] >> shift);
+        const uint32_t r = (uint32_t)(key[t] >> shift);
+        const uint32_t X = r < R ? list[r] : M;
         const uint32_t j = src[t];
         const uint64_t f = X < M ? first[X] + (t - soff[X]) : n;
         if (f >= n || j >= n) { raise(err, FP_ERR_CAPACITY); continue; }
@@ -1828,6 +1831,7 @@ static const uint64_t kMaxScanNodes = (uint64_t)kScanTile * kScanMaxTiles;
 struct SubBufs {
     SortScratch sc;
     uint32_t *nown, *mark, *mrank, *mlist, *mown, *soff, *cnt;
+    uint32_t *srank, *slist;   // staging: rank of a node outside every chunk subtree, and back
     uint64_t* first;
     int4* t_pt;
     uint32_t *t_val, *t_k32, *fown;
@@ -1851,7 +1855,8 @@ static SubBufs sub_carve(const Workspace& ws, uint64_t n, uint64_t M)
     B.sc = take_sort_scratch(ws, N);
     B.nown = ws.take<uint32_t>(M); B.first = ws.take<uint64_t>(M + 1);
     B.mark = ws.take<uint32_t>(M); B.mrank = ws.take<uint32_t>(M); B.mlist = ws.take<uint32_t>(M);
-    B.mown = ws.take<uint32_t>(M); B.soff = ws.take<uint32_t>(M + 1); B.cnt = ws.take<uint32_t>(4);
+    B.mown = ws.take<uint32_t>(M); B.soff = ws.take<uint32_t>(M + 1); B.cnt = ws.take<uint32_t>(8);
+    B.srank = ws.take<uint32_t>(M); B.slist = ws.take<uint32_t>(M);
     // One region serves three sets of per-point buffers that are never live
     // together: the whole-array path's sort temporaries and owner copy (dead
     // once its unsorted segments are marked), the stitch records and their
@@ -1927,13 +1932,15 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     sg.n = N;
     sg.first = first; sg.first_stride = 1;
     sg.st_key = B.s_key; sg.st_src = B.s_val; sg.st_count = nstaged; sg.st_shift = pbits;
+    uint32_t* nrank = cnt + 4;   // nodes outside every chunk subtree
+    sg.st_rank = B.srank; sg.st_list = B.slist; sg.st_nrank = nrank; sg.st_tiles = B.tiles32;
     if ((e = seg_scatter(B.seg, sg, ws, st))) return e;
     // 2. the stitch: staged records sorted by (node, original index), then placed
     k_stitch_counts<<<gM, 256, 0, st>>>(B.seg.inside, nown, nm, B.scnt, M);
     if ((e = scan_exclusive<uint32_t, uint32_t>(B.scnt, soff, M, nm, B.tiles32, (uint32_t*)nullptr,
                                                 (uint32_t*)nullptr, st)))
         return e;
-    if ((e = sort_plan_keys(sc, B.s_key, N, nstaged, 0, (uint32_t)pbits, st, nm))) return e;
+    if ((e = sort_plan_keys(sc, B.s_key, N, nstaged, 0, (uint32_t)pbits, st, nrank))) return e;
     {
         SortArgs b{};
         b.b.k64_src = B.s_key; b.b.k64_tmp = B.s_key2; b.b.k64_dst = B.s_key3;
@@ -1943,7 +1950,7 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
         for (int slot = 0; slot < np; ++slot)
             if ((e = sort_run_pass<DIG_K64, false, true, false>(sc, b, slot, ws.num_sms, st))) return e;
     }
-    k_stitch_place<<<gN, 256, 0, st>>>(nstaged, B.s_key3, B.s_val3, pbits, nm, soff, first,
+    k_stitch_place<<<gN, 256, 0, st>>>(nstaged, B.s_key3, B.s_val3, pbits, B.slist, nrank, nm, soff, first,
                                        reinterpret_cast<const int4*>(sorted), perm, N,
                                        reinterpret_cast<int4*>(final_pts), final_perm, ws.err);
 

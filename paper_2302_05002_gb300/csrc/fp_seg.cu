@@ -61,6 +61,20 @@ __global__ void k_seg_setup(int mode, const fp_node* nodes, const uint32_t* num_
     }
 }
 
+// owner layout: 1 for a node outside every chunk subtree (then its rank, by the scan)
+__global__ void k_outside_flags(const uint8_t* inside, const uint32_t* num_nodes, uint32_t cap, uint32_t* flag)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cap) flag[i] = i < min(*num_nodes, cap) && !inside[i] ? 1u : 0u;
+}
+
+__global__ void k_outside_list(const uint8_t* inside, const uint32_t* num_nodes, uint32_t cap, const uint32_t* rank,
+                               uint32_t* list)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < min(*num_nodes, cap) && !inside[i]) list[rank[i]] = i;
+}
+
 // clear the status words that later tiles of the same chunk will read
 template <int MAXB>
 __global__ void k_seg_zero(const SegTile* tiles, const uint32_t* d_ntiles, uint64_t tiles_max,
@@ -233,6 +247,14 @@ cudaError_t seg_scatter(const SegScratch& sc, const SegCall& c, const Workspace&
     k_seg_setup<<<gk, 256, 0, st>>>((int)c.mode, c.nodes, c.num_nodes, c.node_cap, c.chunks, c.num_chunks,
                                     c.offsets, sc.kmax, c.n, sc.lo, sc.nb, sc.tiles[0], sc.tiles[1], sc.tiles_max, sc.cnt,
                                     owner ? sc.inside : nullptr, ws.err);
+    if (owner && c.st_rank) {
+        const unsigned gn = (c.node_cap + 255) / 256;
+        k_outside_flags<<<gn, 256, 0, st>>>(sc.inside, c.num_nodes, c.node_cap, c.st_rank);
+        if ((e = scan_exclusive<uint32_t, uint32_t>(c.st_rank, c.st_rank, c.node_cap, nullptr, c.st_tiles, c.st_nrank,
+                                                    (uint32_t*)nullptr, st)))
+            return e;
+        k_outside_list<<<gn, 256, 0, st>>>(sc.inside, c.num_nodes, c.node_cap, c.st_rank, c.st_list);
+    }
     const int gz = std::max(1, ws.num_sms * 8);
     k_seg_zero<kSegSmallBits><<<gz, 256, 0, st>>>(sc.tiles[0], sc.cnt + 0, sc.tiles_max, c.offsets, sc.nb,
                                                    sc.status[0], sc.cnt + 2);
@@ -247,6 +269,7 @@ cudaError_t seg_scatter(const SegScratch& sc, const SegCall& c, const Workspace&
     a.first = c.first; a.first_stride = c.first_stride;
     a.stitch = owner ? 1 : 0;
     a.st_key = c.st_key; a.st_src = c.st_src; a.st_count = c.st_count; a.st_cap = c.n; a.st_shift = c.st_shift;
+    a.st_rank = owner ? c.st_rank : nullptr;
     a.n = c.out_n ? c.out_n : c.n;
     a.d_fail = sc.cnt + 2;
     a.err = ws.err;

@@ -47,7 +47,8 @@ struct SegArgs {
     uint32_t* status;                     // [row][1 << MAXB], row = tile start / kSortTile
     uint32_t* counter;
     int stitch;                           // nonzero: the chunk's last digit is the staging digit
-    uint64_t* st_key;                     // (node id << st_shift) | original index
+    uint64_t* st_key;                     // (node << st_shift) | original index, node = st_rank[id] or id
+    const uint32_t* st_rank;              // nullable: rank of a node among those outside every chunk subtree
     uint32_t* st_src;                     // position in the chunk array
     uint32_t* st_count;
     uint64_t st_cap;
@@ -244,7 +245,8 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
             if (d == sdig) {
                 if (o >= a.st_cap) { raise(a.err, FP_ERR_CAPACITY); continue; }
                 const uint64_t src = base + s_pos[q];
-                a.st_key[o] = ((uint64_t)a.id_in[src] << a.st_shift) | s_val[q];
+                const uint32_t id = a.id_in[src];
+                a.st_key[o] = ((uint64_t)(a.st_rank ? a.st_rank[id] : id) << a.st_shift) | s_val[q];
                 a.st_src[o] = (uint32_t)src;
             } else {
                 if (o >= a.n) { raise(a.err, FP_ERR_CAPACITY); continue; }   // inconsistent node table
@@ -282,6 +284,11 @@ struct SegCall {
     const uint64_t* first; uint32_t first_stride;
     // owner layout: staging
     uint64_t* st_key; uint32_t* st_src; uint32_t* st_count; int st_shift;
+    // owner layout, nullable: staging keys by rank among the nodes outside every
+    // chunk subtree (in node order, so the sorted order is that of node ids):
+    // st_rank[node] (node_cap), st_list[rank] = node, *st_nrank = their number;
+    // st_tiles: scan scratch (kScanMaxTiles)
+    uint32_t *st_rank, *st_list, *st_nrank, *st_tiles;
 };
 
 // Distribution of n points into 257..2048 chunks in one sweep: one segment
