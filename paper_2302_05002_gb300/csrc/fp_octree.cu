@@ -63,8 +63,10 @@ struct OpenNode {
     uint64_t key;
     uint32_t begin, count;
     uint8_t q, hier, A, pad;
+    uint32_t rb;          // its ancestor-or-self in the open list the current round started from
+    uint32_t pad2, pad3;
 };
-static_assert(sizeof(OpenNode) == 24, "OpenNode layout");
+static_assert(sizeof(OpenNode) == 32, "OpenNode layout");
 
 // A record of the cell-grouped arrays in one 16-byte word, so that a record is
 // moved by one load and one store: Morton key (level 21) in x | y << 32, its
@@ -236,6 +238,7 @@ __global__ void k_cell_setup(OctCtx c, OpenNode* open0, uint32_t* nopen0)
         o.hier = hier;
         o.A = (uint8_t)c.g;
         o.pad = 0;
+        o.rb = o.pad2 = o.pad3 = 0;
         open0[id] = o;
     }
 }
@@ -280,35 +283,47 @@ __global__ void k_open_counts(const OpenNode* open0, const uint32_t* nopen0, uin
 
 // Counting slots of a round are digit-major (slot = d * cap + node): the cells
 // of one node, used together, lie far apart in the array (and in L2 slices).
-__global__ void k_round_zero(const uint32_t* nopen, uint32_t cap, int nd, uint32_t* cnt)
+__global__ void k_round_zero(const uint32_t* nopen, uint32_t cap, int nd, uint32_t* cnt, uint32_t* smin)
 {
     const uint32_t nb = min(*nopen, cap);
     const uint64_t tot = (uint64_t)nb * nd;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < tot; x += (uint64_t)gridDim.x * blockDim.x)
-        cnt[(x / nb) * cap + x % nb] = 0;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < tot; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t slot = (x / nb) * cap + x % nb;
+        cnt[slot] = 0;
+        smin[slot] = kNone;
+    }
 }
 
 // copy of the open nodes' records (key, j) and their slot (node, cell of the
-// round's depth), counted per slot with one atomic per slot and warp
+// round's depth), counted per slot with one atomic per slot and warp, and the
+// smallest index of every slot (the splits of the round take their children's
+// minima from these)
 __global__ void k_round_copy(const OpenNode* open, const uint32_t* nopen, uint32_t cap, const uint32_t* bigstart,
                              const uint32_t* total, const uint4* __restrict__ rec, uint4* __restrict__ trec, int sh,
-                             uint32_t dmask, uint32_t* cnt)
+                             uint32_t dmask, uint32_t* cnt, uint32_t* smin)
 {
     const uint32_t nb = min(*nopen, cap), T = *total;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); p0 < T; p0 += stride) {   // warp-uniform
         const uint32_t p = p0 + lane;
-        uint32_t slot = kNone;
+        uint32_t slot = kNone, jv = kNone;
         if (p < T) {
             const uint32_t b = big_of(bigstart, nb, p);
             const uint32_t src = open[b].begin + (p - bigstart[b]);
             const uint4 r = rec[src];
             slot = (uint32_t)((rec_key(r) >> sh) & dmask) * cap + b;
+            jv = r.z;
             trec[p] = make_uint4(r.x, r.y, r.z, slot);
         }
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
-        if (slot != kNone && lane == __ffs(peers) - 1) atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
+        if (slot != kNone) {   // every lane of a slot's group takes part in its reduction
+            const uint32_t m = __reduce_min_sync(peers, jv);
+            if (lane == __ffs(peers) - 1) {
+                atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
+                atomicMin(&smin[slot], m);
+            }
+        }
     }
 }
 
@@ -372,13 +387,14 @@ __global__ void k_round_scatter(const uint32_t* total, const uint4* __restrict__
 // key-sorted records, smallest index of every child, hierarchy status, first-min
 // level; children that are still too large stay open, the others become pieces.
 __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, OpenNode* nxt, uint32_t* nnxt,
-                        uint32_t open_cap, int srt)
+                        uint32_t open_cap, int srt, const uint32_t* smin, int q0)
 {
     const uint32_t nc = *ncur;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = warp; w < nc; w += nwarps) {
         const OpenNode o = cur[w];
+        const uint32_t rb = o.q == q0 ? w : o.rb;   // slot column of the round (q0: the round's first level)
         const int q1 = o.q + 1;
         const int sh = 3 * (kKeyLevels - q1);
         // lane d (0..8): first record whose child digit is >= d
@@ -392,21 +408,19 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
             }
             lo = a;
         }
-        // smallest index of every child, and of the node (the smallest of those)
+        // smallest index of every child, and of the node (the smallest of those):
+        // from the round's per-slot minima -- child d covers the slots whose
+        // digits below q0 start with the node's digits below q0, then d
+        // (8^(srt - q1) of them)
         uint32_t mjd[8];
         uint32_t pmin = 0xFFFFFFFFu;
+        const int span = 3 * (srt - q1);
+        const uint32_t pre = (uint32_t)(o.key & ((1ull << (3 * (o.q - q0))) - 1));
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-            const uint32_t cb = __shfl_sync(0xFFFFFFFFu, lo, d);
-            const uint32_t ce = __shfl_sync(0xFFFFFFFFu, lo, d + 1);
+            const uint32_t d0 = ((pre << 3) | (uint32_t)d) << span;
             uint32_t mj = 0xFFFFFFFFu;
-            uint32_t r = cb + lane;
-            for (; r + 96 < ce; r += 128) {   // four independent loads in flight per lane
-                const uint32_t v0 = rec_j_at(c.rec, r), v1 = rec_j_at(c.rec, r + 32), v2 = rec_j_at(c.rec, r + 64),
-                               v3 = rec_j_at(c.rec, r + 96);
-                mj = min(mj, min(min(v0, v1), min(v2, v3)));
-            }
-            for (; r < ce; r += 32) mj = min(mj, rec_j_at(c.rec, r));
+            for (uint32_t t = lane; t < (1u << span); t += 32) mj = min(mj, smin[(uint64_t)(d0 + t) * open_cap + rb]);
             for (int off = 16; off > 0; off >>= 1) mj = min(mj, __shfl_xor_sync(0xFFFFFFFFu, mj, off));
             mjd[d] = mj;
             pmin = min(pmin, mj);
@@ -440,6 +454,8 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
                     ch.hier = hier;
                     ch.A = A;
                     ch.pad = 0;
+                    ch.rb = rb;
+                    ch.pad2 = ch.pad3 = 0;
                     nxt[id] = ch;
                 } else {
                     emit_piece(c, cb, cn, q1, hier, A, srt);
@@ -1308,6 +1324,7 @@ uint64_t node_capacity_bound(uint64_t n, const fp_params& p) { return oct_layout
 struct OctBufs {
     SortScratch sc;
     uint32_t* rcnt;        // counting slots of a split round: 8^3 per open node
+    uint32_t* rmin;        // the smallest index of every slot
     uint4* trec;   // split rounds: the copied records with their slots
     int4* lt_pt;
     uint32_t *lt_val, *lt_k32;
@@ -1342,6 +1359,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     const uint64_t N = n ? n : 1;
     B.sc = take_sort_scratch(ws, std::max<uint64_t>(N, std::max(Ly.node_cap, Ly.piece_cap)));
     B.rcnt = ws.take<uint32_t>(Ly.open_cap << (3 * kRoundLevels));
+    B.rmin = ws.take<uint32_t>(Ly.open_cap << (3 * kRoundLevels));
     // aliased phase region: grouping temporaries, later the leaf scatter temporaries
     const size_t phase_base = ws.used;
     B.trec = ws.take<uint4>(N);
@@ -1532,15 +1550,15 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
             if ((e = scan_exclusive<uint32_t, uint32_t>(B.bigstart, B.bigstart, cap, nullptr, B.leafw, B.ocount + 3,
                                                         (uint32_t*)nullptr, st)))
                 return e;
-            k_round_zero<<<gr, 256, 0, st>>>(B.ocount + cur, cap, nd, B.rcnt);
+            k_round_zero<<<gr, 256, 0, st>>>(B.ocount + cur, cap, nd, B.rcnt, B.rmin);
             k_round_copy<<<gr, 256, 0, st>>>(B.open[cur], B.ocount + cur, cap, B.bigstart, B.ocount + 3, B.rec,
-                                             B.trec, 3 * (kKeyLevels - q - k), (uint32_t)(nd - 1), B.rcnt);
+                                             B.trec, 3 * (kKeyLevels - q - k), (uint32_t)(nd - 1), B.rcnt, B.rmin);
             k_round_bases<<<gw, 256, 0, st>>>(B.open[cur], B.ocount + cur, cap, nd, B.rcnt);
             k_round_scatter<<<gr, 256, 0, st>>>(B.ocount + 3, B.trec, B.rcnt, B.rec, N, ws.err);
             for (int l = q; l < q + k; ++l) {
                 k_set_u32<<<1, 1, 0, st>>>(B.ocount + (1 - cur), 0);
                 k_split<<<gw, 256, 0, st>>>(c, B.open[cur], B.ocount + cur, B.open[1 - cur], B.ocount + (1 - cur),
-                                            cap, q + k);
+                                            cap, q + k, B.rmin, q);
                 cur = 1 - cur;
             }
             q += k;
