@@ -62,6 +62,17 @@ def incore_need(n, prm):
             16 * fp._preview_cap(n, prm.decim_modulus) + (64 << 20))
 
 
+def pick_request(queue, free, ooc_slot_free, big_points, big_active):
+    """The request the loop admits next, or None.  A request fits when its device
+    need fits in the free budget and, out of core, a host slot is free, or, in
+    core, it is smaller than big_points or no other such build is running.  Of
+    those, a waiting out-of-core request goes first (long and bound by the host
+    link, so in-core builds overlap it), else the first in arrival order."""
+    fits = [r for r in queue if r.need <= free and
+            (ooc_slot_free if r.mode == "out-of-core" else (r.n < big_points or big_active == 0))]
+    return next((r for r in fits if r.mode == "out-of-core"), fits[0] if fits else None)
+
+
 def _preview_slot_cap(p, m):
     return fp._preview_cap(p, m)
 
@@ -113,12 +124,8 @@ class Server:
                 while True:
                     if self._stop and not self.queue:
                         return
-                    fits = [r for r in self.queue if r.need <= self.free and
-                            (self.ooc_free if r.mode == "out-of-core" else
-                             (r.n < self.big_points or self.big_active == 0))]
-                    # an out-of-core build is long and bound by the host link: start it
-                    # first, then fill the rest of the budget with in-core requests
-                    pick = next((r for r in fits if r.mode == "out-of-core"), fits[0] if fits else None)
+                    pick = pick_request(self.queue, self.free, bool(self.ooc_free), self.big_points,
+                                        self.big_active)
                     if pick is not None:
                         break
                     self.cv.wait()

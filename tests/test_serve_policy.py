@@ -1,0 +1,46 @@
+"""Admission policy of the served loop (host logic, no GPU): which waiting request
+starts next under a device budget, one out-of-core slot and one large in-core build
+at a time."""
+import types
+
+from paper_2302_05002_gb300.serve import pick_request
+
+
+def req(name, need, mode="in-core", n=1_000_000):
+    return types.SimpleNamespace(name=name, need=need, mode=mode, n=n)
+
+
+BIG = 1 << 24
+
+
+def pick(queue, free=100, ooc=True, big_active=0):
+    r = pick_request(queue, free, ooc, BIG, big_active)
+    return None if r is None else r.name
+
+
+def test_first_fit_in_arrival_order():
+    q = [req("a", 150), req("b", 60), req("c", 10)]
+    assert pick(q) == "b"                      # a does not fit, b is the first that does
+
+
+def test_nothing_fits():
+    assert pick([req("a", 150), req("b", 101)]) is None
+    assert pick([]) is None
+
+
+def test_out_of_core_goes_first_when_a_slot_is_free():
+    q = [req("a", 10), req("o", 50, "out-of-core"), req("b", 10)]
+    assert pick(q) == "o"
+    assert pick(q, ooc=False) == "a"            # no host slot: the in-core requests go on
+    assert pick(q, free=40) == "a"              # the arena does not fit: same
+
+
+def test_one_large_in_core_build_at_a_time():
+    q = [req("big", 10, n=BIG), req("small", 10, n=BIG - 1)]
+    assert pick(q) == "big"
+    assert pick(q, big_active=1) == "small"     # a large one runs: only smaller ones start
+    assert pick([req("big", 10, n=2 * BIG)], big_active=1) is None
+
+
+def test_budget_is_inclusive():
+    assert pick([req("a", 100)]) == "a"
