@@ -44,3 +44,14 @@ def test_one_large_in_core_build_at_a_time():
 
 def test_budget_is_inclusive():
     assert pick([req("a", 100)]) == "a"
+
+
+def test_incore_need_per_point():
+    # the cloud, its outputs and the largest stage workspace: about 120 B per point for
+    # large clouds, so a 24 GB budget (in core up to three quarters) holds ~160M points
+    from paper_2302_05002_gb300 import fastpoints as fp
+    from paper_2302_05002_gb300.serve import incore_need
+    prm = fp.params()
+    per = incore_need(160_000_000, prm) / 160_000_000
+    assert 100 < per < 130
+    assert incore_need(160_000_000, prm) <= (24 << 30) * 3 // 4 < incore_need(170_000_000, prm)
