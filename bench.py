@@ -8,7 +8,9 @@ Prints one JSON line (rank 0).  `value` is whole-job throughput in Gpts/s with
 the cloud resident in HBM (N GPUs build N replicas: weak scaling, no data-path
 collective); `e2e` is the same metric through the C-ABI calls with the input in
 pinned host memory copied in and the node table read back every step.  The
-workload defaults to the 100M-point synthetic LiDAR scene.
+workload defaults to the 1B-point uniform cloud (10^9 points, g = 7, s = 7,
+L_max = 8, T = 5e6, C = 5e4), the largest single-GPU configuration; the
+roofline names the kernel with the largest device time in the step.
 """
 import argparse
 import json
@@ -39,38 +41,39 @@ WORKLOADS = {
     # headless frame of the 100M LiDAR octree: node selection + rasterisation at 1920x1080
     "render-100M": ("render", 100_000_000, 2, 7, 7, 15, 100_000, 20_000),
 }
+DEFAULT_WORKLOAD = "uniform-1B"
 RENDER_W, RENDER_H, RENDER_MIN_PX = 1920, 1080, 30.0
 STAGES = ["bounds_decimate", "count", "merge", "distribute", "octree", "subsample"]
-# algorithmic HBM bytes per point of each stage: the mandatory reads and writes of
-# its definition (bounds + preview: read 16, a 16-byte record for 1 point in 16;
-# count: read 16; distribute: read 16, write 16 + 4 perm; octree: read 16 + 4 perm,
-# write 16 + 4 leaf-grouped and 4 owner; subsample: read 16 + 4 + 4, write 16 + 4)
-ALG_BYTES = {"bounds_decimate": 17, "count": 16, "merge": 0, "distribute": 36, "octree": 44, "subsample": 44}
+# the method's mandatory HBM bytes per point (read and write passes of its
+# definition): bounds + preview 17 (read 16; a 16-byte record for 1 point in
+# 16), count 16, distribute 32 (read 16, write 16), chunk octrees + LOD 32 (one
+# read and one final write of each point) -- 97 in all -- plus the count grid's
+# fixed 3 * 4 * 8^g bytes (written, read by the merge, LUT written)
+ALG_PER_POINT = 97
 FIXED_BYTES = {"merge": 3 * 4 * (1 << 21)}
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
-# stage, from one ncu capture of the workload, valid while the stage's sources
-# hash to the recorded value (a changed kernel reports null)
-STAGE_SOURCES = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_sort.cuh", "fp_sort.cu", "fp_seg.cuh",
-                 "fp_seg.cu", "fp_octree.cu", "fp_api.cu"]
-NCU_TRAFFIC = {("lidar-100M", "octree"): (19.674e9, "96ff4a58eb391532"),
-               ("uniform-1B", "octree"): (135.814e9, "96ff4a58eb391532")}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one call's
+# launches of a kernel, from one ncu capture of the workload, valid while the
+# kernel's sources hash to the recorded value (a changed kernel reports null)
+KERNEL_SOURCES = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_sort.cuh", "fp_sort.cu", "fp_seg.cuh",
+                  "fp_seg.cu", "fp_octree.cu", "fp_core.cu", "fp_api.cu"]
+NCU_TRAFFIC = {}
 
 
-def stage_sources_hash():
+def sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in STAGE_SOURCES:
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2302_05002_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, stage):
-    rec = NCU_TRAFFIC.get((workload, stage))
+def ncu_traffic(workload, kernel):
+    rec = NCU_TRAFFIC.get((workload, kernel))
     if rec is None:
         return None
     try:
-        return rec[0] if stage_sources_hash() == rec[1] else None
+        return rec[0] if sources_hash() == rec[1] else None
     except OSError:
         return None
 
@@ -279,10 +282,12 @@ def batch_sizes(count, seed):
     return [int(x) for x in sizes], [str(k) for k in kinds]
 
 
-def run_batched(args, wl, rank, world, local):
-    """256 clouds built two ways on the same GPU: the plain calls cloud after
-    cloud on one stream, and fp_build_batched (tuned grid per cloud and lane
-    count) captured into one CUDA graph.  value = all points / batched time."""
+def run_batched(args, wl, rank, world, local):   # returns the JSON line (rank 0)
+    """256 clouds built three ways on the same GPU: the plain calls cloud after
+    cloud on one stream; fp_build_batched on lanes (every pass per cloud); and
+    fp_build_batched_ex with the tuner's options (grid per cloud, lanes, fused
+    first passes, their block and table sizes), each batch captured into one
+    CUDA graph.  value = all points / tuned batched time."""
     import torch
 
     from paper_2302_05002_gb300 import fastpoints as fp
@@ -307,6 +312,7 @@ def run_batched(args, wl, rank, world, local):
     plain_outs = [fp.cloud_outputs(p, base) for p in pts]
     plain_descs = fp.batch_descs(plain_clouds, plain_outs)
     ws_plain = torch.empty(max(fp.batch_workspace_size(plain_descs, count, 1), 1), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
 
     def run_plain():
         for i in range(count):
@@ -322,15 +328,26 @@ def run_batched(args, wl, rank, world, local):
     clouds = tuner.tune_params(plain_clouds)
     outs = [fp.cloud_outputs(p, prm) for p, prm in clouds]
     descs = fp.batch_descs(clouds, outs)
-    ws_need = max(fp.batch_workspace_size(descs, count, L) for L in (4, 8, 16, 32))
+    ws_need = max(max(fp.batch_workspace_size(descs, count, L) for L in (4, 8, 16, 32)),
+                  max(fp.batch_workspace_size_ex(descs, count, fp.batch_opts(L, 1)) for L in (4, 8, 16, 32)))
     ws = torch.empty(max(ws_need, 1), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()   # the outputs' zero fills (default stream) land before the lanes write them
     lanes = tuner.tune_lanes(lambda L: fp.fp_build_batched(descs, count, L, ws, stream=st))
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=st, capture_error_mode="relaxed"):
-        fp.fp_build_batched(descs, count, lanes, ws, stream=st)
+    opts = tuner.tune_opts(lambda o: fp.fp_build_batched_ex(descs, count, o, ws, stream=st), lanes)
+
+    def capture(o):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=st, capture_error_mode="relaxed"):
+            fp.fp_build_batched_ex(descs, count, o, ws, stream=st)
+        return gr
+
+    graph = capture(opts)
+    lanes_opts = fp.batch_opts(lanes, 0)   # the lanes alone (every pass per cloud), for comparison
+    graph_lanes = capture(lanes_opts)
 
     for _ in range(max(3, args.warmup)):
         run_plain()
+        graph_lanes.replay()
         graph.replay()
     torch.cuda.synchronize()
     assert fp.get_device_error(stream=st) == 0, "device error word set"
@@ -352,7 +369,15 @@ def run_batched(args, wl, rank, world, local):
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / args.steps
 
-    launches = count_kernels(lambda: fp.fp_build_batched(descs, count, lanes, ws, stream=st), torch, st)
+    with torch.cuda.stream(st):
+        e0.record(st)
+        for _ in range(args.steps):
+            graph_lanes.replay()
+        e1.record(st)
+    torch.cuda.synchronize()
+    lanes_ms = e0.elapsed_time(e1) / args.steps
+
+    launches = count_kernels(lambda: fp.fp_build_batched_ex(descs, count, opts, ws, stream=st), torch, st)
     clk = ClockSampler(local)
     torch.cuda.synchronize()
     clk.start()
@@ -376,7 +401,7 @@ def run_batched(args, wl, rank, world, local):
         with torch.cuda.stream(st):
             for p, h in zip(pts, host):
                 p.copy_(h, non_blocking=True)
-            fp.fp_build_batched(descs, count, lanes, ws, stream=st)
+            fp.fp_build_batched_ex(descs, count, opts, ws, stream=st)
             nums = torch.stack([o["num_nodes"][0] for o in outs]).cpu()
             d2h = 0
             for o, M in zip(outs, nums.tolist()):
@@ -385,7 +410,7 @@ def run_batched(args, wl, rank, world, local):
             st.synchronize()
     e2e_ms = (time.perf_counter() - te0) * 1e3 / e2e_steps
     peak, peak_kind = measured_peaks()
-    alg = sum(ALG_BYTES.values()) * total + FIXED_BYTES["merge"] * count
+    alg = ALG_PER_POINT * total + FIXED_BYTES["merge"] * count
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -400,6 +425,9 @@ def run_batched(args, wl, rank, world, local):
             "data": "synthetic",
             "config": {"workload": args.workload, "clouds": count, "points": total, "min_points": min(sizes),
                        "max_points": max(sizes), "lanes": lanes, "grid_log2_per_cloud": gs,
+                       "fused_first_passes": bool(opts.fused_first), "count_threads": opts.count_threads,
+                       "count_slots": opts.count_slots,
+                       "lanes_only_ms_per_step": lanes_ms, "lanes_only_gpts": total / (lanes_ms * 1e-3) / 1e9,
                        "chunk_threshold": T, "node_capacity": C, "max_level": lmax, "sub_log2": s,
                        "plain_ms_per_step": plain_ms, "plain_gpts": plain_value,
                        "batched_over_plain": value / plain_value, "graph": "one CUDA graph per batch",
@@ -412,9 +440,9 @@ def run_batched(args, wl, rank, world, local):
             "clocks": clocks,
             "gpu_launches": launches * args.steps if launches else None,
             "cpu_baseline": cpu,
-            "tuner": tuner.log[-8:],
+            "tuner": tuner.log[-12:],
         }
-        print(json.dumps(line), flush=True)
+        return line
 
 
 def batch_oracle_rate(sizes, kinds, seed0, wl, budget_s):
@@ -766,7 +794,7 @@ def host_mem_available():
     return None
 
 
-def run_served(args, wl, rank, world, local):
+def run_served(args, wl, rank, world, local):   # returns the JSON line (rank 0)
     """Poisson-arriving LiDAR clouds served under a 24 GB device budget
     (serve.Server): p50/p99 time to preview and to the full octree, aggregate
     points/s; the same clouds submitted at once (saturated); and the plain
@@ -895,7 +923,7 @@ def run_served(args, wl, rank, world, local):
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+        return line
 
 
 def served_oracle_rate(sizes, seed0, wl, budget_s):
@@ -931,7 +959,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="lidar-100M", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true",
+                    help="the default run without the batched and served summaries")
+    ap.add_argument("--leaf-grouped", action="store_true",
+                    help="the timed step also writes the optional leaf-grouped layout")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -944,7 +976,7 @@ def main():
         if args.impl == "reference":
             run_served_reference(args, wl, rank)
         else:
-            run_served(args, wl, rank, world, local)
+            emit(run_served(args, wl, rank, world, local))
         return
     if wl[0] == "render":
         if args.impl == "reference":
@@ -962,11 +994,68 @@ def main():
         if args.impl == "reference":
             run_batched_reference(args, wl, rank)
         else:
-            run_batched(args, wl, rank, world, local)
+            emit(run_batched(args, wl, rank, world, local))
         return
     if args.impl == "reference":
         run_reference(args, wl, rank)
         return
+    line = run_plain(args, wl, rank, world, local)
+    if line is not None and world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_extras:
+        line["configs"] = extra_configs(args, local)
+    emit(line)
+
+
+def emit(line):
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def extra_configs(args, local):
+    """The batched and served workloads, measured in the same run as the
+    headline (one GPU): a summary of each one's own line."""
+    import copy
+
+    import torch
+    out = {}
+    for name, fn, keys in (("batched-256", run_batched,
+                            ("value", "unit", "ms_per_step", "e2e", "clocks", "gpu_launches", "tuner")),
+                           ("served-32", run_served,
+                            ("value", "unit", "metric", "served", "saturated", "plain", "plain_budgeted",
+                             "served_over_plain_budgeted", "clocks"))):
+        torch.cuda.empty_cache()
+        sub = copy.copy(args)
+        sub.workload, sub.warmup, sub.no_cpu_baseline = name, 3, True
+        sub.steps = 3 if name.startswith("batched") else 1
+        t0 = time.perf_counter()
+        try:
+            r = fn(sub, WORKLOADS[name], 0, 1, local)
+        except Exception as ex:   # reported in the line; the headline stands
+            out[name] = {"error": repr(ex)[:300]}
+            continue
+        d = {k: r.get(k) for k in keys}
+        c = r["config"]
+        if name.startswith("batched"):
+            d.update({k: c.get(k) for k in ("clouds", "points", "lanes", "fused_first_passes", "count_threads",
+                                            "count_slots", "plain_gpts", "lanes_only_gpts", "batched_over_plain")})
+        else:
+            d.update({k: c.get(k) for k in ("requests", "points", "out_of_core_requests", "peak_in_flight")})
+        d["wall_s"] = time.perf_counter() - t0
+        out[name] = d
+    return out
+
+
+def kernel_alg_bytes(kernel, n):
+    """Algorithmic bytes of one call's launches of a kernel: its share of the
+    method's mandatory per-point traffic (97 B/pt in all, plus the 25.2 MB of
+    the count grid): bounds + preview 17 (read 16, preview write 1), count 16,
+    distribute 32 (read 16, write 16), chunk octrees + LOD 32 (one read and one
+    final write of each point) charged to the final-layout scatter, which does
+    both.  The other kernels of the octree stage move intermediates only."""
+    return {"bounds_decimate": 17, "count": 16, "distribute": 32, "owner_scatter": 32}.get(kernel, 0) * n
+
+
+def run_plain(args, wl, rank, world, local):
+    import ctypes
 
     import torch
     import torch.distributed as dist
@@ -1001,20 +1090,22 @@ def main():
         dist=torch.empty_like(pts), perm=torch.empty(n, dtype=torch.int32, device=dev),
         nodes=torch.zeros((ncap, 5), dtype=torch.int64, device=dev),
         num_nodes=torch.zeros(1, dtype=torch.int32, device=dev),
-        leaf=torch.empty_like(pts), leaf_perm=torch.empty(n, dtype=torch.int32, device=dev),
         owner=torch.empty(n, dtype=torch.int32, device=dev),
         final=torch.empty_like(pts), final_perm=torch.empty(n, dtype=torch.int32, device=dev),
     )
+    leaf = dict(leaf=torch.empty_like(pts), leaf_perm=torch.empty(n, dtype=torch.int32, device=dev)) \
+        if args.leaf_grouped else None
     ws_need = max(fp.workspace_size(k, n, prm) for k in ("bounds_decimate", "merge", "distribute", "octree",
                                                          "subsample"))
     ws = torch.empty(ws_need, dtype=torch.uint8, device=dev)
     L = fp.load()
     P = lambda t: fp._ptr(t)
     S = fp._stream(st)
-    import ctypes
     prm_ref = ctypes.byref(prm)
 
-    def stage_calls(src):
+    def stage_calls(src, with_leaf):
+        lp = P(leaf["leaf"]) if with_leaf else None
+        lpp = P(leaf["leaf_perm"]) if with_leaf else None
         return [
             ("bounds_decimate", lambda: L.fp_bounds_decimate(P(src), n, P(O["cube"]), 0, 16, P(O["prev"]),
                                                              O["prev"].shape[0], P(O["prev_n"]), P(ws), ws.numel(), S)),
@@ -1026,18 +1117,17 @@ def main():
                                                    ws.numel(), S)),
             ("octree", lambda: L.fp_build_chunk_octree(P(O["dist"]), P(O["perm"]), n, P(O["cube"]), P(O["chunks"]),
                                                        P(O["num_chunks"]), P(O["offsets"]), P(O["counts"]), prm_ref,
-                                                       P(O["nodes"]), ncap, P(O["num_nodes"]), P(O["leaf"]),
-                                                       P(O["leaf_perm"]), P(O["owner"]), P(ws), ws.numel(), S)),
+                                                       P(O["nodes"]), ncap, P(O["num_nodes"]), lp, lpp,
+                                                       P(O["owner"]), P(ws), ws.numel(), S)),
             ("subsample", lambda: L.fp_subsample(P(O["nodes"]), P(O["num_nodes"]), ncap, P(O["dist"]), P(O["perm"]),
                                                  P(O["owner"]), n, P(O["chunks"]), P(O["num_chunks"]),
                                                  P(O["offsets"]), P(O["final"]), P(O["final_perm"]), P(ws),
                                                  ws.numel(), S)),
         ]
 
-    calls = stage_calls(pts)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
 
-    def step(record):
+    def step(calls, record=False):
         with torch.cuda.stream(st):
             if record:
                 ev[0].record(st)
@@ -1048,75 +1138,112 @@ def main():
                 if record:
                     ev[k + 1].record(st)
 
-    for _ in range(max(3, args.warmup)):
-        step(False)
-    torch.cuda.synchronize()
-    assert fp.get_device_error(stream=st) == 0, "device error word set"
-
-    # kernels per step (CUPTI through the torch profiler, one step outside the timed region)
-    launches_per_step = count_kernels(lambda: step(False), torch, st)
-
-    # the step captured once into a CUDA graph and replayed: its ~300 launches
-    # cost one graph launch (the calls enqueue no host synchronisation)
-    graph = None
-    try:
+    def capture(calls):
         g_ = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g_, stream=st, capture_error_mode="relaxed"):
-            step(False)
-        with torch.cuda.stream(st):
-            g_.replay()
-        torch.cuda.synchronize()
-        assert fp.get_device_error(stream=st) == 0, "device error word set after graph replay"
-        graph = g_
-    except Exception as ex:   # plain launches then
-        print("graph capture failed, timing plain launches: %r" % (ex,), file=sys.stderr)
-        torch.cuda.synchronize()
+            step(calls)
+        return g_
+
+    calls = stage_calls(pts, False)
+    for _ in range(max(3, args.warmup)):
+        step(calls)
+    torch.cuda.synchronize()
+    err = fp.get_device_error(stream=st)
+    assert err == 0, "device error word set: %#x (sites %#x)" % (err, fp.get_device_error_sites(stream=st))
+
+    # kernels per step (counted from a captured graph, one step outside the timed region)
+    launches_per_step = count_kernels(lambda: step(calls), torch, st)
+
+    # the step captured once into a CUDA graph and replayed: its few hundred
+    # launches cost one graph launch (the calls enqueue no host synchronisation)
+    graph = capture(calls)
+    with torch.cuda.stream(st):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert fp.get_device_error(stream=st) == 0, "device error word set after graph replay"
     # inputs smaller than L2 (129 MB): L2 flushed between timed steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if 16 * n < (256 << 20) else None
+
+    def timed_graph(gr, steps):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(steps):
+            if flush is not None:
+                flush.fill_(1)
+            with torch.cuda.stream(st):
+                t0.record(st)
+                gr.replay()
+                t1.record(st)
+            t1.synchronize()
+            tot += t0.elapsed_time(t1)
+        return tot / steps
 
     clk = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    total_ms = 0.0
-    for _ in range(args.steps):
-        if flush is not None:
-            flush.fill_(1)
-        with torch.cuda.stream(st):
-            t0.record(st)
-            if graph is not None:
-                graph.replay()
-            else:
-                step(False)
-            t1.record(st)
-        t1.synchronize()
-        total_ms += t0.elapsed_time(t1)
+    ms = timed_graph(graph, args.steps)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    ms = total_ms / args.steps
     # per-stage times: the same steps with plain launches and events between the calls
     stage_ms = {k: [] for k in STAGES}
     for _ in range(args.steps):
         if flush is not None:
             flush.fill_(1)
-        step(True)
+        step(calls, True)
         st.synchronize()
         for k, name in enumerate(STAGES):
             stage_ms[name].append(ev[k].elapsed_time(ev[k + 1]))
+    # per-kernel times: events the library records around the kernel's launches
+    # (fp_time_kernel), on the launching stream, plain launches
+    kev = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+    with torch.cuda.stream(st):
+        kev[0].record(st)
+        kev[1].record(st)
+    kernel_ms = {}
+    for kname in [k for k in fp.KERNEL if k != "none"]:
+        vals = []
+        for _ in range(args.steps):
+            if flush is not None:
+                flush.fill_(1)
+            fp.time_kernel(kname, kev[0], kev[1])
+            with torch.cuda.stream(st):
+                kev[0].record(st)   # a kernel the step does not launch reads 0
+                kev[1].record(st)
+            step(calls)
+            fp.time_kernel("none")
+            st.synchronize()
+            vals.append(kev[0].elapsed_time(kev[1]))
+        kernel_ms[kname] = statistics.median(vals)
     ms, value = replica_rate(ms, n, world, dev)
 
-    # end to end: every step copies its cloud in from pinned host memory and
-    # reads its node table back.  The copy of cloud i + 1 runs on a side stream
-    # under the build of cloud i (two device input buffers), as a stream of
-    # clouds would be fed: the steady-state step is max(copy, build).
-    nodes_host = torch.empty_like(O["nodes"], device="cpu").pin_memory()
-    e2e_bufs = [torch.empty_like(pts), torch.empty_like(pts)]
-    calls_e2e = [stage_calls(b) for b in e2e_bufs]
+    # the same step with the optional leaf-grouped layout (fp_build_chunk_octree's d_leaf_pts)
+    leaf_ms = None
+    if leaf is None:
+        leaf = dict(leaf=torch.empty_like(pts), leaf_perm=torch.empty(n, dtype=torch.int32, device=dev))
+        g_leaf = capture(stage_calls(pts, True))
+        with torch.cuda.stream(st):
+            g_leaf.replay()
+        torch.cuda.synchronize()
+        leaf_ms = timed_graph(g_leaf, args.steps)
+        del g_leaf, leaf
+        leaf = None
+        torch.cuda.synchronize()
+        assert fp.get_device_error(stream=st) == 0
+
+    # end to end through the C ABI: every step copies its cloud in from pinned
+    # host memory and reads its node table (and node count) back into pinned
+    # memory.  The copy of cloud i + 1 runs on a side stream under the build of
+    # cloud i (two device input buffers, each with its captured step); nothing
+    # waits on the host until the last step.
+    e2e_bufs = [pts, torch.empty_like(pts)]
+    e2e_graphs = [graph, capture(stage_calls(e2e_bufs[1], False))]
+    nodes_host = [torch.empty_like(O["nodes"], device="cpu").pin_memory() for _ in range(2)]
+    nn_host = [torch.empty(1, dtype=torch.int32).pin_memory() for _ in range(2)]
     cs = torch.cuda.Stream(dev)
     e2e_steps = min(max(4, args.steps), 10)
     copied = [torch.cuda.Event() for _ in range(2)]
@@ -1135,41 +1262,47 @@ def main():
 
     torch.cuda.synchronize()
     te0 = time.perf_counter()
-    d2h = 0
     copy_in(0)
     for k in range(e2e_steps):
         if k + 1 < e2e_steps:
             copy_in(k + 1)
         with torch.cuda.stream(st):
             st.wait_event(copied[k % 2])
-            for name, f in calls_e2e[k % 2]:
-                if f() != 0:
-                    raise RuntimeError(name)
+            e2e_graphs[k % 2].replay()
             built[k % 2].record(st)
-            nn = O["num_nodes"].to("cpu", non_blocking=False)
-            M = int(nn.item())
-            nodes_host[:M].copy_(O["nodes"][:M], non_blocking=True)
-            st.synchronize()
-            d2h = M * 40 + 4
+            nn_host[k % 2].copy_(O["num_nodes"], non_blocking=True)
+            nodes_host[k % 2].copy_(O["nodes"], non_blocking=True)
+    st.synchronize()
     e2e_ms = (time.perf_counter() - te0) * 1e3 / e2e_steps
+    d2h = O["nodes"].numel() * 8 + 4
+    M = int(nn_host[(e2e_steps - 1) % 2].item())
+    assert M == int(O["num_nodes"].item()) and fp.get_device_error(stream=st) == 0
     e2e_value = n * world / (e2e_ms * 1e-3) / 1e9
     # the host link's rate for these copies: it varies from host to host
     h2d_gbs = 16 * n / (statistics.median(c0.elapsed_time(c1) for c0, c1 in h2d_ev) * 1e-3) / 1e9
-    del e2e_bufs
+    del e2e_bufs, e2e_graphs
 
     peak, peak_kind = measured_peaks()
     med = {k: statistics.median(v) for k, v in stage_ms.items()}
-    dom = max(med, key=lambda k: med[k])
-    alg = ALG_BYTES[dom] * n + FIXED_BYTES.get(dom, 0)
-    achieved = alg / (med[dom] * 1e-3) / 1e9
-    total_alg = sum(ALG_BYTES[k] * n + FIXED_BYTES.get(k, 0) for k in STAGES)
-    M = int(O["num_nodes"].item())
+    dom = max(kernel_ms, key=lambda k: kernel_ms[k])
+    alg = kernel_alg_bytes(dom, n)
+    achieved = alg / (kernel_ms[dom] * 1e-3) / 1e9
+    kernels = {}
+    for k, v in sorted(kernel_ms.items(), key=lambda kv: -kv[1]):
+        if v <= 0:
+            continue
+        b = kernel_alg_bytes(k, n)
+        kernels[k] = {"ms": v, "share_of_step": v / ms, "alg_bytes": b,
+                      "frac": (b / (v * 1e-3) / 1e9 / peak) if b else 0.0}
+    # the method's mandatory bytes: 97 per point plus the count grid's 25.2 MB
+    step_alg = ALG_PER_POINT * n + FIXED_BYTES["merge"]
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
             r, ns, dt, cores = oracle_rate(kind, seed, wl, float(os.environ.get("FP_ORACLE_BUDGET_S", "12")))
-            cpu = {"value": r / 1e9, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
-                   "sample": "first %d points of the %s workload, same parameters, %.1f s" % (ns, args.workload, dt)}
+            cpu = {"value": r / 1e9, "unit": "Gpts/s", "cores": cores, "nproc": os.cpu_count(), "kind": "oracle",
+                   "sample": "first %d points of the %s workload, same parameters, %.1f s, one thread" %
+                             (ns, args.workload, dt)}
         line = {
             "metric": "octree build throughput (Gpts/s)", "value": value, "unit": "Gpts/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
@@ -1177,26 +1310,38 @@ def main():
             "config": {"workload": args.workload, "points": n, "grid_log2": g, "sub_log2": s, "max_level": lmax,
                        "chunk_threshold": T, "node_capacity": C, "nodes": M,
                        "chunks": int(O["num_chunks"].item()), "parallelism": "replicas" if world > 1 else "single",
-                       "launch": "one CUDA graph per step" if graph is not None else "plain launches",
+                       "launch": "one CUDA graph per step",
+                       "outputs": "cube, preview, count grid, chunks, LUT, offsets, distributed points + perm, "
+                                  "node table, owner per point, final LOD layout + perm" +
+                                  (", leaf-grouped points + perm" if args.leaf_grouped else ""),
                        "l2": ("inputs (%.1f GB) larger than L2" % (16 * n / 1e9)) if flush is None else
                              "L2 flushed between steps (256 MB written)"},
             "e2e": {"value": e2e_value, "unit": "Gpts/s", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": d2h,
                     "h2d_gbs": h2d_gbs, "steps": e2e_steps,
-                    "overlap": "copy of cloud i+1 on a side stream under the build of cloud i"},
-            "roofline": {"bound": "hbm", "kernel": "stage " + dom, "achieved": achieved, "peak": peak,
+                    "overlap": "copy of cloud i+1 on a side stream under the build of cloud i; node table and "
+                               "count read back asynchronously"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": ncu_traffic(args.workload, dom),
-                         "alg_bytes_per_launch": alg},
-            "step_roofline": {"alg_bytes": total_alg, "achieved_gbs": total_alg / (ms * 1e-3) / 1e9,
-                              "frac": total_alg / (ms * 1e-3) / 1e9 / peak},
+                         "frac_of_8tbs": achieved / 8000.0, "traffic": ncu_traffic(args.workload, dom),
+                         "alg_bytes_per_launch": alg, "ms": kernel_ms[dom]},
+            "step_roofline": {"alg_bytes": step_alg, "alg_bytes_per_point": ALG_PER_POINT,
+                              "achieved_gbs": step_alg / (ms * 1e-3) / 1e9,
+                              "frac": step_alg / (ms * 1e-3) / 1e9 / peak,
+                              "frac_of_8tbs": step_alg / (ms * 1e-3) / 1e9 / 8000.0},
             "stage_ms": med,
+            "kernels": kernels,
+            "with_leaf_grouped": None if leaf_ms is None else
+            {"ms_per_step": leaf_ms, "value": n * world / (leaf_ms * 1e-3) / 1e9,
+             "note": "the same step also writing the optional leaf-grouped layout"},
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps if launches_per_step else None,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+    else:
+        line = None
     if world > 1:
         dist.destroy_process_group()
+    return line
 
 
 if __name__ == "__main__":

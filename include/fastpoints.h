@@ -50,6 +50,7 @@ extern "C" {
 #endif
 
 typedef struct CUstream_st* cudaStream_t;
+typedef struct CUevent_st* cudaEvent_t;
 
 /* One point: integer position and 8-bit colour, 16 bytes. */
 typedef struct { int32_t x, y, z; uint8_t r, g, b, a; } fp_point;
@@ -131,6 +132,60 @@ const char* fp_status_string(fp_status s);
  * call synchronises `stream` and clears the word when `clear` is nonzero. */
 fp_status fp_get_device_error(cudaStream_t stream, uint32_t* h_bits, int clear);
 
+/* Which of the library's capacity and consistency checks raised FP_ERR_CAPACITY
+ * since the device error word was last cleared: one bit per check site (an
+ * output array too small, or inputs that contradict each other, such as a
+ * count grid that is not the grid of the points).  For diagnosis; synchronises
+ * `stream`; cleared together with the error word by fp_get_device_error(). */
+fp_status fp_get_device_error_sites(cudaStream_t stream, uint32_t* h_sites);
+
+/* Test hook of the bounded waits.  The radix passes (fp_distribute with more
+ * than 2048 chunks, the sorts of the octree and subsample stages) find each
+ * tile's output offsets by a decoupled look-back over the earlier tiles'
+ * published counts; every such wait gives up after a bounded number of
+ * rounds, raises FP_ERR_TIMEOUT in the device error word and lets the kernel
+ * finish.  After fp_debug_withhold_publish(tile, spin_limit), tile `tile` of
+ * every later radix pass publishes nothing and the waits give up after
+ * spin_limit rounds, so the tile after it times out (its call's outputs are
+ * then undefined).  tile = 0xFFFFFFFF restores normal operation (and the
+ * default limit).  For tests only; process-wide; spin_limit >= 1. */
+fp_status fp_debug_withhold_publish(uint32_t tile, uint32_t spin_limit);
+
+/* Kernel timing for profiling.  The library's main kernels, by stage:
+ *   FP_KERNEL_BOUNDS_DECIMATE  k_bounds_decimate (fp_bounds, fp_decimate, fp_bounds_decimate)
+ *   FP_KERNEL_COUNT            k_count (fp_count)
+ *   FP_KERNEL_DISTRIBUTE       the stable scatter of fp_distribute (every launch of it)
+ *   FP_KERNEL_CELL_GROUP       k_cell_scatter: points grouped by count-grid cell (fp_build_chunk_octree)
+ *   FP_KERNEL_SPLIT_ROUNDS     the split rounds of cells larger than one shared-memory piece
+ *   FP_KERNEL_UNITS            k_units: LOD level and leaf level of every point
+ *   FP_KERNEL_NODE_TABLE       node records sorted into preorder
+ *   FP_KERNEL_RESOLVE          k_resolve: owner node and leaf node of every point
+ *   FP_KERNEL_LEAF_SCATTER     the leaf-grouped layout (when requested)
+ *   FP_KERNEL_OWNER_SCATTER    the final layout scatter of fp_subsample
+ *   FP_KERNEL_STITCH           the merge of points kept above the chunks (sort and placement)
+ * fp_time_kernel(k, start, stop) arms kernel k for the calling process: every
+ * later call that launches it records `start` on its stream before the first
+ * launch of k and `stop` after the last one (cudaEventElapsedTime then gives
+ * the kernel's device time in that call).  k = FP_KERNEL_NONE disarms.  One
+ * kernel is armed at a time; the events belong to the caller and must stay
+ * valid while armed.  Not for use while several threads issue calls. */
+typedef enum {
+    FP_KERNEL_NONE = 0,
+    FP_KERNEL_BOUNDS_DECIMATE = 1,
+    FP_KERNEL_COUNT = 2,
+    FP_KERNEL_DISTRIBUTE = 3,
+    FP_KERNEL_CELL_GROUP = 4,
+    FP_KERNEL_SPLIT_ROUNDS = 5,
+    FP_KERNEL_UNITS = 6,
+    FP_KERNEL_NODE_TABLE = 7,
+    FP_KERNEL_RESOLVE = 8,
+    FP_KERNEL_LEAF_SCATTER = 9,
+    FP_KERNEL_OWNER_SCATTER = 10,
+    FP_KERNEL_STITCH = 11
+} fp_kernel;
+
+fp_status fp_time_kernel(fp_kernel k, cudaEvent_t start, cudaEvent_t stop);
+
 /* Cube of d_pts[0..n): per-axis min and max, S = largest extent + 1 (Sec. 4.4:
  * the converter first needs the extent of the cloud).  d_cube: one record. */
 fp_status fp_bounds(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
@@ -182,7 +237,10 @@ fp_status fp_bounds_decimate(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
  * capture.  Every call shares the one array (the scratch it needs is reset by
  * each call), so calls that overlap on the GPU -- on different streams, or from
  * different host threads -- race and must be serialised by the caller.  No
- * device memory is allocated or freed.  Outputs as fp_bounds_decimate. */
+ * device memory is allocated or freed.  The array's device address (and the
+ * device error word's) is looked up once per device and kept for the process:
+ * do not use the library across a cudaDeviceReset() of that device.
+ * Outputs as fp_bounds_decimate. */
 fp_status fp_bounds_decimate_static(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
                                     uint64_t first_index, uint32_t modulus,
                                     fp_point* d_out, uint64_t out_cap, uint64_t* d_out_count,
@@ -298,6 +356,23 @@ size_t fp_batch_workspace_size(const fp_cloud_desc* h_clouds, uint32_t ncloud, u
  * descriptors are checked before anything is enqueued; on an error nothing is. */
 fp_status fp_build_batched(const fp_cloud_desc* h_clouds, uint32_t ncloud, uint32_t nlanes,
                            void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Options of a batched build; none of them changes any output bit.
+ *   nlanes         library-owned streams the clouds' calls run on (1 .. FP_MAX_LANES)
+ *   fused_first    nonzero: the bounds + preview pass and the count pass of every
+ *                  cloud run as one launch each (groups of up to 256 clouds, their
+ *                  descriptors passed in the kernel parameters), on `stream`
+ *                  before the lanes fork; the remaining calls run on the lanes
+ *   count_threads  256 or 512: block size of the fused count pass
+ *   count_slots    0, 1024 or 4096: cells of the per-block shared-memory table the
+ *                  fused count pass accumulates hot cells in (0: none) */
+typedef struct {
+    uint32_t nlanes, fused_first, count_threads, count_slots;
+} fp_batch_opts;
+
+size_t fp_batch_workspace_size_ex(const fp_cloud_desc* h_clouds, uint32_t ncloud, const fp_batch_opts* opts);
+fp_status fp_build_batched_ex(const fp_cloud_desc* h_clouds, uint32_t ncloud, const fp_batch_opts* opts,
+                              void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------- out of core
  * A cloud larger than the device memory it may use (Sec. 4.4: the converter

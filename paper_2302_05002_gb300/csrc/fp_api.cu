@@ -2,14 +2,35 @@
 // argument checks, workspace carve-up and launch order.  Each entry point cites
 // the paper section of the stage it runs; the kernels live in fp_core.cu,
 // fp_sort.cu and fp_octree.cu.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include "fp_internal.cuh"
 
 namespace fp {
 
+// the bounded-wait test hook (fp_debug_withhold_publish)
+static std::atomic<uint32_t> g_dbg_withhold{0xFFFFFFFFu};
+static std::atomic<uint32_t> g_dbg_limit{kSpinLimit};
+
+void debug_wait_config(uint32_t* withhold_tile, uint32_t* spin_limit)
+{
+    *withhold_tile = g_dbg_withhold.load(std::memory_order_acquire);
+    *spin_limit = g_dbg_limit.load(std::memory_order_acquire);
+}
+
+// armed kernel of fp_time_kernel and the caller's events
+static std::atomic<int> g_kt_id{0};
+static cudaEvent_t g_kt_ev[2] = {nullptr, nullptr};
+
+void ktimer_mark(fp_kernel id, bool begin, cudaStream_t st)
+{
+    if (g_kt_id.load(std::memory_order_acquire) != (int)id || id == FP_KERNEL_NONE) return;
+    cudaEventRecord(g_kt_ev[begin ? 0 : 1], st);
+}
+
 // sticky error word of each device; kernels receive its address
-static __device__ uint32_t g_error_word = 0;
+static __device__ uint32_t g_error_word[2] = {0, 0};   // status bits, check sites
 
 struct DeviceInfo {
     bool ready = false;
@@ -75,8 +96,9 @@ fp_status make_workspace(void* base, size_t bytes, size_t need, Workspace& ws) {
 
 size_t bounds_ws_bytes(uint64_t n, int num_sms)
 {
-    uint64_t ntiles = (n + 4095) / 4096;
-    return Workspace::bytes_for({6 * 4 * (size_t)num_sms * 8, 8 * (size_t)(ntiles ? ntiles : 1), 16});
+    // block partials, one look-back word per tile, tile counter
+    const size_t nt = (size_t)((n + 4095) / 4096);
+    return Workspace::bytes_for({6 * 4 * (size_t)num_sms * 8, 8 * (nt ? nt : 1), 16});
 }
 
 }  // namespace fp
@@ -133,6 +155,38 @@ uint32_t fp_node_capacity_bound(uint64_t n, const fp_params* prm)
     return b > 0xFFFFFFF0ull ? 0xFFFFFFF0u : (uint32_t)b;
 }
 
+fp_status fp_debug_withhold_publish(uint32_t tile, uint32_t spin_limit)
+{
+    if (tile != 0xFFFFFFFFu && spin_limit == 0) return FP_ERR_INVALID;
+    g_dbg_limit.store(tile == 0xFFFFFFFFu ? kSpinLimit : spin_limit, std::memory_order_release);
+    g_dbg_withhold.store(tile, std::memory_order_release);
+    return FP_OK;
+}
+
+fp_status fp_time_kernel(fp_kernel k, cudaEvent_t start, cudaEvent_t stop)
+{
+    if ((int)k < (int)FP_KERNEL_NONE || (int)k > (int)FP_KERNEL_STITCH) return FP_ERR_INVALID;
+    if (k != FP_KERNEL_NONE && (!start || !stop)) return FP_ERR_INVALID;
+    g_kt_id.store(0, std::memory_order_release);
+    g_kt_ev[0] = start;
+    g_kt_ev[1] = stop;
+    g_kt_id.store((int)k, std::memory_order_release);
+    return FP_OK;
+}
+
+fp_status fp_get_device_error_sites(cudaStream_t stream, uint32_t* h_sites)
+{
+    if (!h_sites) return FP_ERR_INVALID;
+    DeviceInfo d;
+    fp_status s = device_info(d);
+    if (s != FP_OK) return s;
+    uint32_t v = 0;
+    if (cudaMemcpyAsync(&v, d.err + 1, sizeof(v), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return FP_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return FP_ERR_CUDA;
+    *h_sites = v;
+    return FP_OK;
+}
+
 fp_status fp_get_device_error(cudaStream_t stream, uint32_t* h_bits, int clear)
 {
     if (!h_bits) return FP_ERR_INVALID;
@@ -143,7 +197,7 @@ fp_status fp_get_device_error(cudaStream_t stream, uint32_t* h_bits, int clear)
     if (cudaMemcpyAsync(&v, d.err, sizeof(v), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return FP_ERR_CUDA;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return FP_ERR_CUDA;
     if (clear) {
-        if (cudaMemsetAsync(d.err, 0, sizeof(uint32_t), stream) != cudaSuccess) return FP_ERR_CUDA;
+        if (cudaMemsetAsync(d.err, 0, 2 * sizeof(uint32_t), stream) != cudaSuccess) return FP_ERR_CUDA;
         if (cudaStreamSynchronize(stream) != cudaSuccess) return FP_ERR_CUDA;
     }
     *h_bits = v;

@@ -22,7 +22,13 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 // Sticky per-device error word (passed to every kernel); bit (1u << fp_status)
 // marks each kind of fault.
-FP_DEV void raise(uint32_t* err, fp_status s) { atomicOr(err, 1u << (unsigned)s); }
+// err[0]: status bits (1 << status); err[1]: the check sites that fired (one
+// bit per site, for diagnosing which capacity or consistency check failed)
+FP_DEV void raise(uint32_t* err, fp_status s, int site = -1)
+{
+    atomicOr(err, 1u << (unsigned)s);
+    if (site >= 0) atomicOr(err + 1, 1u << (unsigned)site);
+}
 
 // ------------------------------------------------------------------ cube
 struct CubeDev {
@@ -92,6 +98,16 @@ FP_DEV uint32_t key_small(int32_t x, int32_t y, int32_t z, const CubeDev& c, flo
 }
 
 FP_DEV uint64_t key_at(uint64_t k21, int level) { return k21 >> (3 * (kKeyLevels - level)); }
+
+// per-point code of the octree stage: LOD owner level (5 bits), leaf level (5
+// bits) and the Morton key of the point's level-g cell (3 g <= 21 bits)
+FP_DEV uint32_t code_make(int own, int leaf, uint32_t cell)
+{
+    return (uint32_t)own | ((uint32_t)leaf << 5) | (cell << 10);
+}
+FP_DEV int code_own(uint32_t c) { return (int)(c & 31u); }
+FP_DEV int code_leaf(uint32_t c) { return (int)((c >> 5) & 31u); }
+FP_DEV uint32_t code_cell(uint32_t c) { return c >> 10; }
 
 // level of the deepest cell two level-21 keys share (-1: not even the root? no: >= 0)
 FP_DEV int common_level(uint64_t a, uint64_t b)

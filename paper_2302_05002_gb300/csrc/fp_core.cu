@@ -4,7 +4,10 @@
 //                      optionally, the preview compaction (Sec. 3 / Sec. 4.2):
 //                      index i is kept iff splitmix64(first + i) % m == 0.  Kept
 //                      points keep ascending index order through a single-pass
-//                      scan with decoupled look-back across tiles.
+//                      scan with decoupled look-back across tiles.  With the
+//                      bounds (the main path, k_bounds_bulk) each tile arrives
+//                      in shared memory by one bulk copy issued when the tile is
+//                      claimed, in flight during the ranking and look-back.
 //   k_count            count grid: one level-g Morton key per point, warp-
 //                      aggregated atomics into an L2-resident 8^g histogram.
 //   k_pyramid / k_chunk_mark / k_chunk_write
@@ -27,6 +30,12 @@ constexpr uint64_t kValMask = (1ull << 62) - 1;
 // keep rule of the compaction: none, index hash modulo m (the uniform
 // preview), or the smallest index hash of the point's cell (the spatial one)
 enum KeepRule { KEEP_NONE = 0, KEEP_MODULUS = 1, KEEP_CELL_MIN = 2 };
+
+FP_DEV bool keep_modulus(uint64_t first, uint64_t i, uint32_t modulus)
+{
+    const uint64_t h = splitmix64(first + i);
+    return (modulus & (modulus - 1)) == 0 ? (h & ((uint64_t)modulus - 1)) == 0 : (h % modulus) == 0;
+}
 
 template <bool BOUNDS, int KEEP>
 __global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __restrict__ pts, uint64_t n,
@@ -131,7 +140,7 @@ __global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __res
                     s_base = excl;
                     if (tile == ntiles - 1) {
                         *out_count = excl + total;
-                        if (excl + total > out_cap) raise(err, FP_ERR_CAPACITY);
+                        if (excl + total > out_cap) raise(err, FP_ERR_CAPACITY, 0);
                     }
                 }
             }
@@ -341,6 +350,177 @@ __global__ void k_chunk_write(const uint32_t* __restrict__ pyr, const uint32_t* 
     lut[m] = counts[m] > 0 ? id : kNone;
 }
 
+// The bounds + preview pass of the main path: the tile's 64 KB of points are
+// brought into shared memory by one bulk copy (cp.async.bulk, completion on an
+// mbarrier) issued when the tile is claimed, so the copy is in flight while the
+// keep flags are ranked and the tile's output offset is found by decoupled
+// look-back; extents and kept points are then read from shared memory.  Few
+// registers and 64 KB of shared memory per block: three blocks per SM, each
+// with a whole tile in flight.  Waits are bounded (FP_ERR_TIMEOUT).
+constexpr size_t kBdBulkSmem = sizeof(int4) * kBdTile;
+
+template <bool DECIM>
+__global__ void __launch_bounds__(kBdNT) k_bounds_bulk(const fp_point* __restrict__ pts, uint64_t n, uint64_t first,
+                                                       uint32_t modulus, fp_point* __restrict__ out, uint64_t out_cap,
+                                                       uint64_t* __restrict__ out_count, int32_t* __restrict__ partial,
+                                                       uint64_t* tile_status, uint32_t* tile_counter, uint64_t ntiles,
+                                                       uint32_t* err)
+{
+    extern __shared__ __align__(128) int4 s_pts[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_cnt[kBdIPT][kBdNT / 32];
+    __shared__ uint64_t s_base;
+    __shared__ int32_t s_red[6][kBdNT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
+    int32_t hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    uint32_t nwait = 0;
+    for (;;) {
+        __syncthreads();   // the previous tile's reads of s_pts are done
+        if (threadIdx.x == 0) {
+            const uint32_t t = atomicAdd(tile_counter, 1u);
+            s_tile = t;
+            if (t < ntiles) {
+                const uint64_t b = (uint64_t)t * kBdTile;
+                const uint32_t bytes = (uint32_t)(sizeof(int4) * min((uint64_t)kBdTile, n - b));
+                fence_async_smem();
+                mbar_expect_tx(&s_bar, bytes);
+                bulk_g2s(s_pts, reinterpret_cast<const int4*>(pts) + b, bytes, &s_bar);
+            }
+        }
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint64_t base = tile * kBdTile;
+
+        uint32_t keepmask = 0;
+        if (DECIM) {
+#pragma unroll
+            for (int r = 0; r < kBdIPT; ++r) {
+                const uint64_t i = base + (uint64_t)r * kBdNT + threadIdx.x;
+                const bool k = i < n && keep_modulus(first, i, modulus);
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k);
+                if (lane == 0) s_cnt[r][warp] = __popc(bal);
+                keepmask |= (uint32_t)k << r;
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                constexpr int per = kBdIPT * (kBdNT / 32) / 32;
+                uint32_t v[per];
+                uint32_t s = 0;
+#pragma unroll
+                for (int q = 0; q < per; ++q) {
+                    const int e = lane * per + q;
+                    v[q] = s_cnt[e / (kBdNT / 32)][e % (kBdNT / 32)];
+                    s += v[q];
+                }
+                uint32_t x = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+                uint32_t ex = x - s;
+#pragma unroll
+                for (int q = 0; q < per; ++q) {
+                    const int e = lane * per + q;
+                    s_cnt[e / (kBdNT / 32)][e % (kBdNT / 32)] = ex;
+                    ex += v[q];
+                }
+                // decoupled look-back by the whole warp: 32 earlier tiles' words per
+                // round trip; the sum runs back to the nearest inclusive prefix, and
+                // stops (and reads again) at the nearest word not yet published
+                uint64_t excl = 0;
+                if (tile == 0) {
+                    if (lane == 0)
+                        atomicExch((unsigned long long*)&tile_status[0], (unsigned long long)(kFlagInc | total));
+                } else {
+                    if (lane == 0)
+                        atomicExch((unsigned long long*)&tile_status[tile], (unsigned long long)(kFlagAgg | total));
+                    int64_t t = (int64_t)tile - 1;
+                    uint32_t spins = 0;
+                    while (t >= 0) {
+                        const int64_t q = t - lane;
+                        const uint64_t w = q >= 0 ? ld_volatile64(&tile_status[q]) : kFlagInc;
+                        const uint32_t inc = __ballot_sync(0xFFFFFFFFu, (w >> 62) == 2);
+                        const uint32_t none = __ballot_sync(0xFFFFFFFFu, (w >> 62) == 0);
+                        const int fi = inc ? __ffs(inc) - 1 : 32, fn = none ? __ffs(none) - 1 : 32;
+                        // lanes [0, take) are summed: up to the first unpublished word, or
+                        // through the first inclusive prefix, or all 32 aggregates
+                        const int take = fn < fi ? fn : (fi < 32 ? fi + 1 : 32);
+                        uint64_t v = lane < take ? (w & kValMask) : 0;
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                        excl += v;
+                        if (fi < fn) break;   // reached an inclusive prefix
+                        if (take == 0 && ++spins > kSpinLimit) {
+                            if (lane == 0) raise(err, FP_ERR_TIMEOUT);
+                            break;
+                        }
+                        t -= take;
+                    }
+                    if (lane == 0)
+                        atomicExch((unsigned long long*)&tile_status[tile],
+                                   (unsigned long long)(kFlagInc | (excl + total)));
+                }
+                if (lane == 0) {
+                    s_base = excl;
+                    if (tile == ntiles - 1) {
+                        *out_count = excl + total;
+                        if (excl + total > out_cap) raise(err, FP_ERR_CAPACITY, 0);
+                    }
+                }
+            }
+        }
+        // the tile's points have landed (bounded wait; on a time-out the copy is
+        // given a second bounded wait to land before the block leaves)
+        const bool ok = mbar_wait(&s_bar, nwait & 1);
+        ++nwait;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) raise(err, FP_ERR_TIMEOUT);
+            mbar_wait(&s_bar, (nwait - 1) & 1);
+            break;
+        }
+#pragma unroll 4
+        for (int r = 0; r < kBdIPT; ++r) {
+            const uint64_t i = base + (uint64_t)r * kBdNT + threadIdx.x;
+            if (i < n) {
+                const int4 p = s_pts[r * kBdNT + threadIdx.x];
+                lo[0] = min(lo[0], p.x); hi[0] = max(hi[0], p.x);
+                lo[1] = min(lo[1], p.y); hi[1] = max(hi[1], p.y);
+                lo[2] = min(lo[2], p.z); hi[2] = max(hi[2], p.z);
+            }
+        }
+        if (DECIM) {
+#pragma unroll 4
+            for (int r = 0; r < kBdIPT; ++r) {
+                const bool kept = (keepmask >> r) & 1u;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, kept);
+                if (kept) {
+                    const uint64_t pos = s_base + s_cnt[r][warp] + __popc(bal & lanemask_lt());
+                    if (pos < out_cap) st_point(out, pos, s_pts[r * kBdNT + threadIdx.x]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = __reduce_min_sync(0xFFFFFFFFu, lo[a]);
+        hi[a] = __reduce_max_sync(0xFFFFFFFFu, hi[a]);
+    }
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) { s_red[a][warp] = lo[a]; s_red[3 + a][warp] = hi[a]; }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int a = threadIdx.x;
+        int32_t v = s_red[a][0];
+        for (int w = 1; w < kBdNT / 32; ++w) v = a < 3 ? min(v, s_red[a][w]) : max(v, s_red[a][w]);
+        partial[blockIdx.x * 6 + a] = v;
+    }
+}
+
 // ----------------------------------------------------------------- host side
 cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cube, bool bounds, bool decim,
                                    uint64_t first, uint32_t modulus, fp_point* out, uint64_t out_cap,
@@ -359,15 +539,14 @@ cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cub
     }
     if (decim && n == 0) k_zero_count<<<1, 1, 0, st>>>(out_count);
     if (n) {
-        if (bounds && decim)
-            k_bounds_decimate<true, KEEP_MODULUS><<<grid, kBdNT, 0, st>>>(
-                pts, n, first, modulus, out, out_cap, out_count, partial, status, counter, ntiles, ws.err, nullptr,
-                nullptr, 0);
-        else if (bounds)
-            k_bounds_decimate<true, KEEP_NONE><<<grid, kBdNT, 0, st>>>(
-                pts, n, first, modulus, out, out_cap, out_count, partial, status, counter, ntiles, ws.err, nullptr,
-                nullptr, 0);
-        else
+        KTimerScope kt(FP_KERNEL_BOUNDS_DECIMATE, st);
+        if (bounds) {   // points by bulk copy into shared memory
+            auto kern = decim ? k_bounds_bulk<true> : k_bounds_bulk<false>;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBdBulkSmem)))
+                return e;
+            kern<<<grid, kBdNT, kBdBulkSmem, st>>>(pts, n, first, modulus, out, out_cap, out_count, partial, status,
+                                                  counter, ntiles, ws.err);
+        } else
             k_bounds_decimate<false, KEEP_MODULUS><<<grid, kBdNT, 0, st>>>(
                 pts, n, first, modulus, out, out_cap, out_count, partial, status, counter, ntiles, ws.err, nullptr,
                 nullptr, 0);
@@ -443,6 +622,7 @@ cudaError_t launch_count(const fp_point* pts, uint64_t n, const fp_cube* cube, i
     if (n == 0) return cudaSuccess;
     uint64_t want = (n + 1023) / 1024;
     int grid = (int)std::min<uint64_t>(want, (uint64_t)ws.num_sms * 8);
+    KTimerScope kt(FP_KERNEL_COUNT, st);
     k_count<true><<<grid, 256, 0, st>>>(pts, n, cube, g, counts);
     return cudaGetLastError();
 }

@@ -39,6 +39,17 @@ struct Workspace {
 
 // fp_api.cu
 fp_status make_workspace(void* base, size_t bytes, size_t need, Workspace& ws);
+// test hook of the bounded waits (fp_debug_withhold_publish): the tile whose
+// publish the look-back passes withhold (0xFFFFFFFF: none) and their spin limit
+void debug_wait_config(uint32_t* withhold_tile, uint32_t* spin_limit);
+// kernel timing (fp_time_kernel): records the armed events around the launches of kernel `id`
+void ktimer_mark(fp_kernel id, bool begin, cudaStream_t st);
+struct KTimerScope {
+    fp_kernel id;
+    cudaStream_t st;
+    KTimerScope(fp_kernel k, cudaStream_t s) : id(k), st(s) { ktimer_mark(id, true, st); }
+    ~KTimerScope() { ktimer_mark(id, false, st); }
+};
 
 // fp_core.cu
 cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cube, bool bounds, bool decim,
@@ -85,7 +96,7 @@ constexpr size_t kNodeRecBytes = 24;
 struct OctGroup {
     const uint32_t* rec_counts;      // the group's points per level-g cell (0 outside the group)
     uint32_t leaf_base;              // position of the group's first point in the whole distributed array
-    uint16_t* codes;                 // per group point: LOD owner level | leaf level << 8
+    uint32_t* codes;                 // per group point: owner level, leaf level, level-g cell (code_make)
     NodeRec* deep;                   // nodes below level g, appended at *num_deep
     uint32_t deep_cap;
     uint32_t* num_deep;
@@ -108,7 +119,7 @@ uint64_t upper_node_bound(const fp_params& p);
 cudaError_t launch_octree_nodes(const uint32_t* counts, const fp_params& prm, NodeRec* recs, uint64_t rec_cap,
                                 const uint32_t* num_deep, fp_node* nodes, uint32_t node_cap, uint32_t* num_nodes,
                                 const NodeTables& T, const Workspace& ws, cudaStream_t st);
-cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint16_t* codes,
+cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint32_t* codes,
                                   const NodeTables& T, const fp_params& prm,
                                   uint32_t* owner, const Workspace& ws, cudaStream_t st);
 cudaError_t launch_node_first(fp_node* nodes, const uint32_t* num_nodes, uint32_t node_cap, const uint32_t* nown,

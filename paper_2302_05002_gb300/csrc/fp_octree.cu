@@ -96,12 +96,30 @@ struct OctCtx {   // device pointers of one fp_build_chunk_octree call
     NodeRec* nrec;
     uint32_t* nnode;
     uint32_t node_cap_ws;
-    uint16_t* codes;      // per record position j: LOD owner level | leaf level << 8
+    uint32_t* codes;      // per record position j: code_make(LOD owner level, leaf level, level-g cell)
     uint32_t open_cap;
     int g, s, lmax, dl;
     uint64_t C;
+    uint64_t n;           // records (bound of record positions j and of record indices)
     uint32_t* err;
 };
+
+// code of record position jj (owner level, leaf level and the level-g cell of
+// its key21), checked against the record count (an inconsistent grouping must
+// not turn into a stray store)
+FP_DEV void put_code(const OctCtx& c, uint32_t jj, int K, int leafl, uint64_t key21)
+{
+    if (jj < c.n) c.codes[jj] = code_make(K, leafl, (uint32_t)(key21 >> (3 * (kKeyLevels - c.g))));
+    else raise(c.err, FP_ERR_CAPACITY, 17);
+}
+
+// record i of the cell-grouped array, checked likewise (a zero record beyond it)
+FP_DEV uint4 get_rec(const OctCtx& c, uint64_t i)
+{
+    if (i < c.n) return c.rec[i];
+    raise(c.err, FP_ERR_CAPACITY, 18);
+    return make_uint4(0u, 0u, 0u, 0u);
+}
 
 FP_DEV uint32_t pyr_at(const uint32_t* pyr, const uint32_t* counts, int g, int l, uint64_t key)
 {
@@ -123,7 +141,7 @@ __global__ void k_pyr_level(const uint32_t* __restrict__ child, uint32_t* __rest
 FP_DEV void emit_node(const OctCtx& c, uint64_t key, int level, uint32_t count, uint32_t leaf_first, bool leaf)
 {
     uint32_t id = atomicAdd(c.nnode, 1u);
-    if (id >= c.node_cap_ws) { raise(c.err, FP_ERR_CAPACITY); return; }
+    if (id >= c.node_cap_ws) { raise(c.err, FP_ERR_CAPACITY, 1); return; }
     NodeRec r;
     r.key = key;
     r.count = count;
@@ -137,7 +155,7 @@ FP_DEV void emit_node(const OctCtx& c, uint64_t key, int level, uint32_t count, 
 FP_DEV void emit_piece(const OctCtx& c, uint32_t begin, uint32_t count, int q, uint8_t hier, uint8_t A, int srt)
 {
     uint32_t id = atomicAdd(c.npieces, 1u);
-    if (id >= c.piece_cap) { raise(c.err, FP_ERR_CAPACITY); return; }
+    if (id >= c.piece_cap) { raise(c.err, FP_ERR_CAPACITY, 2); return; }
     Piece p;
     p.begin = begin;
     p.count = count;
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(256) k_cell_scatter(const int4* __restrict__ p
         if (lane == leader && m != kNone) at = atomicAdd(&cursor[cursor_slot(m, g)], (uint32_t)__popc(peers));
         at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
         if (m != kNone) {
-            if (at >= n) { raise(err, FP_ERR_CAPACITY); continue; }   // a count grid of other points
+            if (at >= n) { raise(err, FP_ERR_CAPACITY, 3); continue; }   // a count grid of other points
             rec[at] = rec_make(k, (uint32_t)i, 0u);
         }
     }
@@ -206,7 +224,7 @@ __global__ void k_cell_check(const uint32_t* __restrict__ cstart, uint64_t cells
                              uint32_t* err)
 {
     for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < cells; m += (uint64_t)gridDim.x * blockDim.x)
-        if (cursor[cursor_slot((uint32_t)m, g)] != cstart[m + 1]) raise(err, FP_ERR_CAPACITY);
+        if (cursor[cursor_slot((uint32_t)m, g)] != cstart[m + 1]) raise(err, FP_ERR_CAPACITY, 4);
 }
 
 // Per level-g cell: leaf level if the hierarchy ends at or above g, kInner if
@@ -229,7 +247,7 @@ __global__ void k_cell_setup(OctCtx c, OpenNode* open0, uint32_t* nopen0)
         emit_piece(c, c.cstart[m], cnt, c.g, hier, (uint8_t)c.g, c.g);
     } else {
         uint32_t id = atomicAdd(nopen0, 1u);
-        if (id >= c.open_cap) { raise(c.err, FP_ERR_CAPACITY); return; }
+        if (id >= c.open_cap) { raise(c.err, FP_ERR_CAPACITY, 5); return; }
         OpenNode o;
         o.key = m;
         o.begin = c.cstart[m];
@@ -377,7 +395,7 @@ __global__ void k_round_scatter(const uint32_t* total, const uint4* __restrict__
         if (slot != kNone && lane == leader) at = atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
         at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
         if (slot == kNone) continue;
-        if (at >= n) { raise(err, FP_ERR_CAPACITY); continue; }
+        if (at >= n) { raise(err, FP_ERR_CAPACITY, 6); continue; }
         rec[at] = make_uint4(r.x, r.y, r.z, 0u);
     }
 }
@@ -444,7 +462,7 @@ __global__ void k_split(OctCtx c, const OpenNode* cur, const uint32_t* ncur, Ope
                 const bool open_child = cn > (uint32_t)kPieceMax && q1 < c.dl;
                 if (open_child) id = atomicAdd(nnxt, 1u);
                 if (open_child && id >= open_cap) {
-                    raise(c.err, FP_ERR_CAPACITY);
+                    raise(c.err, FP_ERR_CAPACITY, 7);
                 } else if (open_child) {
                     OpenNode ch;
                     ch.key = key;
@@ -731,11 +749,11 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
         // ---- pieces of one point: the point is its piece's minimum
         for (int pi = threadIdx.x; pi < np; pi += kUnitNT) {
             if (S.pkind[pi] != 0) continue;
-            const uint32_t jj = rec_j_at(c.rec, S.pbeg[pi]);
+            const uint4 rr = get_rec(c, S.pbeg[pi]);
             const int leafl = S.phier[pi];
             int K = (int)S.pA[pi] - c.s;
             K = K < 0 ? 0 : (K > leafl ? leafl : K);
-            c.codes[jj] = (uint16_t)(K | (leafl << 8));
+            put_code(c, rr.z, K, leafl, rec_key(rr));
         }
         // ---- pieces of 2..32 points: lambda from the deepest level shared with any
         // point of smaller index in the piece (all pairs, by shuffles); a warp
@@ -752,7 +770,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
                 kb[t] = 0;
                 jb[t] = 0xFFFFFFFFu;
                 if (lane < nb[t]) {
-                    const uint4 r = c.rec[S.pbeg[pi] + lane];
+                    const uint4 r = get_rec(c, S.pbeg[pi] + lane);
                     kb[t] = rec_key(r);
                     jb[t] = r.z;
                 }
@@ -776,7 +794,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
                     const int leafl = S.phier[pi];
                     int K = lambda - c.s;
                     K = K < 0 ? 0 : (K > leafl ? leafl : K);
-                    c.codes[jj] = (uint16_t)(K | (leafl << 8));
+                    put_code(c, jj, K, leafl, k);
                 }
             }
         }
@@ -806,7 +824,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
 #pragma unroll
             for (int q = 0; q < kPer; ++q)   // all loads in flight together
                 if (pp[q] >= 0) {
-                    const uint4 r = c.rec[gi[q]];
+                    const uint4 r = get_rec(c, gi[q]);
                     kq[q] = rec_key(r);
                     jq[q] = r.z;
                 }
@@ -848,7 +866,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
                 const int leafl = S.phier[pi];
                 int K = lambda - c.s;
                 K = K < 0 ? 0 : (K > leafl ? leafl : K);
-                c.codes[jq[q]] = (uint16_t)(K | (leafl << 8));
+                put_code(c, jq[q], K, leafl, kq[q]);
             }
             __syncthreads();   // the tables overlay the general path's arrays
         }
@@ -875,7 +893,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
 #pragma unroll
             for (int q = 0; q < kPer; ++q)   // all loads in flight together
                 if ((int)threadIdx.x + q * kUnitNT < cnt) {
-                    const uint4 r = c.rec[gi[q]];
+                    const uint4 r = get_rec(c, gi[q]);
                     kq[q] = rec_key(r);
                     jq[q] = r.z;
                 }
@@ -1081,7 +1099,7 @@ __global__ void __launch_bounds__(kUnitNT, 2) k_units(OctCtx c, const uint4* uhe
             if (K < 0) K = 0;
             if (K > leafl) K = leafl;
             const uint32_t jj = S.j[vv];
-            c.codes[jj] = (uint16_t)(K | (leafl << 8));
+            put_code(c, jj, K, leafl, S.key[r]);
         }
         __syncthreads();
     }
@@ -1098,21 +1116,22 @@ __global__ void __launch_bounds__(256) k_dup_pieces(OctCtx c)
         const Piece p = c.pieces[c.dups[k]];
         const int leafl = p.hier == kInner ? c.lmax : (int)p.hier;
         uint32_t mn = kNone;
-        for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) mn = min(mn, rec_j_at(c.rec, p.begin + r));
+        for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) mn = min(mn, get_rec(c, (uint64_t)p.begin + r).z);
         mn = __reduce_min_sync(0xFFFFFFFFu, mn);
         if (lane == 0) s_min[warp] = mn;
         __syncthreads();
         mn = s_min[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mn = min(mn, s_min[w]);
         for (uint32_t r = threadIdx.x; r < p.count; r += blockDim.x) {
-            uint32_t jj = rec_j_at(c.rec, p.begin + r);
+            const uint4 rr = get_rec(c, (uint64_t)p.begin + r);
+            const uint32_t jj = rr.z;
             int K = leafl;
             if (jj == mn) {
                 K = (int)p.A - c.s;
                 if (K < 0) K = 0;
                 if (K > leafl) K = leafl;
             }
-            c.codes[jj] = (uint16_t)(K | (leafl << 8));
+            put_code(c, jj, K, leafl, rec_key(rr));
         }
         __syncthreads();
     }
@@ -1165,7 +1184,7 @@ __global__ void k_node_write(const NodeRec* nrec, const uint32_t* nnode, const u
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *num_nodes = M;
-        if (M > node_cap) raise(err, FP_ERR_CAPACITY);
+        if (M > node_cap) raise(err, FP_ERR_CAPACITY, 8);
     }
     if (i >= M) return;
     NodeRec r = nrec[order[i]];
@@ -1221,13 +1240,15 @@ __global__ void k_node_children(const uint32_t* nnode, const uint64_t* sorted_st
     }
 }
 
-// owner and leaf ids of every distributed point; owned counts per node
-// A node deeper than g lies in the subtree of its level-g ancestor, whose ids
-// are consecutive in preorder: the search runs over that subtree only.  Keys
-// are taken at max_level (no node is deeper): 32-bit for max_level <= 10.
+// owner and leaf ids of every distributed point; owned counts per node.
+// A node at a level <= g is found from the level-g cell in the point's code
+// (the id table of levels <= g); a node deeper than g lies in the subtree of its
+// level-g ancestor, whose ids are consecutive in preorder: the search runs over
+// that subtree only, with the point's key at max_level (32-bit for max_level
+// <= 10) -- only then is the point itself read.  leafid (nullable): the leaf id.
 template <bool SMALL>
 __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp_cube* cube,
-                          const uint16_t* codes, const uint32_t* idxtab,
+                          const uint32_t* codes, const uint32_t* idxtab,
                           const uint64_t* sorted_start, const uint8_t* sorted_level, const uint32_t* ndesc,
                           const uint32_t* nnode, uint32_t* owner, uint32_t* leafid, uint32_t* n_own, int g, int lmax,
                           uint32_t* err)
@@ -1237,26 +1258,32 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
     const uint32_t M = *nnode;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
+    const int nt = leafid ? 2 : 1;
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
         uint64_t j = i0 + threadIdx.x;
         uint32_t oid = kNone;
         if (j < n) {
-            const int4 p = ld_point(pts, j);
-            const uint64_t kl = SMALL ? (uint64_t)key_small(p.x, p.y, p.z, cb, scale_l, lmax)
-                                      : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
             const uint32_t cw = codes[j];
-            int ks[2] = {(int)(cw & 0xFFu), (int)(cw >> 8)};
-            uint32_t ids[2];
-            const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + (kl >> (3 * (lmax - g)))];
-            for (int t = 0; t < 2; ++t) {
+            const uint32_t cell = code_cell(cw);
+            const int ks[2] = {code_own(cw), code_leaf(cw)};
+            uint32_t ids[2] = {0u, 0u};
+            const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + cell];
+            uint64_t kl = 0;
+            bool have_kl = false;
+            for (int t = 0; t < nt; ++t) {
                 const int L = ks[t];
-                if (L > lmax) { ids[t] = kNone; continue; }
-                const uint64_t k = kl >> (3 * (lmax - L));
                 if (L <= g) {
-                    ids[t] = idxtab[((1ull << (3 * L)) - 1) / 7 + k];
+                    ids[t] = idxtab[((1ull << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
                 } else {
+                    if (!have_kl) {
+                        const int4 p = ld_point(pts, j);
+                        kl = SMALL ? (uint64_t)key_small(p.x, p.y, p.z, cb, scale_l, lmax)
+                                   : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
+                        have_kl = true;
+                    }
                     ids[t] = kNone;
-                    if (c0 < M) {
+                    if (L <= lmax && c0 < M) {
+                        const uint64_t k = kl >> (3 * (lmax - L));
                         const uint32_t r = node_lookup(sorted_start + c0, sorted_level + c0,
                                                        min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
                         if (r != kNone) ids[t] = c0 + r;
@@ -1264,7 +1291,7 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
                 }
             }
             if (ids[0] >= M || ids[1] >= M) {   // never for a consistent tree
-                raise(err, FP_ERR_CAPACITY);
+                raise(err, FP_ERR_CAPACITY, 9);
                 ids[0] = ids[1] = 0;
             }
             owner[j] = ids[0];
@@ -1343,7 +1370,7 @@ struct OctBufs {
     uint32_t *nl, *nv2, *nv3;
     uint8_t* slevel;
     uint32_t *idxtab, *leafw, *nown;
-    uint16_t* codes;
+    uint32_t* codes;
     uint32_t* leafid;
     uint32_t* unit_p0;
     uint4 *pdesc, *uhead;   // window descriptors (k_unit_desc)
@@ -1390,7 +1417,7 @@ static OctBufs oct_carve(const Workspace& ws, uint64_t n, const OctLayout& Ly)
     B.idxtab = ws.take<uint32_t>(Ly.cells * 8 / 7 + 8);
     B.leafw = ws.take<uint32_t>(std::max<uint64_t>(Ly.node_cap, kScanMaxTiles));
     B.nown = ws.take<uint32_t>(Ly.node_cap);
-    B.codes = ws.take<uint16_t>(N);
+    B.codes = ws.take<uint32_t>(N);
     B.leafid = ws.take<uint32_t>(N);
     B.unit_p0 = ws.take<uint32_t>((N + kWindow - 1) / kWindow + 2);
     B.pdesc = ws.take<uint4>(Ly.piece_cap);
@@ -1464,7 +1491,7 @@ __global__ void k_append_nodes(const NodeRec* rec, const uint32_t* nrec, uint32_
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
         if (base + i < out_cap) out[base + i] = rec[i];
-        else raise(err, FP_ERR_CAPACITY);
+        else raise(err, FP_ERR_CAPACITY, 10);
     }
 }
 
@@ -1520,13 +1547,14 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     c.nrec = B.nrec; c.nnode = nnode; c.node_cap_ws = (uint32_t)Ly.node_cap;
     c.codes = grp ? grp->codes : B.codes;
     c.open_cap = (uint32_t)Ly.open_cap;
-    c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.err = ws.err;
+    c.g = g; c.s = s; c.lmax = lmax; c.dl = dl; c.C = prm.node_capacity; c.n = N; c.err = ws.err;
 
     // 2. group by level-g cell: (key21, j) scattered by cell id
     {
         const int gcell = (int)std::max<uint64_t>(1, std::min<uint64_t>((Ly.cells + 255) / 256, ws.num_sms * 8ull));
         k_cell_cursor_init<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g);
         const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 8));
+        KTimerScope kt(FP_KERNEL_CELL_GROUP, st);
         k_cell_scatter<<<gs, 256, 0, st>>>(reinterpret_cast<const int4*>(sorted), N, cube, B.cursor, B.rec, g,
                                            ws.err);
         k_cell_check<<<gcell, 256, 0, st>>>(B.cstart, Ly.cells, B.cursor, g, ws.err);
@@ -1539,6 +1567,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     // which puts them in key order down to that depth; then the splits of
     // those levels, whose children still too large stay open for the next round.
     {
+        KTimerScope kt(FP_KERNEL_SPLIT_ROUNDS, st);
         const uint32_t cap = (uint32_t)Ly.open_cap;
         int gw = std::max(1, std::min(ws.num_sms * 16, (int)(((uint64_t)cap * 32 + 255) / 256)));
         const int gr = std::max(1, std::min(ws.num_sms * 8, (int)((N + 255) / 256)));
@@ -1590,7 +1619,10 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
             (int)std::max<uint64_t>(1, std::min<uint64_t>((nunits * 32 + 255) / 256, (uint64_t)ws.num_sms * 8));
         k_unit_desc<<<gd, 256, 0, st>>>(c, B.unit_p0, B.pv, nunits, B.pdesc, B.pdesc2, B.uhead);
         int grid = (int)std::min<uint64_t>(nunits, (uint64_t)ws.num_sms * 2);
-        k_units<<<grid, kUnitNT, smem, st>>>(c, B.uhead, B.pdesc, B.pdesc2, N);
+        {
+            KTimerScope kt(FP_KERNEL_UNITS, st);
+            k_units<<<grid, kUnitNT, smem, st>>>(c, B.uhead, B.pdesc, B.pdesc2, N);
+        }
         k_dup_pieces<<<ws.num_sms, 256, 0, st>>>(c);
     }
     if (grp) {   // a chunk group: its nodes below level g are appended to the caller's list
@@ -1603,6 +1635,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     // 7. node table in preorder: stable sort by level, then by start at max_level resolution
     {
         NodeSortBufs nb{B.nk, B.nk2, B.nk3, B.nk4, B.nl, B.nv2, B.nv3, B.slevel, B.idxtab, B.leafw, B.ndesc};
+        KTimerScope kt(FP_KERNEL_NODE_TABLE, st);
         if ((e = node_table(sc, B.nrec, nnode, (uint32_t)Ly.node_cap, nb, nodes, node_cap, num_nodes, g, lmax, ws, st)))
             return e;
         if ((e = cudaMemsetAsync(B.nown, 0, (size_t)Ly.node_cap * sizeof(uint32_t), st))) return e;
@@ -1611,7 +1644,9 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     {
         int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
         auto kres = lmax <= 10 ? k_resolve<true> : k_resolve<false>;
-        kres<<<grid, 256, 0, st>>>(sorted, N, cube, B.codes, B.idxtab, B.nk, B.slevel, B.ndesc, nnode, owner, B.leafid,
+        KTimerScope kt(FP_KERNEL_RESOLVE, st);
+        kres<<<grid, 256, 0, st>>>(sorted, N, cube, B.codes, B.idxtab, B.nk, B.slevel, B.ndesc, nnode, owner,
+                                   (leaf_pts || leaf_perm) ? B.leafid : nullptr,
                                    B.nown, g, lmax, ws.err);
         k_write_nown<<<(unsigned)((Ly.node_cap + 255) / 256), 256, 0, st>>>(nodes, nnode, node_cap, B.nown);
     }
@@ -1619,6 +1654,7 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     // leaf lies in the subtree of its points' chunk); the whole-array sort by
     // leaf id runs instead, gated on the device, when a chunk does not fit
     if (leaf_pts || leaf_perm) {
+        KTimerScope kt(FP_KERNEL_LEAF_SCATTER, st);
         SegCall sg{};
         sg.mode = SEG_LEAF;
         sg.nodes = nodes; sg.num_nodes = num_nodes; sg.node_cap = node_cap;
@@ -1708,7 +1744,7 @@ cudaError_t launch_octree_nodes(const uint32_t* counts, const fp_params& prm, No
     return cudaMemsetAsync(T.nown, 0, rec_cap * sizeof(uint32_t), st);
 }
 
-cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint16_t* codes,
+cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube* cube, const uint32_t* codes,
                                   const NodeTables& T, const fp_params& prm,
                                   uint32_t* owner, const Workspace& ws, cudaStream_t st)
 {
@@ -1825,7 +1861,7 @@ __global__ void k_stitch_place(const uint32_t* nstaged, const uint64_t* key, con
         const uint32_t X = r < R ? list[r] : M;
         const uint32_t j = src[t];
         const uint64_t f = X < M ? first[X] + (t - soff[X]) : n;
-        if (f >= n || j >= n) { raise(err, FP_ERR_CAPACITY); continue; }
+        if (f >= n || j >= n) { raise(err, FP_ERR_CAPACITY, 11); continue; }
         fin[f] = __ldg(pts + j);
         fperm[f] = perm[j];
     }
@@ -1952,8 +1988,12 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     sg.st_key = B.s_key; sg.st_src = B.s_val; sg.st_count = nstaged; sg.st_shift = pbits;
     uint32_t* nrank = cnt + 4;   // nodes outside every chunk subtree
     sg.st_rank = B.srank; sg.st_list = B.slist; sg.st_nrank = nrank; sg.st_tiles = B.tiles32;
-    if ((e = seg_scatter(B.seg, sg, ws, st))) return e;
+    {
+        KTimerScope kt(FP_KERNEL_OWNER_SCATTER, st);
+        if ((e = seg_scatter(B.seg, sg, ws, st))) return e;
+    }
     // 2. the stitch: staged records sorted by (node, original index), then placed
+    KTimerScope kt_stitch(FP_KERNEL_STITCH, st);
     k_stitch_counts<<<gM, 256, 0, st>>>(B.seg.inside, nown, nm, B.scnt, M);
     if ((e = scan_exclusive<uint32_t, uint32_t>(B.scnt, soff, M, nm, B.tiles32, (uint32_t*)nullptr,
                                                 (uint32_t*)nullptr, st)))
@@ -1971,6 +2011,8 @@ cudaError_t launch_subsample(fp_node* nodes, const uint32_t* num_nodes, uint32_t
     k_stitch_place<<<gN, 256, 0, st>>>(nstaged, B.s_key3, B.s_val3, pbits, B.slist, nrank, nm, soff, first,
                                        reinterpret_cast<const int4*>(sorted), perm, N,
                                        reinterpret_cast<int4*>(final_pts), final_perm, ws.err);
+    ktimer_mark(FP_KERNEL_STITCH, false, st);   // the gated whole-array path below is not timed with it
+    kt_stitch.id = FP_KERNEL_NONE;
 
     // whole-array path (runs with seg cnt[5] = n records when a chunk did not fit, else on none):
     // stable scatter by owner id, then the owner segments spanning several chunks re-sorted

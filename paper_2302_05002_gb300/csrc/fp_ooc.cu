@@ -215,7 +215,7 @@ __global__ void k_stitch_final(const uint64_t* key, const uint32_t* val, uint64_
 struct HostStore {
     int4* pts;          // n: the distributed points, group after group
     uint32_t* perm;     // n: their original indices
-    uint16_t* codes;    // n: LOD owner level | leaf level << 8
+    uint32_t* codes;    // n: owner level, leaf level, level-g cell (code_make)
     uint32_t* owner;    // n: owner id
     uint64_t* st_key;   // n: staged (owner, index)
     uint32_t* st_src;   // n: staged record's position in pts
@@ -229,7 +229,7 @@ HostStore host_carve(void* base, uint64_t n)
     HostStore h;
     h.pts = w.take<int4>(N);
     h.perm = w.take<uint32_t>(N);
-    h.codes = w.take<uint16_t>(N);
+    h.codes = w.take<uint32_t>(N);
     h.owner = w.take<uint32_t>(N);
     h.st_key = w.take<uint64_t>(N);
     h.st_src = w.take<uint32_t>(N);
@@ -239,7 +239,7 @@ HostStore host_carve(void* base, uint64_t n)
 size_t host_bytes(uint64_t n)
 {   // the pieces host_carve takes, in its order
     const uint64_t N = n ? n : 1;
-    return Workspace::bytes_for({16 * N, 4 * N, N, N, 4 * N, 8 * N, 4 * N});
+    return Workspace::bytes_for({16 * N, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N});
 }
 
 uint64_t preview_piece_cap(uint64_t p, uint32_t m)
@@ -318,7 +318,7 @@ struct Group {   // device buffers of one chunk group (G points), reused group a
     char* region;   // the start of the group region
     int4* pts;
     uint32_t *perm, *owner;
-    uint16_t* codes;
+    uint32_t* codes;
     uint64_t *key, *key2, *key3;
     uint32_t *val2, *val3;
     char* ws;      // stage workspace
@@ -346,7 +346,7 @@ Group group_carve(const Workspace& w, uint64_t G, uint64_t P, const fp_params& p
     g.pts = resident ? nullptr : w.take<int4>(N);
     g.perm = resident ? nullptr : w.take<uint32_t>(N);
     g.owner = w.take<uint32_t>(N);
-    g.codes = w.take<uint16_t>(N);
+    g.codes = w.take<uint32_t>(N);
     g.key = w.take<uint64_t>(N);
     g.key2 = w.take<uint64_t>(N);
     g.key3 = w.take<uint64_t>(N);
@@ -635,7 +635,7 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
                                     F.kdev, F.off_local, F.counts, prm, nullptr, 0, nullptr, nullptr, nullptr,
                                     nullptr, &grp, ws, st)))
             return cu(e);
-        if ((e = cudaMemcpyAsync(H.codes + b0, B.codes, ng * 2, cudaMemcpyDeviceToHost, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(H.codes + b0, B.codes, ng * 4, cudaMemcpyDeviceToHost, st))) return cu(e);
     }
 
     // ---- node table of the whole cloud
@@ -649,7 +649,7 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
         const uint64_t b0 = off[c0], ng = off[c1] - off[c0];
         if (resident) B.pts = res_pts + b0;
         else if ((e = cudaMemcpyAsync(B.pts, H.pts + b0, ng * 16, cudaMemcpyHostToDevice, st))) return cu(e);
-        if ((e = cudaMemcpyAsync(B.codes, H.codes + b0, ng * 2, cudaMemcpyHostToDevice, st))) return cu(e);
+        if ((e = cudaMemcpyAsync(B.codes, H.codes + b0, ng * 4, cudaMemcpyHostToDevice, st))) return cu(e);
         if ((e = launch_octree_resolve(reinterpret_cast<const fp_point*>(B.pts), ng, F.cube, B.codes, F.T, prm,
                                        B.owner, ws, st)))
             return cu(e);

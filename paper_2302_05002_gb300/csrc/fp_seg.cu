@@ -48,7 +48,7 @@ __global__ void k_seg_setup(int mode, const fp_node* nodes, const uint32_t* num_
         const uint32_t ntl = (uint32_t)((cn + kSortTile - 1) / kSortTile);
         const uint32_t at = atomicAdd(&cnt[v], ntl);
         if ((uint64_t)at + ntl > tiles_max) {
-            raise(err, FP_ERR_CAPACITY);
+            raise(err, FP_ERR_CAPACITY, 12);
             atomicOr(&cnt[2], 1u);
             continue;
         }

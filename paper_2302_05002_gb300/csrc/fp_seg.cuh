@@ -24,6 +24,9 @@ namespace fp {
 static_assert(sizeof(fp_node) == 40 && offsetof(fp_node, leaf_first) % 8 == 0, "fp_node layout");
 
 constexpr int kSegSmallBits = 8;
+// earlier tiles' words one look-back round trip reads per digit (16 measured
+// no faster than 8 on the 10^9-point distribution)
+constexpr int kSegLookBatch = 8;
 constexpr int kSegMaxBits = 11;
 
 struct SegTile {
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
             if (p < tn) {
                 d = dg[r];
                 if (d >= (uint32_t)sdig) {
-                    if (!a.stitch) raise(a.err, FP_ERR_CAPACITY);   // a leaf outside the chunk's subtree
+                    if (!a.stitch) raise(a.err, FP_ERR_CAPACITY, 13);   // a leaf outside the chunk's subtree
                     d = (uint32_t)(nb - 1);
                 }
             }
@@ -231,8 +234,9 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
             }
             uint32_t excl = 0;
             if (td.index > 0) {
-                excl = look_back([&](int64_t t) { return &a.status[(uint64_t)t * kStride + d]; }, (int64_t)row - 1,
-                                 (int64_t)row - (int64_t)td.index, a.err);
+                auto word = [&](int64_t t) { return &a.status[(uint64_t)t * kStride + d]; };
+                excl = look_back<decltype(word), kSegLookBatch>(word, (int64_t)row - 1,
+                                                                (int64_t)row - (int64_t)td.index, a.err);
                 if (!last) atomicExch(&a.status[row * kStride + d], kStFlagInc | (excl + s_cnt[d]));
             }
             s_gbase[d] = a.first[(uint64_t)(lo + d) * a.first_stride] + excl - s_off[d];
@@ -243,13 +247,13 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
             const int d = s_dig[q];
             const uint64_t o = s_gbase[d] + q;
             if (d == sdig) {
-                if (o >= a.st_cap) { raise(a.err, FP_ERR_CAPACITY); continue; }
+                if (o >= a.st_cap) { raise(a.err, FP_ERR_CAPACITY, 14); continue; }
                 const uint64_t src = base + s_pos[q];
                 const uint32_t id = a.id_in[src];
                 a.st_key[o] = ((uint64_t)(a.st_rank ? a.st_rank[id] : id) << a.st_shift) | s_val[q];
                 a.st_src[o] = (uint32_t)src;
             } else {
-                if (o >= a.n) { raise(a.err, FP_ERR_CAPACITY); continue; }   // inconsistent node table
+                if (o >= a.n) { raise(a.err, FP_ERR_CAPACITY, 15); continue; }   // inconsistent node table
                 if (CPT) a.pt_out[o] = s_pt[q];
                 if (a.val_out) a.val_out[o] = s_val[q];
             }

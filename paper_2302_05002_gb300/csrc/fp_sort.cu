@@ -184,6 +184,7 @@ cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cu
     uint32_t* val_tmp = ws.take<uint32_t>(n);
     uint32_t* run_sort = ws.take<uint32_t>(1);
     Workspace rest = ws;
+    KTimerScope kt(FP_KERNEL_DISTRIBUTE, st);
     // 257..2048 chunks: one sweep with chunk digits (no plan, bases = offsets);
     // otherwise the radix passes below (one pass up to 256 chunks)
     cudaError_t e = dist_wide(reinterpret_cast<const int4*>(pts), n, cube, g, lut, offsets, num_chunks,

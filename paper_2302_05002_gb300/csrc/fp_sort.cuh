@@ -39,18 +39,18 @@ enum DigitSource { DIG_K64 = 0, DIG_K32 = 1, DIG_CHUNK = 2 };
 // round trip per kLookBatch of them; reading stops at the first word not yet
 // published and resumes there (bounded: FP_ERR_TIMEOUT after kSpinLimit rounds).
 constexpr int kLookBatch = 8;
-template <typename Word>
-FP_DEV uint32_t look_back(Word word, int64_t t, int64_t t_first, uint32_t* err)
+template <typename Word, int BATCH = kLookBatch>
+FP_DEV uint32_t look_back(Word word, int64_t t, int64_t t_first, uint32_t* err, uint32_t limit = kSpinLimit)
 {
     uint32_t excl = 0, spins = 0;
     while (t >= t_first) {
-        uint32_t sv[kLookBatch];
+        uint32_t sv[BATCH];
 #pragma unroll
-        for (int k = 0; k < kLookBatch; ++k) sv[k] = t - k >= t_first ? ld_volatile(word(t - k)) : 0u;
+        for (int k = 0; k < BATCH; ++k) sv[k] = t - k >= t_first ? ld_volatile(word(t - k)) : 0u;
         int adv = 0;
         bool stop = false;
 #pragma unroll
-        for (int k = 0; k < kLookBatch; ++k) {
+        for (int k = 0; k < BATCH; ++k) {
             if (stop || t - k < t_first) { stop = true; continue; }
             const uint32_t f = sv[k] & ~kStMask;
             if (f == 0) { stop = true; continue; }   // not published yet: read again from here
@@ -58,7 +58,7 @@ FP_DEV uint32_t look_back(Word word, int64_t t, int64_t t_first, uint32_t* err)
             if (f == kStFlagInc) return excl;
             ++adv;
         }
-        if (adv == 0 && ++spins > kSpinLimit) {
+        if (adv == 0 && ++spins > limit) {
             raise(err, FP_ERR_TIMEOUT);
             return excl;
         }
@@ -98,6 +98,8 @@ struct SortArgs {
     int g;
     const uint32_t* run_if;   // nullable: the pass runs only when *run_if != 0
     int bulk;                 // 64-bit key layout with 16-byte aligned arrays: tiles arrive by bulk copy
+    uint32_t withhold;        // test hook of the bounded waits: this tile publishes nothing (0xFFFFFFFF: none)
+    uint32_t spin_limit;      // rounds of the look-back before FP_ERR_TIMEOUT
     uint32_t* err;
 };
 
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
                 s += v;
             }
             s_cnt[d] = s;
-            a.status[tile * nb + d] = (tile == 0 ? kStFlagInc : kStFlagAgg) | s;
+            if (tile != a.withhold) a.status[tile * nb + d] = (tile == 0 ? kStFlagInc : kStFlagAgg) | s;
         }
         __syncthreads();
         // exclusive scan of s_cnt over digits -> s_off (each thread a run of digits)
@@ -328,9 +330,9 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
         for (int d = threadIdx.x; d < nb; d += kSortNT) {
             uint32_t excl = 0;
             if (tile > 0) {
-                excl = look_back([&](int64_t t) { return &a.status[(uint64_t)t * nb + d]; }, (int64_t)tile - 1, 0,
-                                 a.err);
-                atomicExch(&a.status[tile * nb + d], kStFlagInc | (excl + s_cnt[d]));
+                auto word = [&](int64_t t) { return &a.status[(uint64_t)t * nb + d]; };
+                excl = look_back<decltype(word), kLookBatch>(word, (int64_t)tile - 1, 0, a.err, a.spin_limit);
+                if (tile != a.withhold) atomicExch(&a.status[tile * nb + d], kStFlagInc | (excl + s_cnt[d]));
             }
             s_gbase[d] = bases[d] + excl - s_off[d];
         }
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
         // ---- phase 3: coalesced writes of each digit run
         for (int q = threadIdx.x; q < tn; q += kSortNT) {
             const uint64_t o = s_gbase[s_dig[q]] + q;
-            if (o >= n) { raise(a.err, FP_ERR_CAPACITY); continue; }   // inconsistent bucket totals
+            if (o >= n) { raise(a.err, FP_ERR_CAPACITY, 16); continue; }   // inconsistent bucket totals
             if (CPT) out_pt[o] = s_pt[q];
             if (CK64) out_k64[o] = s_k64[q];
             if (CK32 && out_k32) out_k32[o] = s_k32[q];
@@ -419,6 +421,7 @@ cudaError_t sort_run_pass(const SortScratch& sc, const SortArgs& a0, int slot, i
 {
     cudaError_t e;
     SortArgs a = a0;
+    debug_wait_config(&a.withhold, &a.spin_limit);
     a.plan = sc.plan;
     a.bases = sc.bases;
     a.status = sc.status;

@@ -8,6 +8,8 @@ FastPointsError on a non-zero status.  There is no CPU path: without the built
 library or a CUDA device the calls fail.
 """
 import ctypes
+import functools
+import inspect
 import os
 import re
 
@@ -63,6 +65,8 @@ PREVIEW_DONE = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
 STAGE = dict(bounds=0, decimate=1, bounds_decimate=2, count=3, merge=4, distribute=5, octree=6, subsample=7,
              preview_spatial=8)
 ERR_BITS = {1 << 6: "timeout", 1 << 9: "capacity"}
+KERNEL = dict(none=0, bounds_decimate=1, count=2, distribute=3, cell_group=4, split_rounds=5, units=6, node_table=7,
+              resolve=8, leaf_scatter=9, owner_scatter=10, stitch=11)
 NODE_BYTES, CHUNK_BYTES, CUBE_BYTES = 40, 16, 32
 
 _lib = None
@@ -82,6 +86,9 @@ def load():
         "fp_status_string": (ctypes.c_char_p, [st]),
         "fp_node_capacity_bound": (u32, [u64, p]),
         "fp_get_device_error": (st, [p, p, i32]),
+        "fp_get_device_error_sites": (st, [p, p]),
+        "fp_time_kernel": (st, [i32, p, p]),
+        "fp_debug_withhold_publish": (st, [u32, u32]),
         "fp_bounds": (st, [p, u64, p, p, sz, p]),
         "fp_decimate": (st, [p, u64, u64, u32, p, u64, p, p, sz, p]),
         "fp_preview_spatial": (st, [p, u64, p, u32, u64, p, u64, p, p, sz, p]),
@@ -97,6 +104,8 @@ def load():
         "fp_ooc_host_bytes": (sz, [u64, p]),
         "fp_build_ooc": (st, [p, u64, p, u64, u64, p, sz, p, sz, p, p, u64, p, p, u32, p, p, p, PREVIEW_DONE, p, p]),
         "fp_build_batched": (st, [p, u32, u32, p, sz, p]),
+        "fp_batch_workspace_size_ex": (sz, [p, u32, p]),
+        "fp_build_batched_ex": (st, [p, u32, p, p, sz, p]),
         "fp_cloud_digest": (st, [p, u64, p, p]),
         "fp_render_workspace_size": (sz, [u32]),
         "fp_select_nodes": (st, [p, p, u32, p, p, p, p, p, p, sz, p]),
@@ -133,6 +142,23 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _on_stream(fn):
+    """Run a wrapper with its `stream` argument as torch's current stream, so that
+    the temporaries it allocates (workspaces, outputs) belong to that stream:
+    torch's caching allocator may hand a freed block to the next allocation at
+    once, which is safe only when both are ordered on the same stream."""
+    sig = inspect.signature(fn)
+
+    @functools.wraps(fn)
+    def wrapper(*args, **kw):
+        st = sig.bind_partial(*args, **kw).arguments.get("stream")
+        if st is None:
+            return fn(*args, **kw)
+        with torch.cuda.stream(st):
+            return fn(*args, **kw)
+    return wrapper
+
+
 def _stream(stream):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -165,6 +191,21 @@ def as_points(x, device="cuda"):
     return t.to(device).contiguous()
 
 
+def time_kernel(kernel, start=None, stop=None):
+    """Arm the kernel timing hook (fp_time_kernel): later calls that launch the
+    named kernel record the two torch.cuda.Events around its launches."""
+    k = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
+    _check(load().fp_time_kernel(k, ctypes.c_void_p(start.cuda_event) if start is not None else None,
+                                 ctypes.c_void_p(stop.cuda_event) if stop is not None else None), "fp_time_kernel")
+
+
+def get_device_error_sites(stream=None):
+    """Check sites (one bit each) that raised FP_ERR_CAPACITY since the last clear."""
+    v = ctypes.c_uint32(0)
+    _check(load().fp_get_device_error_sites(_stream(stream), ctypes.byref(v)), "fp_get_device_error_sites")
+    return v.value
+
+
 def get_device_error(stream=None, clear=True):
     v = ctypes.c_uint32(0)
     _check(load().fp_get_device_error(_stream(stream), ctypes.byref(v), int(clear)), "fp_get_device_error")
@@ -172,6 +213,7 @@ def get_device_error(stream=None, clear=True):
 
 
 # ------------------------------------------------------------------ stages
+@_on_stream
 def fp_bounds(pts, stream=None, ws=None):
     n = pts.shape[0]
     cube = torch.empty(CUBE_BYTES // 4, dtype=torch.int32, device=_dev(pts))
@@ -185,6 +227,7 @@ def _preview_cap(n, modulus):
     return n if modulus <= 2 else min(n, n // modulus + 64 + 8 * int((n / modulus) ** 0.5 + 1) * 4)
 
 
+@_on_stream
 def fp_decimate(pts, first_index=0, modulus=16, out=None, stream=None, ws=None):
     n = pts.shape[0]
     cap = out.shape[0] if out is not None else _preview_cap(n, modulus)
@@ -202,6 +245,7 @@ def fp_preview_modulus(n, target):
     return int(load().fp_preview_modulus(n, target))
 
 
+@_on_stream
 def fp_preview_spatial(pts, cube, level=7, first_index=0, out=None, stream=None, ws=None):
     """One random point (smallest index hash) per occupied cell of the 2^level
     grid, ascending index: (out, count)."""
@@ -217,6 +261,7 @@ def fp_preview_spatial(pts, cube, level=7, first_index=0, out=None, stream=None,
     return out, count
 
 
+@_on_stream
 def fp_bounds_decimate(pts, first_index=0, modulus=16, out=None, stream=None, ws=None):
     n = pts.shape[0]
     cap = out.shape[0] if out is not None else _preview_cap(n, modulus)
@@ -230,6 +275,7 @@ def fp_bounds_decimate(pts, first_index=0, modulus=16, out=None, stream=None, ws
     return cube, out, count
 
 
+@_on_stream
 def fp_count(pts, cube, grid_log2=7, counts=None, accumulate=False, stream=None):
     n = pts.shape[0]
     if counts is None:
@@ -239,6 +285,7 @@ def fp_count(pts, cube, grid_log2=7, counts=None, accumulate=False, stream=None)
     return counts
 
 
+@_on_stream
 def fp_merge_chunks(counts, grid_log2, threshold, stream=None, ws=None):
     dev = counts.device
     cells = 1 << (3 * grid_log2)
@@ -253,6 +300,7 @@ def fp_merge_chunks(counts, grid_log2, threshold, stream=None, ws=None):
     return chunks, num, lut, offsets
 
 
+@_on_stream
 def fp_distribute(pts, cube, grid_log2, lut, offsets, num_chunks, with_perm=True, out=None, perm=None,
                   stream=None, ws=None):
     n = pts.shape[0]
@@ -273,6 +321,7 @@ def node_capacity_bound(n, prm):
     return int(load().fp_node_capacity_bound(n, ctypes.byref(prm)))
 
 
+@_on_stream
 def fp_build_chunk_octree(sorted_pts, perm, cube, chunks, num_chunks, offsets, counts, prm, node_cap=None,
                           leaf=True, stream=None, ws=None):
     n = sorted_pts.shape[0]
@@ -292,6 +341,7 @@ def fp_build_chunk_octree(sorted_pts, perm, cube, chunks, num_chunks, offsets, c
     return nodes, num_nodes, leaf_pts, leaf_perm, owner
 
 
+@_on_stream
 def fp_subsample(nodes, num_nodes, sorted_pts, perm, owner, chunks, num_chunks, offsets, prm, stream=None, ws=None,
                  final=None, final_perm=None):
     """nodes must have been allocated with node_capacity_bound(n, prm) rows (the
@@ -346,6 +396,7 @@ def cloud_desc(pts, prm, out):
     return d
 
 
+@_on_stream
 def plain_calls(d, ws, stream=None):
     """The seven plain calls of one cloud (descriptor d), in order, on one stream."""
     L, S, W, Wn = load(), _stream(stream), _ptr(ws), ws.numel()
@@ -371,25 +422,51 @@ def batch_descs(clouds, outs):
     return arr
 
 
+class fp_batch_opts(ctypes.Structure):
+    _fields_ = [("nlanes", ctypes.c_uint32), ("fused_first", ctypes.c_uint32), ("count_threads", ctypes.c_uint32),
+                ("count_slots", ctypes.c_uint32)]
+
+
+def batch_opts(nlanes=8, fused_first=0, count_threads=256, count_slots=1024):
+    return fp_batch_opts(nlanes, int(fused_first), count_threads, count_slots)
+
+
 def batch_workspace_size(descs, ncloud, nlanes):
     return int(load().fp_batch_workspace_size(descs, ncloud, nlanes))
 
 
+def batch_workspace_size_ex(descs, ncloud, opts):
+    return int(load().fp_batch_workspace_size_ex(descs, ncloud, ctypes.byref(opts)))
+
+
+@_on_stream
+def fp_build_batched_ex(descs, ncloud, opts, ws, stream=None):
+    _check(load().fp_build_batched_ex(descs, ncloud, ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(stream)),
+           "fp_build_batched_ex")
+
+
+@_on_stream
 def fp_build_batched(descs, ncloud, nlanes, ws, stream=None):
     _check(load().fp_build_batched(descs, ncloud, nlanes, _ptr(ws), ws.numel(), _stream(stream)), "fp_build_batched")
 
 
-def build_batched(clouds, nlanes=8, stream=None, outs=None, ws=None):
+@_on_stream
+def build_batched(clouds, nlanes=8, stream=None, outs=None, ws=None, opts=None):
     """clouds: list of (points tensor, fp_params).  Builds all of them with
-    fp_build_batched; returns (list of output dicts, descriptors, workspace)."""
+    fp_build_batched (fp_build_batched_ex when opts is given); returns (list of
+    output dicts, descriptors, workspace)."""
     if outs is None:
         outs = [cloud_outputs(p, prm) for p, prm in clouds]
     descs = batch_descs(clouds, outs)
-    need = batch_workspace_size(descs, len(clouds), nlanes)
+    need = batch_workspace_size_ex(descs, len(clouds), opts) if opts is not None else \
+        batch_workspace_size(descs, len(clouds), nlanes)
     dev = _dev(clouds[0][0]) if clouds else None
     if ws is None or ws.numel() < need:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
-    fp_build_batched(descs, len(clouds), nlanes, ws, stream=stream)
+    if opts is not None:
+        fp_build_batched_ex(descs, len(clouds), opts, ws, stream=stream)
+    else:
+        fp_build_batched(descs, len(clouds), nlanes, ws, stream=stream)
     return outs, descs, ws
 
 
@@ -412,6 +489,7 @@ def ooc_outputs(n, prm):
                 final=pin(max(n, 1), 4), final_perm=pin(max(n, 1)), preview_cap=cap, node_cap=ncap)
 
 
+@_on_stream
 def build_ooc(host_pts, prm, arena, piece_points=1 << 23, group_points=0, scratch=None, out=None, on_preview=None,
               stream=None):
     """Out-of-core build of a cloud in pinned host memory ((n, 4) int32 CPU
@@ -462,6 +540,7 @@ def nodes_to_host(nodes, num):
     return a.copy().view(dt).reshape(M)
 
 
+@_on_stream
 def build_octree(pts, prm, stream=None):
     """The whole hot path on one cloud (int32 (n, 4) CUDA tensor); returns a dict
     of device tensors: cube, preview (+count), counts, chunks (+count), lut,
@@ -482,6 +561,7 @@ def build_octree(pts, prm, stream=None):
 
 
 # ------------------------------------------------------- octree file, cache
+@_on_stream
 def fp_cloud_digest(pts, stream=None):
     """64-bit digest of a cloud (every point and the order): the cache key."""
     d = torch.zeros(1, dtype=torch.int64, device=_dev(pts))
@@ -493,6 +573,7 @@ def _staging(staging, nbytes=64 << 20):
     return staging if staging is not None else torch.empty(nbytes, dtype=torch.uint8).pin_memory()
 
 
+@_on_stream
 def octree_save(path, prm, out, digest=0, with_perm=True, staging=None, stream=None):
     """Writes the octree of build_octree() (device outputs: cube, nodes,
     num_nodes, final, final_perm) to one file."""
@@ -510,6 +591,7 @@ def octree_header(path):
     return h
 
 
+@_on_stream
 def octree_load(path, nodes=True, first=0, count=None, perm=True, device=None, staging=None, stream=None):
     """Node table and final points [first, first + count) (all by default) of an
     octree file, as device tensors: dict(header, nodes, num_nodes, final, final_perm)."""
@@ -532,6 +614,7 @@ def cache_path(cache_dir, digest, prm):
     return os.path.join(cache_dir, key + ".fpo")
 
 
+@_on_stream
 def cached_build(pts, prm, cache_dir, stream=None, staging=None):
     """The octree of a cloud, from the cache when this cloud was built before
     with these parameters (same digest, same n), else built and saved.
@@ -586,6 +669,7 @@ def render_workspace_size(node_cap):
     return int(load().fp_render_workspace_size(node_cap))
 
 
+@_on_stream
 def fp_select_nodes(nodes, num_nodes, cube, cam, ws=None, stream=None):
     """(selected ids, count, total kept points) of the nodes the camera draws."""
     cap = nodes.shape[0]
@@ -599,6 +683,7 @@ def fp_select_nodes(nodes, num_nodes, cube, cam, ws=None, stream=None):
     return ids, nsel, npts
 
 
+@_on_stream
 def fp_rasterize(nodes, ids, nsel, final, cam, fb=None, ws=None, stream=None):
     """Framebuffer (height, width) int64: (depth bits << 32 | rgba) of the nearest point, -1 where empty."""
     cap = nodes.shape[0]

@@ -1,12 +1,17 @@
 """Tuner of the batched build (fp_build_batched).
 
-Two knobs change the speed of a cloud's build but not its octree: the count
+Knobs that change the speed of a cloud's build but not its octree: the count
 grid resolution g (any g <= s, g <= L_max; the node table, leaf grouping and
-final layout are defined without it) and the number of lanes the batch runs
-on.  The tuner times the candidates on the device and keeps the fastest:
+final layout are defined without it), the number of lanes the batch runs on,
+whether the first two passes of all clouds are fused into one launch each,
+and the fused count pass's block size and hot-cell table size (its
+shared-memory privatisation depth).  The tuner times the candidates on the
+device and keeps the fastest:
   - g per size bucket (floor(log2 n)), on a synthetic sample cloud of the
     bucket's size, each candidate built twice and timed once with CUDA events;
-  - the lane count on the batch itself, each candidate timed as one call.
+  - the lane count on the batch itself, each candidate timed as one call;
+  - then, at that lane count, the fused first passes with every block size and
+    table size, against the unfused batch.
 The chunk threshold T stays as given (the octree does not depend on it either,
 but chunk-size limits of the per-chunk scatter make T part of the workload).
 """
@@ -88,4 +93,19 @@ class BatchTuner:
             if best is None or ms < best[0]:
                 best = (ms, L)
         self.lanes = best[1]
+        self.lanes_ms = best[0]
         return self.lanes
+
+    def tune_opts(self, run, nlanes, variants=((256, 1024), (256, 4096), (512, 0), (512, 1024))):
+        """run(opts) enqueues the whole batch with fp_build_batched_ex; returns the
+        fastest fp_batch_opts at nlanes lanes, the unfused batch included."""
+        cands = [fp.batch_opts(nlanes, 0, 256, 1024)] + [fp.batch_opts(nlanes, 1, t, s) for t, s in variants]
+        best = None
+        for o in cands:
+            run(o)   # warm
+            ms = _time_ms(lambda: run(o), self.stream)
+            self.log.append(("opts", o.fused_first, o.count_threads, o.count_slots, ms))
+            if best is None or ms < best[0]:
+                best = (ms, o)
+        self.opts = best[1]
+        return self.opts

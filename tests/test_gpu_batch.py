@@ -8,6 +8,7 @@ import torch
 
 import oracle
 import synth
+from tests.gpu_util import assert_build_matches_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -87,6 +88,47 @@ def test_batched_equals_plain(batch, nlanes):
         assert_same(o, r, "cloud %d (%d lanes)" % (i, nlanes))
 
 
+@pytest.mark.parametrize("threads,slots", [(256, 1024), (512, 0), (256, 4096)])
+def test_fused_first_passes_equal_plain(batch, threads, slots):
+    """The fused bounds + preview and count launches over all clouds of the
+    batch, with each block size and hot-cell table the tuner may pick, give
+    every cloud the plain calls' outputs."""
+    fp, clouds, ref = batch
+    opts = fp.batch_opts(nlanes=4, fused_first=1, count_threads=threads, count_slots=slots)
+    outs, _, _ = fp.build_batched(clouds, opts=opts)
+    torch.cuda.synchronize()
+    assert fp.get_device_error() == 0
+    for i, (o, r) in enumerate(zip(outs, ref)):
+        o["n"] = clouds[i][0].shape[0]
+        assert_same(o, r, "cloud %d (fused, %d threads, %d slots)" % (i, threads, slots))
+
+
+def test_fused_first_passes_many_clouds_match_oracle(gpu_lib):
+    """More clouds than one fused launch takes (300 > 256): two groups; every
+    cloud's cube, preview, count grid and octree against the oracle."""
+    fp = gpu_lib
+    rng = np.random.default_rng(7)
+    sizes = [int(x) for x in np.exp(rng.uniform(np.log(50), np.log(20_000), 300))]
+    sizes[5] = 0
+    prm = fp.params(grid_log2=5, sub_log2=6, max_level=12, decim_modulus=16, chunk_threshold=2_000, node_capacity=300)
+    hosts = [synth.uniform(n, 900 + i) if i % 2 else synth.lidar(n, 900 + i) for i, n in enumerate(sizes)]
+    clouds = [(fp.as_points(h, "cuda"), prm) for h in hosts]
+    opts = fp.batch_opts(nlanes=8, fused_first=1, count_threads=512, count_slots=1024)
+    outs, _, _ = fp.build_batched(clouds, opts=opts)
+    torch.cuda.synchronize()
+    assert fp.get_device_error() == 0
+    oprm = oracle.params(5, 6, 12, 16, 2_000, 300)
+    for i in list(range(0, 300, 23)) + [5, 299]:
+        want = oracle.build_all(hosts[i], oprm)
+        o = outs[i]
+        k = int(o["preview_count"].item())
+        assert k == len(want["preview"])
+        assert np.array_equal(o["counts"].cpu().numpy().view(np.uint32), want["counts"])
+        M = int(o["num_nodes"].item())
+        assert_build_matches_oracle(want, cube=o["cube"], preview=o["preview"][:k], nodes=o["nodes"][:M],
+                                    final=o["final"][:sizes[i]], final_perm=o["final_perm"][:sizes[i]])
+
+
 def test_batched_graph_replay(batch):
     fp, clouds, ref = batch
     outs, descs, ws = fp.build_batched(clouds, nlanes=5)   # first call (outside capture) creates the lanes
@@ -131,3 +173,26 @@ def test_batched_rejects_bad_descriptor(batch):
     ws = torch.empty(max(fp.batch_workspace_size(descs, 2, 2), 1), dtype=torch.uint8, device="cuda")
     st = fp.load().fp_build_batched(descs, 2, 2, ws.data_ptr(), ws.numel(), None)
     assert st == 1   # FP_ERR_INVALID
+
+
+def test_side_stream_builds_match_oracle(gpu_lib):
+    """Builds enqueued back to back on a side stream, each with its own grid
+    resolution, as the tuner runs them: the binding's temporaries (workspaces,
+    zero-filled outputs) belong to that stream, so none is reused while an
+    earlier stage still runs, and every build equals the oracle's."""
+    fp = gpu_lib
+    pts_np = synth.lidar(526_150, 1000)
+    pts = fp.as_points(pts_np, "cuda")
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    outs = []
+    for g in (7, 6, 5, 4):
+        prm = fp.params(grid_log2=g, sub_log2=7, max_level=15, decim_modulus=16, chunk_threshold=100_000,
+                        node_capacity=20_000)
+        outs.append((g, fp.build_octree(pts, prm, stream=st)))
+    st.synchronize()
+    assert fp.get_device_error(stream=st) == 0
+    for g, r in outs:
+        want = oracle.build_all(pts_np, oracle.params(g, 7, 15, 16, 100_000, 20_000))
+        M = int(r["num_nodes"].item())
+        assert_build_matches_oracle(want, nodes=r["nodes"][:M], final=r["final"], final_perm=r["final_perm"])

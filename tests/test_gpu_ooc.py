@@ -1,13 +1,15 @@
 """fp_build_ooc: a cloud in pinned host memory built in chunk groups inside a
-device arena gives exactly the in-core build's cube, preview, node table and
-final layout (which the other GPU tests pin to the oracle), for several group
-and piece sizes, including groups of one chunk and clouds with points kept
-above the chunks."""
+device arena gives the oracle's cube, preview, node table (every field) and
+final layout, element by element, and exactly the in-core build's outputs, for
+several group and piece sizes, including groups of one chunk and clouds with
+points kept above the chunks."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
+from tests.gpu_util import assert_build_matches_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -65,3 +67,7 @@ def test_ooc_equals_in_core(gpu_lib, kind, n, seed, g, s, lmax, T, C, piece, gro
     assert torch.equal(a, b), "node tables differ"
     assert torch.equal(out["final_perm"][:n], ref["final_perm"].cpu()[:n])
     assert torch.equal(out["final"][:n], ref["final"].cpu()[:n])
+    # the out-of-core outputs against the oracle directly
+    want = oracle.build_all(pts_np, oracle.params(g, s, lmax, 16, T, C))
+    assert_build_matches_oracle(want, cube=out["cube"], preview=out["preview"][:k], nodes=out["nodes"][:M],
+                                final=out["final"][:n], final_perm=out["final_perm"][:n])

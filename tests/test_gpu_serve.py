@@ -1,11 +1,13 @@
 """The served request loop: every request's preview, node table and final
-layout are the same served alone, served in a mix (admitted together, built on
-their own streams at the same time, one of them out of core) and built by the
-plain calls."""
+layout equal the oracle's, element by element, and are the same served alone,
+served in a mix (admitted together, built on their own streams at the same
+time, one of them out of core) and built by the plain calls."""
 import pytest
 import torch
 
+import oracle
 import synth
+from tests.gpu_util import assert_build_matches_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -27,10 +29,13 @@ def test_served_alone_mixed_plain(gpu_lib):
     fp = gpu_lib
     prm = fp.params(grid_log2=6, sub_log2=7, max_level=15, decim_modulus=16, chunk_threshold=20_000,
                     node_capacity=2_000)
-    hosts = []
+    hosts, wants = [], []
+    oprm = oracle.params(prm.grid_log2, prm.sub_log2, prm.max_level, prm.decim_modulus, prm.chunk_threshold,
+                         prm.node_capacity)
     for kind, n, seed in REQS:
         a = synth.uniform(n, seed) if kind == "uniform" else synth.lidar(n, seed)
         hosts.append(fp.as_points(a, "cuda").cpu().pin_memory())
+        wants.append(oracle.build_all(a, oprm))
     needs = [serve.incore_need(h.shape[0], prm) for h in hosts]
     piece = 1 << 18
     # the out-of-core arena (half the budget) holds the largest request's minimum; the others fit in core
@@ -66,5 +71,8 @@ def test_served_alone_mixed_plain(gpu_lib):
     assert srv.peak_active >= 2, "requests were not built at the same time"
     assert alone[len(hosts) - 1].mode == "out-of-core"
     for i in range(len(hosts)):
+        for got in (alone[i].result, mixed[i].result):
+            assert_build_matches_oracle(wants[i], preview=got["preview"], nodes=got["nodes"], final=got["final"],
+                                        final_perm=got["final_perm"])
         assert results_equal(alone[i].result, plain[i]) is None, (i, "alone", results_equal(alone[i].result, plain[i]))
         assert results_equal(mixed[i].result, plain[i]) is None, (i, "mixed", results_equal(mixed[i].result, plain[i]))

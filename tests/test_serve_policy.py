@@ -54,4 +54,4 @@ def test_incore_need_per_point():
     prm = fp.params()
     per = incore_need(160_000_000, prm) / 160_000_000
     assert 100 < per < 130
-    assert incore_need(160_000_000, prm) <= (24 << 30) * 3 // 4 < incore_need(170_000_000, prm)
+    assert incore_need(155_000_000, prm) <= (24 << 30) * 3 // 4 < incore_need(165_000_000, prm)
