@@ -962,6 +962,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true",
                     help="the default run without the batched and served summaries")
+    ap.add_argument("--quick", action="store_true",
+                    help="warm-up and timed steps only (no per-kernel times, leaf-grouped or e2e runs): "
+                         "the form the ncu captures use")
     ap.add_argument("--leaf-grouped", action="store_true",
                     help="the timed step also writes the optional leaf-grouped layout")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -1088,6 +1091,7 @@ def run_plain(args, wl, rank, world, local):
         lut=torch.empty(cells, dtype=torch.int32, device=dev),
         offsets=torch.empty(cells + 1, dtype=torch.int64, device=dev),
         dist=torch.empty_like(pts), perm=torch.empty(n, dtype=torch.int32, device=dev),
+        cells=torch.empty(n, dtype=torch.int32, device=dev),
         nodes=torch.zeros((ncap, 5), dtype=torch.int64, device=dev),
         num_nodes=torch.zeros(1, dtype=torch.int32, device=dev),
         owner=torch.empty(n, dtype=torch.int32, device=dev),
@@ -1109,12 +1113,13 @@ def run_plain(args, wl, rank, world, local):
         return [
             ("bounds_decimate", lambda: L.fp_bounds_decimate(P(src), n, P(O["cube"]), 0, 16, P(O["prev"]),
                                                              O["prev"].shape[0], P(O["prev_n"]), P(ws), ws.numel(), S)),
-            ("count", lambda: L.fp_count(P(src), n, P(O["cube"]), g, P(O["counts"]), 0, None, 0, S)),
+            ("count", lambda: L.fp_count_cells(P(src), n, P(O["cube"]), g, P(O["counts"]), 0, P(O["cells"]), None,
+                                               0, S)),
             ("merge", lambda: L.fp_merge_chunks(P(O["counts"]), g, T, P(O["chunks"]), P(O["num_chunks"]),
                                                 P(O["lut"]), P(O["offsets"]), P(ws), ws.numel(), S)),
-            ("distribute", lambda: L.fp_distribute(P(src), n, P(O["cube"]), g, P(O["lut"]), P(O["offsets"]),
-                                                   P(O["num_chunks"]), P(O["dist"]), P(O["perm"]), P(ws),
-                                                   ws.numel(), S)),
+            ("distribute", lambda: L.fp_distribute_cells(P(src), P(O["cells"]), n, P(O["cube"]), g, P(O["lut"]),
+                                                         P(O["offsets"]), P(O["num_chunks"]), P(O["dist"]),
+                                                         P(O["perm"]), P(ws), ws.numel(), S)),
             ("octree", lambda: L.fp_build_chunk_octree(P(O["dist"]), P(O["perm"]), n, P(O["cube"]), P(O["chunks"]),
                                                        P(O["num_chunks"]), P(O["offsets"]), P(O["counts"]), prm_ref,
                                                        P(O["nodes"]), ncap, P(O["num_nodes"]), lp, lpp,
@@ -1205,7 +1210,7 @@ def run_plain(args, wl, rank, world, local):
         kev[0].record(st)
         kev[1].record(st)
     kernel_ms = {}
-    for kname in [k for k in fp.KERNEL if k != "none"]:
+    for kname in ([] if args.quick else [k for k in fp.KERNEL if k != "none"]):
         vals = []
         for _ in range(args.steps):
             if flush is not None:
@@ -1223,7 +1228,7 @@ def run_plain(args, wl, rank, world, local):
 
     # the same step with the optional leaf-grouped layout (fp_build_chunk_octree's d_leaf_pts)
     leaf_ms = None
-    if leaf is None:
+    if leaf is None and not args.quick:
         leaf = dict(leaf=torch.empty_like(pts), leaf_perm=torch.empty(n, dtype=torch.int32, device=dev))
         g_leaf = capture(stage_calls(pts, True))
         with torch.cuda.stream(st):
@@ -1245,7 +1250,7 @@ def run_plain(args, wl, rank, world, local):
     nodes_host = [torch.empty_like(O["nodes"], device="cpu").pin_memory() for _ in range(2)]
     nn_host = [torch.empty(1, dtype=torch.int32).pin_memory() for _ in range(2)]
     cs = torch.cuda.Stream(dev)
-    e2e_steps = min(max(4, args.steps), 10)
+    e2e_steps = 1 if args.quick else min(max(4, args.steps), 10)
     copied = [torch.cuda.Event() for _ in range(2)]
     built = [torch.cuda.Event() for _ in range(2)]
     h2d_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
@@ -1284,6 +1289,8 @@ def run_plain(args, wl, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     med = {k: statistics.median(v) for k, v in stage_ms.items()}
+    if not kernel_ms:   # --quick: no per-kernel times, the distribution stands in
+        kernel_ms = {"distribute": statistics.median(stage_ms["distribute"])}
     dom = max(kernel_ms, key=lambda k: kernel_ms[k])
     alg = kernel_alg_bytes(dom, n)
     achieved = alg / (kernel_ms[dom] * 1e-3) / 1e9
@@ -1311,7 +1318,8 @@ def run_plain(args, wl, rank, world, local):
                        "chunk_threshold": T, "node_capacity": C, "nodes": M,
                        "chunks": int(O["num_chunks"].item()), "parallelism": "replicas" if world > 1 else "single",
                        "launch": "one CUDA graph per step",
-                       "outputs": "cube, preview, count grid, chunks, LUT, offsets, distributed points + perm, "
+                       "outputs": "cube, preview, count grid (+ each point's cell, handed to the distribution), "
+                                  "chunks, LUT, offsets, distributed points + perm, "
                                   "node table, owner per point, final LOD layout + perm" +
                                   (", leaf-grouped points + perm" if args.leaf_grouped else ""),
                        "l2": ("inputs (%.1f GB) larger than L2" % (16 * n / 1e9)) if flush is None else

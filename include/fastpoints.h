@@ -256,6 +256,13 @@ fp_status fp_count(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uin
                    uint32_t* d_counts, int accumulate,
                    void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* fp_count that also writes d_cells[i] = the level-g Morton cell of point i (n
+ * entries, required for n > 0): fp_distribute_cells then reads the cells
+ * instead of computing them from the points again. */
+fp_status fp_count_cells(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uint32_t grid_log2,
+                         uint32_t* d_counts, int accumulate, uint32_t* d_cells,
+                         void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
 /* Chunks (Fig. "octree": each chunk is a node of the global tree): sums the count
  * grid up to the root; a chunk is a node with 0 < count <= threshold whose parent
  * holds more than threshold points (or the root itself), or a level-g cell holding
@@ -275,6 +282,16 @@ fp_status fp_distribute(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube
                         const uint32_t* d_lut, const uint64_t* d_offsets, const uint32_t* d_num_chunks,
                         fp_point* d_out, uint32_t* d_perm,
                         void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* fp_distribute with the points' level-g cells given (d_cells from
+ * fp_count_cells, same cube and grid_log2): up to 2048 chunks the one-sweep
+ * scatter reads the chunk of point i as d_lut[d_cells[i]] instead of computing
+ * the cell from the point; more chunks take the radix passes, which compute it.
+ * Outputs identical to fp_distribute's. */
+fp_status fp_distribute_cells(const fp_point* d_pts, const uint32_t* d_cells, uint64_t n, const fp_cube* d_cube,
+                              uint32_t grid_log2, const uint32_t* d_lut, const uint64_t* d_offsets,
+                              const uint32_t* d_num_chunks, fp_point* d_out, uint32_t* d_perm,
+                              void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Local octrees of all chunks, stitched under the global nodes above them
  * (Sec. 4.4, Fig. "octree"), and the level-of-detail selection.

@@ -321,7 +321,21 @@ fp_status fp_count(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uin
     Workspace ws;
     fp_status s = make_ws(d_ws, ws_bytes, 0, ws);
     if (s != FP_OK) return s;
-    return cuda_status(launch_count(d_pts, n, d_cube, (int)grid_log2, d_counts, accumulate != 0, ws, stream));
+    return cuda_status(launch_count(d_pts, n, d_cube, (int)grid_log2, d_counts, accumulate != 0, nullptr, ws, stream));
+}
+
+fp_status fp_count_cells(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube, uint32_t grid_log2,
+                         uint32_t* d_counts, int accumulate, uint32_t* d_cells, void* d_ws, size_t ws_bytes,
+                         cudaStream_t stream)
+{
+    if (!d_cube || !d_counts || (n && (!d_pts || !d_cells))) return FP_ERR_INVALID;
+    if (grid_log2 < 1 || grid_log2 > 7) return FP_ERR_UNSUPPORTED;
+    if (n >= kMaxPoints) return FP_ERR_TOO_LARGE;
+    if (n && !aligned16(d_pts)) return FP_ERR_ALIGN;
+    Workspace ws;
+    fp_status s = make_ws(d_ws, ws_bytes, 0, ws);
+    if (s != FP_OK) return s;
+    return cuda_status(launch_count(d_pts, n, d_cube, (int)grid_log2, d_counts, accumulate != 0, d_cells, ws, stream));
 }
 
 // Fig. "octree": chunks are nodes of the global tree holding at most T points
@@ -357,6 +371,26 @@ fp_status fp_distribute(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube
     if (s != FP_OK) return s;
     return cuda_status(launch_distribute(d_pts, n, d_cube, (int)grid_log2, d_lut, d_offsets, d_num_chunks, d_out,
                                          d_perm, ws, stream));
+}
+
+fp_status fp_distribute_cells(const fp_point* d_pts, const uint32_t* d_cells, uint64_t n, const fp_cube* d_cube,
+                              uint32_t grid_log2, const uint32_t* d_lut, const uint64_t* d_offsets,
+                              const uint32_t* d_num_chunks, fp_point* d_out, uint32_t* d_perm, void* d_ws,
+                              size_t ws_bytes, cudaStream_t stream)
+{
+    if (!d_cube || !d_lut || !d_offsets || !d_num_chunks || (n && (!d_pts || !d_out || !d_cells)))
+        return FP_ERR_INVALID;
+    if (grid_log2 < 1 || grid_log2 > 7) return FP_ERR_UNSUPPORTED;
+    if (n >= kMaxPoints) return FP_ERR_TOO_LARGE;
+    if (n && (!aligned16(d_pts) || !aligned16(d_out))) return FP_ERR_ALIGN;
+    if (n && d_pts == d_out) return FP_ERR_INVALID;
+    Workspace ws;
+    fp_params p{};
+    p.grid_log2 = grid_log2;
+    fp_status s = make_ws(d_ws, ws_bytes, fp_workspace_size(FP_STAGE_DISTRIBUTE, n, &p), ws);
+    if (s != FP_OK) return s;
+    return cuda_status(launch_distribute(d_pts, n, d_cube, (int)grid_log2, d_lut, d_offsets, d_num_chunks, d_out,
+                                         d_perm, ws, stream, d_cells));
 }
 
 // Sec. 4.4 / Fig. "octree": local octrees of the chunks, stitched, and LOD selection

@@ -245,9 +245,11 @@ __global__ void k_put_at(uint64_t* a, const uint32_t* idx, const uint64_t* val) 
 // in the tables and stop contending for the same global counters.
 constexpr int kCountSlots = 1024;
 
+// cells (nullable): the level-g Morton cell of every point, for fp_distribute_cells
 template <bool AGG>
 __global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts, uint64_t n,
-                                               const fp_cube* __restrict__ cube, int g, uint32_t* __restrict__ counts)
+                                               const fp_cube* __restrict__ cube, int g, uint32_t* __restrict__ counts,
+                                               uint32_t* __restrict__ cells)
 {
     __shared__ uint32_t s_tag[kCountSlots], s_cnt[kCountSlots];
     for (int q = threadIdx.x; q < kCountSlots; q += blockDim.x) { s_tag[q] = kNone; s_cnt[q] = 0; }
@@ -265,6 +267,7 @@ __global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts,
             if (i < n) {
                 int4 p = ld_point_cs(pts, i);
                 key[u] = key_small(p.x, p.y, p.z, c, sg, g);
+                if (cells) cells[i] = key[u];
             }
         }
 #pragma unroll
@@ -612,18 +615,18 @@ cudaError_t launch_preview_spatial(const fp_point* pts, uint64_t n, const fp_cub
 }
 
 cudaError_t launch_count(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, uint32_t* counts,
-                         bool accumulate, const Workspace& ws, cudaStream_t st)
+                         bool accumulate, uint32_t* cells, const Workspace& ws, cudaStream_t st)
 {
-    uint64_t cells = 1ull << (3 * g);
+    const uint64_t ncell = 1ull << (3 * g);
     if (!accumulate) {
-        cudaError_t e = cudaMemsetAsync(counts, 0, cells * sizeof(uint32_t), st);
+        cudaError_t e = cudaMemsetAsync(counts, 0, ncell * sizeof(uint32_t), st);
         if (e) return e;
     }
     if (n == 0) return cudaSuccess;
     uint64_t want = (n + 1023) / 1024;
     int grid = (int)std::min<uint64_t>(want, (uint64_t)ws.num_sms * 8);
     KTimerScope kt(FP_KERNEL_COUNT, st);
-    k_count<true><<<grid, 256, 0, st>>>(pts, n, cube, g, counts);
+    k_count<true><<<grid, 256, 0, st>>>(pts, n, cube, g, counts, cells);
     return cudaGetLastError();
 }
 

@@ -70,7 +70,7 @@ cudaError_t launch_preview_spatial(const fp_point* pts, uint64_t n, const fp_cub
                                    fp_point* out, uint64_t out_cap, uint64_t* out_count, const Workspace& ws,
                                    cudaStream_t st);
 cudaError_t launch_count(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, uint32_t* counts,
-                         bool accumulate, const Workspace& ws, cudaStream_t st);
+                         bool accumulate, uint32_t* cells, const Workspace& ws, cudaStream_t st);
 size_t merge_ws_bytes(int g);
 cudaError_t launch_merge(const uint32_t* counts, int g, uint64_t T, fp_chunk* chunks, uint32_t* num_chunks,
                          uint32_t* lut, uint64_t* offsets, const Workspace& ws, cudaStream_t st);
@@ -79,7 +79,7 @@ cudaError_t launch_merge(const uint32_t* counts, int g, uint64_t T, fp_chunk* ch
 size_t distribute_ws_bytes(uint64_t n, int g);
 cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
                               const uint64_t* offsets, const uint32_t* num_chunks, fp_point* out, uint32_t* perm,
-                              const Workspace& ws, cudaStream_t st);
+                              const Workspace& ws, cudaStream_t st, const uint32_t* cells = nullptr);
 
 // fp_octree.cu
 size_t octree_ws_bytes(uint64_t n, const fp_params& p);

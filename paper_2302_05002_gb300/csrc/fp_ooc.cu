@@ -530,7 +530,7 @@ fp_status build(const fp_point* h_pts, uint64_t n, const fp_params& prm, uint64_
     // ---- pass 2: counts; chunks
     auto count_piece = [&](uint64_t k, const fp_point* p, uint64_t np) -> cudaError_t {
         ws.used = 0;
-        return launch_count(p, np, F.cube, g, F.counts, k > 0, ws, st);
+        return launch_count(p, np, F.cube, g, F.counts, k > 0, nullptr, ws, st);
     };
     e = raw ? io.pass_raw(count_piece) : io.pass(count_piece);
     if (e) return cu(e);

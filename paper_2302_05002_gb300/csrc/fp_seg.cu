@@ -206,7 +206,7 @@ size_t dist_wide_bytes(uint64_t n)
 
 cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
                       const uint64_t* offsets, const uint32_t* num_chunks, int4* out, uint32_t* perm,
-                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st)
+                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st, const uint32_t* cells)
 {
     const DistScratch d = dist_carve(ws, n);
     const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((d.ntiles + 255) / 256, (uint64_t)ws.num_sms * 4));
@@ -226,7 +226,7 @@ cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, c
     a.n = n;
     a.d_fail = d.cnt + 2;
     a.err = ws.err;
-    a.cube = cube; a.lut = lut; a.g = g;
+    a.cube = cube; a.lut = lut; a.cells = cells; a.g = g;
     cudaError_t e;
     a.d_ntiles = d.cnt; a.counter = d.cnt + 1;
     if ((e = dist_launch<kDistMidBits>(a, d.ntiles, ws.num_sms, st))) return e;

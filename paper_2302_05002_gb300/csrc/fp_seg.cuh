@@ -64,6 +64,7 @@ struct SegArgs {
     // distribution (DIST): the digit is the chunk of the point's level-g cell
     const fp_cube* cube;
     const uint32_t* lut;
+    const uint32_t* cells;                // nullable: the level-g cell of every point (else computed)
     int g;
 };
 
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
     if (*a.d_fail) return;
     CubeDev cube;
     float scale_g = 0.f;
-    if (DIST) {
+    if (DIST && !a.cells) {
         cube = load_cube(a.cube);
         scale_g = scale_at(cube, a.g);
     }
@@ -146,8 +147,12 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
             if (DIST) {
                 uint32_t cell = 0;
                 if (p < tn) {
-                    const int4 q = __ldg(a.pt_in + base + p);
-                    cell = key_small(q.x, q.y, q.z, cube, scale_g, a.g);
+                    if (a.cells) {
+                        cell = __ldg(a.cells + base + p);
+                    } else {
+                        const int4 q = __ldg(a.pt_in + base + p);
+                        cell = key_small(q.x, q.y, q.z, cube, scale_g, a.g);
+                    }
                 }
                 dg[r] = cell;
             } else {
@@ -302,7 +307,7 @@ struct SegCall {
 size_t dist_wide_bytes(uint64_t n);
 cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
                       const uint64_t* offsets, const uint32_t* num_chunks, int4* out, uint32_t* perm,
-                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st);
+                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st, const uint32_t* cells = nullptr);
 
 // Setup (chunk node ids, digits, tiles), status reset, both pass variants.
 // Afterwards cnt[2] != 0 means a chunk did not fit (the caller's whole-array

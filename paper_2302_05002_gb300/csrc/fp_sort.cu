@@ -176,7 +176,7 @@ size_t distribute_ws_bytes(uint64_t n, int g)
 
 cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
                               const uint64_t* offsets, const uint32_t* num_chunks, fp_point* out, uint32_t* perm,
-                              const Workspace& ws, cudaStream_t st)
+                              const Workspace& ws, cudaStream_t st, const uint32_t* cells)
 {
     if (n == 0) return cudaSuccess;
     SortScratch sc = take_sort_scratch(ws, n);
@@ -185,10 +185,11 @@ cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cu
     uint32_t* run_sort = ws.take<uint32_t>(1);
     Workspace rest = ws;
     KTimerScope kt(FP_KERNEL_DISTRIBUTE, st);
-    // 257..2048 chunks: one sweep with chunk digits (no plan, bases = offsets);
-    // otherwise the radix passes below (one pass up to 256 chunks)
+    // 257..2048 chunks: one sweep with chunk digits (no plan, bases = offsets; the
+    // cells, when given, read instead of computed); otherwise the radix passes
+    // below (one pass up to 256 chunks), which compute the cells from the points
     cudaError_t e = dist_wide(reinterpret_cast<const int4*>(pts), n, cube, g, lut, offsets, num_chunks,
-                              reinterpret_cast<int4*>(out), perm, run_sort, rest, st);
+                              reinterpret_cast<int4*>(out), perm, run_sort, rest, st, cells);
     if (e) return e;
     // bucket weights = chunk counts (offsets[c+1] - offsets[c])
     if ((e = sort_plan_weights(sc, nullptr, offsets, num_chunks, 1ull << (3 * g), 0, st))) return e;

@@ -95,6 +95,8 @@ def load():
         "fp_preview_modulus": (u32, [u64, u64]),
         "fp_bounds_decimate": (st, [p, u64, p, u64, u32, p, u64, p, p, sz, p]),
         "fp_count": (st, [p, u64, p, u32, p, i32, p, sz, p]),
+        "fp_count_cells": (st, [p, u64, p, u32, p, i32, p, p, sz, p]),
+        "fp_distribute_cells": (st, [p, p, u64, p, u32, p, p, p, p, p, p, sz, p]),
         "fp_merge_chunks": (st, [p, u32, u64, p, p, p, p, p, sz, p]),
         "fp_distribute": (st, [p, u64, p, u32, p, p, p, p, p, p, sz, p]),
         "fp_build_chunk_octree": (st, [p, p, u64, p, p, p, p, p, p, p, u32, p, p, p, p, p, sz, p]),
@@ -286,6 +288,19 @@ def fp_count(pts, cube, grid_log2=7, counts=None, accumulate=False, stream=None)
 
 
 @_on_stream
+def fp_count_cells(pts, cube, grid_log2=7, counts=None, cells=None, accumulate=False, stream=None):
+    """fp_count that also returns every point's level-g Morton cell."""
+    n = pts.shape[0]
+    if counts is None:
+        counts = torch.empty(1 << (3 * grid_log2), dtype=torch.int32, device=_dev(pts))
+    if cells is None:
+        cells = torch.empty(max(n, 1), dtype=torch.int32, device=_dev(pts))
+    _check(load().fp_count_cells(_ptr(pts), n, _ptr(cube), grid_log2, _ptr(counts), int(accumulate), _ptr(cells),
+                                 None, 0, _stream(stream)), "fp_count_cells")
+    return counts, cells
+
+
+@_on_stream
 def fp_merge_chunks(counts, grid_log2, threshold, stream=None, ws=None):
     dev = counts.device
     cells = 1 << (3 * grid_log2)
@@ -314,6 +329,24 @@ def fp_distribute(pts, cube, grid_log2, lut, offsets, num_chunks, with_perm=True
     _check(load().fp_distribute(_ptr(pts), n, _ptr(cube), grid_log2, _ptr(lut), _ptr(offsets), _ptr(num_chunks),
                                 _ptr(out), _ptr(perm) if with_perm else None, _ptr(w), w.numel(), _stream(stream)),
            "fp_distribute")
+    return out, perm
+
+
+@_on_stream
+def fp_distribute_cells(pts, cells, cube, grid_log2, lut, offsets, num_chunks, with_perm=True, out=None, perm=None,
+                        stream=None, ws=None):
+    """fp_distribute with the cells of fp_count_cells."""
+    n = pts.shape[0]
+    dev = _dev(pts)
+    if out is None:
+        out = torch.empty_like(pts)
+    if with_perm and perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+    prm = params(grid_log2=grid_log2)
+    w, need = _ws("distribute", n, prm, dev, ws)
+    _check(load().fp_distribute_cells(_ptr(pts), _ptr(cells), n, _ptr(cube), grid_log2, _ptr(lut), _ptr(offsets),
+                                      _ptr(num_chunks), _ptr(out), _ptr(perm) if with_perm else None, _ptr(w),
+                                      w.numel(), _stream(stream)), "fp_distribute_cells")
     return out, perm
 
 

@@ -8,9 +8,9 @@ memory budget:
     in-core ones: it is long and bound by the host link, so in-core builds
     overlap it), so requests that arrive while others run are built alongside
     them (each on its own CUDA stream; their kernels overlap on the device).
-    In-core builds of `big_points` or more fill the GPU alone and run one at a
-    time (two at once only compete for bandwidth and L2); smaller ones overlap
-    freely;
+    In-core builds of `big_points` or more fill most of the GPU and at most
+    `big_slots` of them run at a time; smaller ones overlap freely; a request
+    passed over `max_bypass` times blocks later admissions until it fits;
   - a cloud whose in-core need exceeds three quarters of the budget is built
     out of core (fp_build_ooc) in an arena of half the budget;
   - in-core requests stream their points in pieces with cudaMemcpyAsync on a
@@ -62,15 +62,28 @@ def incore_need(n, prm):
             16 * fp._preview_cap(n, prm.decim_modulus) + (64 << 20))
 
 
-def pick_request(queue, free, ooc_slot_free, big_points, big_active):
+def pick_request(queue, free, ooc_slot_free, big_points, big_active, big_slots=1, max_bypass=None):
     """The request the loop admits next, or None.  A request fits when its device
     need fits in the free budget and, out of core, a host slot is free, or, in
-    core, it is smaller than big_points or no other such build is running.  Of
-    those, a waiting out-of-core request goes first (long and bound by the host
-    link, so in-core builds overlap it), else the first in arrival order."""
-    fits = [r for r in queue if r.need <= free and
-            (ooc_slot_free if r.mode == "out-of-core" else (r.n < big_points or big_active == 0))]
-    return next((r for r in fits if r.mode == "out-of-core"), fits[0] if fits else None)
+    core, it is smaller than big_points or fewer than big_slots such builds are
+    running.  Of those, a waiting out-of-core request goes first (long and bound
+    by the host link, so in-core builds overlap it), else the first in arrival
+    order.  Aging: once the oldest waiting request has been passed over
+    max_bypass times (requests behind it admitted while it did not fit), nothing
+    else is admitted until it fits, so a large request cannot wait forever
+    behind a stream of small ones."""
+    if not queue:
+        return None
+    head = queue[0]
+
+    def fits(r):
+        return r.need <= free and (ooc_slot_free if r.mode == "out-of-core" else
+                                   (r.n < big_points or big_active < big_slots))
+
+    if max_bypass is not None and getattr(head, "bypassed", 0) >= max_bypass:
+        return head if fits(head) else None
+    ok = [r for r in queue if fits(r)]
+    return next((r for r in ok if r.mode == "out-of-core"), ok[0] if ok else None)
 
 
 def _preview_slot_cap(p, m):
@@ -84,9 +97,11 @@ def preview_slots_shape(n, piece, m):
 
 class Server:
     def __init__(self, budget_bytes=24 << 30, piece_points=1 << 23, device=0, ooc_max_points=0, ooc_prm=None,
-                 ooc_slots=1, big_points=1 << 24):
+                 ooc_slots=1, big_points=1 << 24, big_slots=2, max_bypass=8):
         self.budget = budget_bytes
-        self.big_points = big_points   # in-core builds this large fill the GPU alone: one at a time
+        self.big_points = big_points   # in-core builds this large fill the GPU: at most big_slots at a time
+        self.big_slots = big_slots
+        self.max_bypass = max_bypass   # aging bound of the admission (see pick_request)
         self.big_active = 0
         self.free = budget_bytes
         self.piece = piece_points
@@ -125,10 +140,14 @@ class Server:
                     if self._stop and not self.queue:
                         return
                     pick = pick_request(self.queue, self.free, bool(self.ooc_free), self.big_points,
-                                        self.big_active)
+                                        self.big_active, self.big_slots, self.max_bypass)
                     if pick is not None:
                         break
                     self.cv.wait()
+                for r in self.queue:   # passed over by a later arrival
+                    if r is pick:
+                        break
+                    r.bypassed = getattr(r, "bypassed", 0) + 1
                 self.queue.remove(pick)
                 self.free -= pick.need
                 if pick.mode == "out-of-core":

@@ -77,6 +77,19 @@ def test_stages_match_oracle(gpu_lib, kind, n, seed, g, T):
     assert_points_equal(out, want_out)
     out2, _ = fp.fp_distribute(pts, cube, g, lut, offsets, num, with_perm=False)
     assert_points_equal(out2, want_out)
+    # the same two stages with the cells handed from the count to the distribution
+    counts3, cells = fp.fp_count_cells(pts, cube, g)
+    assert np.array_equal(counts3.cpu().numpy().view(np.uint32), want_counts)
+    got_cells = cells[:n].cpu().numpy().view(np.uint32)
+    if n <= 400_000:   # the oracle's cell of every point
+        assert np.array_equal(got_cells, oracle.point_keys(pts_np, want_cube, g).astype(np.uint32))
+    else:              # every cell as often as the oracle counts it
+        assert np.array_equal(np.bincount(got_cells, minlength=1 << (3 * g)), want_counts)
+    out4, perm4 = fp.fp_distribute_cells(pts, cells, cube, g, lut, offsets, num)
+    assert np.array_equal(perm4.cpu().numpy().view(np.uint32), want_perm)
+    assert_points_equal(out4, want_out)
+    out5, _ = fp.fp_distribute_cells(pts, cells, cube, g, lut, offsets, num, with_perm=False)
+    assert_points_equal(out5, want_out)
     assert fp.get_device_error() == 0
 
 

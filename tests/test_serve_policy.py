@@ -13,8 +13,8 @@ def req(name, need, mode="in-core", n=1_000_000):
 BIG = 1 << 24
 
 
-def pick(queue, free=100, ooc=True, big_active=0):
-    r = pick_request(queue, free, ooc, BIG, big_active)
+def pick(queue, free=100, ooc=True, big_active=0, big_slots=1, max_bypass=None):
+    r = pick_request(queue, free, ooc, BIG, big_active, big_slots, max_bypass)
     return None if r is None else r.name
 
 
@@ -55,3 +55,19 @@ def test_incore_need_per_point():
     per = incore_need(160_000_000, prm) / 160_000_000
     assert 100 < per < 130
     assert incore_need(155_000_000, prm) <= (24 << 30) * 3 // 4 < incore_need(165_000_000, prm)
+
+
+def test_large_in_core_builds_up_to_the_slots():
+    q = [req("big", 10, n=BIG), req("small", 10, n=BIG - 1)]
+    assert pick(q, big_active=1, big_slots=2) == "big"    # a second large build may start
+    assert pick(q, big_active=2, big_slots=2) == "small"
+
+
+def test_aging_stops_bypassing_the_oldest_request():
+    big = req("big", 150)
+    q = [big, req("s1", 10), req("s2", 10)]
+    assert pick(q, max_bypass=2) == "s1"        # the oldest does not fit: a later one starts
+    big.bypassed = 2                            # passed over twice: nothing else starts ...
+    assert pick(q, max_bypass=2) is None
+    assert pick(q, free=150, max_bypass=2) == "big"   # ... until it fits
+    assert pick(q, max_bypass=None) == "s1"     # no aging bound: first fit as before
