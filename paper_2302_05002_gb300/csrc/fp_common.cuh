@@ -143,6 +143,22 @@ FP_DEV uint32_t lanemask_lt()
     return m;
 }
 
+// Lanes of the warp holding the same BITS-bit value v as this lane, among the
+// lanes with `valid` set (one ballot per bit: the cost does not grow with the
+// number of distinct values in the warp).  All 32 lanes take part.
+template <int BITS>
+FP_DEV uint32_t match_bits(uint32_t v, bool valid)
+{
+    uint32_t peers = __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (v >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
 // volatile load for inter-block flags
 FP_DEV uint32_t ld_volatile(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 

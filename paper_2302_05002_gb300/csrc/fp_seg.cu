@@ -133,16 +133,316 @@ static cudaError_t seg_launch(SegArgs a, const SegScratch& sc, int v, int num_sm
     return cudaGetLastError();
 }
 
-// ------------------------------------------------ distribution in one sweep
-// one segment [0, n) with K digits when 256 < K <= 2048: its tiles, the
-// segment bounds, and the flag that gates the radix passes
-constexpr int kDistMidBits = 9;   // up to 512 chunks: two CTAs per SM
+// ---- the distribution with each point's cell given, up to 512 chunks, in four
+// launches and without any wait between blocks:
+//   k_dist_table: per node of level L = min(g, 5), its chunk when every
+//     occupied cell of the node lies in that one chunk (else none) -- a 64 KB
+//     table that spares most points the gather of the cell -> chunk table;
+//   k_dist_count: one block per group of kDistGroup consecutive tiles writes
+//     every point's chunk, and per tile the points of each chunk in the group's
+//     earlier tiles, and per group its totals;
+//   k_dist_colscan: per chunk, the exclusive prefix of the group totals plus the
+//     chunk's offset -- each group's output start in every chunk;
+//   k_dist_sweep: one CTA of 1024 threads per SM; tiles taken in order from a
+//     counter.  The points and chunks of the next tile arrive by bulk copy in
+//     the second buffer while the current tile is worked on; a tile stages only
+//     (tile position, chunk) per output slot, and its write phase reads every
+//     point from the tile buffer.  A tile's run of chunk d starts at its group's
+//     start in d plus the points of d in the group's earlier tiles.
+constexpr int kDistNT = 1024;
+constexpr int kDistIPT = kSortTile / kDistNT;
+constexpr int kDistWarps = kDistNT / 32;
+constexpr int kDistBits = 9;
+constexpr int kDistDig = 1 << kDistBits;
+constexpr int kDistGroup = 64;                  // tiles per block of k_dist_count
+constexpr int kDistCountNT = kDistDig;          // thread d of k_dist_count owns chunk d
+constexpr int kDistCountIPT = kSortTile / kDistCountNT;
+constexpr int kDistTabLevel = 5;                // level of the node -> chunk table
+constexpr uint16_t kDistSplit = 0xFFFFu;        // the node's points lie in several chunks
 
-__global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint64_t* seg_off, uint32_t* seg_lo,
-                             uint32_t* seg_nb, SegTile* tiles, uint32_t* cnt, uint32_t* run_sort)
+struct DistSweepArgs {
+    const int4* pts;
+    const uint32_t* cells;      // level-g cell of every point
+    const uint32_t* lut;        // cell -> chunk (kNone: empty cell)
+    const uint64_t* offsets;    // chunk c = output positions [offsets[c], offsets[c + 1])
+    int4* out;
+    uint32_t* perm;             // nullable
+    uint16_t* tab;              // [8^tl]: chunk of a level-tl node, or kDistSplit
+    uint16_t* chunk;            // chunk of every point, 16-byte aligned
+    uint32_t* before;           // [tile][kDistDig]: points of the chunk in the group's earlier tiles
+    uint32_t* gstart;           // [group][kDistDig]: group totals, then the group's start in the chunk
+    uint32_t* counter;
+    const uint32_t* d_ntiles;   // tiles of this sweep (0: another path runs)
+    uint64_t ntiles_max;
+    const uint32_t* nb;         // chunks (1 .. kDistDig)
+    uint64_t n;
+    uint32_t ncell;             // cells of the grid (bound of a cell id)
+    int g, tl;                  // grid level, table level (tl <= g)
+    uint32_t* err;
+};
+
+// one warp per level-tl node: the chunks of its occupied cells
+__global__ void k_dist_table(DistSweepArgs a)
+{
+    const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
+    if (ntiles == 0) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= (1u << (3 * a.tl))) return;
+    const uint32_t span = 1u << (3 * (a.g - a.tl)), lo = k * span;
+    uint32_t cmin = kNone, cmax = 0;
+    for (uint32_t q = lane; q < span; q += 32) {
+        const uint32_t c = __ldg(a.lut + lo + q);
+        if (c != kNone) { cmin = min(cmin, c); cmax = max(cmax, c); }
+    }
+    cmin = __reduce_min_sync(0xFFFFFFFFu, cmin);
+    cmax = __reduce_max_sync(0xFFFFFFFFu, cmax);
+    if (lane == 0) a.tab[k] = (cmin == cmax && cmin < (uint32_t)kDistDig) ? (uint16_t)cmin : kDistSplit;
+}
+
+__global__ void __launch_bounds__(kDistCountNT) k_dist_count(DistSweepArgs a)
+{
+    extern __shared__ __align__(16) uint16_t dist_tab[];   // 8^tl entries
+    __shared__ uint32_t h[kDistDig];
+    const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
+    if (ntiles == 0) return;
+    const uint64_t ngroups = (ntiles + kDistGroup - 1) / kDistGroup;
+    const uint32_t nb = min(*a.nb, (uint32_t)kDistDig);
+    const uint32_t d = threadIdx.x;
+    const int tsh = 3 * (a.g - a.tl);
+    {
+        const uint32_t nt4 = (1u << (3 * a.tl)) / 8;   // uint4 words of the table (8^tl >= 8 when tl >= 1)
+        if (a.tl >= 1) {
+            for (uint32_t q = d; q < nt4; q += kDistCountNT)
+                reinterpret_cast<uint4*>(dist_tab)[q] = __ldg(reinterpret_cast<const uint4*>(a.tab) + q);
+        } else if (d == 0) {
+            dist_tab[0] = a.tab[0];
+        }
+    }
+    for (uint64_t gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
+        const uint64_t t0 = gi * kDistGroup, t1 = min(ntiles, t0 + kDistGroup);
+        uint32_t run = 0;
+        h[d] = 0;
+        // the cells of the next tile are loaded while the current one is counted
+        uint32_t c[kDistCountIPT];
+        auto load = [&](uint64_t t) {
+            const uint64_t base = t * kSortTile;
+#pragma unroll
+            for (int r = 0; r < kDistCountIPT; ++r) {
+                const uint64_t i = base + (uint64_t)r * kDistCountNT + d;
+                c[r] = i < a.n ? __ldg(a.cells + i) : kNone;
+            }
+        };
+        load(t0);
+        __syncthreads();   // (also: the table is in shared memory)
+        for (uint64_t t = t0; t < t1; ++t) {
+            uint32_t k[kDistCountIPT];
+#pragma unroll
+            for (int r = 0; r < kDistCountIPT; ++r) {
+                k[r] = c[r];
+                if (k[r] != kNone && k[r] >= a.ncell) { raise(a.err, FP_ERR_CAPACITY, 19); k[r] = 0; }
+            }
+            if (t + 1 < t1) load(t + 1);
+#pragma unroll
+            for (int r = 0; r < kDistCountIPT; ++r)   // the table, else the gather
+                if (k[r] != kNone) {
+                    const uint16_t v = dist_tab[k[r] >> tsh];
+                    k[r] = v != kDistSplit ? (uint32_t)v : __ldg(a.lut + k[r]);
+                }
+            const uint64_t base = t * kSortTile;
+#pragma unroll
+            for (int r = 0; r < kDistCountIPT; ++r)
+                if (k[r] != kNone) {
+                    if (k[r] >= nb) { raise(a.err, FP_ERR_CAPACITY, 13); k[r] = nb - 1; }   // not a chunk
+                    a.chunk[base + (uint64_t)r * kDistCountNT + d] = (uint16_t)k[r];
+                    atomicAdd(&h[k[r]], 1u);
+                }
+            __syncthreads();
+            if (d < nb) {
+                a.before[t * kDistDig + d] = run;
+                run += h[d];
+            }
+            h[d] = 0;
+            __syncthreads();
+        }
+        if (d < nb) a.gstart[gi * kDistDig + d] = run;
+    }
+}
+
+// one warp per chunk: exclusive prefix of the group totals, plus the chunk's offset
+__global__ void k_dist_colscan(DistSweepArgs a)
+{
+    const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
+    const uint64_t ngroups = (ntiles + kDistGroup - 1) / kDistGroup;
+    const uint32_t nb = min(*a.nb, (uint32_t)kDistDig);
+    const int lane = threadIdx.x & 31;
+    const uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (d >= nb || ngroups == 0) return;
+    uint32_t run = (uint32_t)a.offsets[d];
+    for (uint64_t g0 = 0; g0 < ngroups; g0 += 32) {
+        const uint64_t gi = g0 + lane;
+        const uint32_t v = gi < ngroups ? a.gstart[gi * kDistDig + d] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (gi < ngroups) a.gstart[gi * kDistDig + d] = run + x - v;
+        run += __shfl_sync(0xFFFFFFFFu, x, 31);
+    }
+}
+
+struct DistSmem {
+    int4 raw[2][kSortTile];                 // the tile's points, as stored
+    uint16_t chk[2][kSortTile];             // and their chunks
+    uint32_t slot[kSortTile];               // by output slot: tile position | chunk << 16
+    uint16_t whist[kDistWarps][kDistDig];   // per-warp counts, then exclusive prefixes over the warps
+    uint32_t gbase[kDistDig];               // output position of slot 0 of every chunk's run
+    uint32_t cnt[kDistDig];
+    uint32_t scan[kDistWarps];
+    uint32_t tile[2];
+    uint64_t bar[2];
+};
+
+__global__ void __launch_bounds__(kDistNT, 1) k_dist_sweep(DistSweepArgs a)
+{
+    extern __shared__ __align__(128) unsigned char dist_smem[];
+    DistSmem& S = *reinterpret_cast<DistSmem*>(dist_smem);
+    const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
+    if (ntiles == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t n = a.n;
+    const int nb = (int)min(*a.nb, (uint32_t)kDistDig);
+    // a full tile by bulk copy into buffer b (thread 0); a partial one is loaded by the threads
+    auto issue = [&](uint64_t t, int b) {
+        const uint64_t base = t * kSortTile;
+        if (base + kSortTile > n) return;
+        fence_async_smem();
+        mbar_expect_tx(&S.bar[b], kSortTile * (uint32_t)(sizeof(int4) + sizeof(uint16_t)));
+        bulk_g2s(S.raw[b], a.pts + base, kSortTile * (uint32_t)sizeof(int4), &S.bar[b]);
+        bulk_g2s(S.chk[b], a.chunk + base, kSortTile * (uint32_t)sizeof(uint16_t), &S.bar[b]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        const uint32_t t0 = atomicAdd(a.counter, 1u);
+        S.tile[0] = t0;
+        if (t0 < ntiles) issue(t0, 0);
+    }
+    __syncthreads();
+    uint32_t phase = 0;   // bit b: parity of buffer b's next completion
+    for (int it = 0;; ++it) {
+        const int b = it & 1;
+        const uint64_t tile = S.tile[b];
+        if (tile >= ntiles) break;
+        // the next tile is claimed now and its copy issued after the ranking,
+        // so that no warp waits on the claim's round trip
+        uint32_t nx = 0;
+        if (threadIdx.x == 0) nx = atomicAdd(a.counter, 1u);
+        // this tile's start in every chunk, in flight during the ranking
+        uint32_t start = 0;
+        if (threadIdx.x < (unsigned)nb)
+            start = __ldg(a.gstart + (tile / kDistGroup) * kDistDig + threadIdx.x) +
+                    __ldg(a.before + tile * kDistDig + threadIdx.x);
+        const uint64_t base = tile * kSortTile;
+        const int tn = (int)(n - base < (uint64_t)kSortTile ? n - base : (uint64_t)kSortTile);
+        if (tn == kSortTile) {
+            if (!mbar_wait(&S.bar[b], (phase >> b) & 1u)) {
+                raise(a.err, FP_ERR_TIMEOUT);
+                mbar_wait(&S.bar[b], (phase >> b) & 1u);   // the copy in flight, once more (bounded)
+            }
+            phase ^= 1u << b;
+        } else {
+            for (int p = threadIdx.x; p < tn; p += kDistNT) {
+                S.raw[b][p] = __ldg(a.pts + base + p);
+                S.chk[b][p] = a.chunk[base + p];
+            }
+        }
+        for (int q = threadIdx.x; q < kDistWarps * kDistDig / 8; q += kDistNT)
+            reinterpret_cast<uint4*>(&S.whist[0][0])[q] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+
+        // ---- in-warp stable ranks of the chunks (checked below nb by k_dist_count)
+        uint32_t pack[kDistIPT];
+#pragma unroll
+        for (int r = 0; r < kDistIPT; ++r) {
+            const int p = warp * (kDistIPT * 32) + r * 32 + lane;
+            uint32_t d = p < tn ? (uint32_t)S.chk[b][p] : 0xFFFFu;
+            if (d != 0xFFFFu && d >= (uint32_t)nb) d = (uint32_t)(nb - 1);
+            const uint32_t peers = match_bits<kDistBits>(d, d != 0xFFFFu);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader && d != 0xFFFFu) {
+                old = S.whist[warp][d];
+                S.whist[warp][d] = (uint16_t)(old + __popc(peers));
+            }
+            old = __shfl_sync(0xFFFFFFFFu, old, leader);
+            pack[r] = d | ((old + __popc(peers & lanemask_lt())) << 16);
+            __syncwarp();
+        }
+        if (threadIdx.x == 0) {   // buffer b ^ 1 was released by the last tile's closing barrier
+            S.tile[b ^ 1] = nx;
+            if (nx < ntiles) issue(nx, b ^ 1);
+        }
+        __syncthreads();
+        // ---- per-chunk totals and per-warp exclusive prefixes
+        for (int d = threadIdx.x; d < nb; d += kDistNT) {
+            uint32_t s = 0;
+#pragma unroll 8
+            for (int w = 0; w < kDistWarps; ++w) {
+                const uint32_t v = S.whist[w][d];
+                S.whist[w][d] = (uint16_t)s;
+                s += v;
+            }
+            S.cnt[d] = s;
+        }
+        __syncthreads();
+        {   // first slot of every chunk's run; output position of its slot 0
+            uint32_t tot;
+            const uint32_t c = threadIdx.x < (unsigned)nb ? S.cnt[threadIdx.x] : 0u;
+            const uint32_t ex = block_exclusive_scan<kDistNT, uint32_t>(c, S.scan, tot);
+            if (threadIdx.x < (unsigned)nb) {
+                S.gbase[threadIdx.x] = start - ex;
+                S.cnt[threadIdx.x] = ex;
+            }
+        }
+        __syncthreads();
+        // ---- staging entries
+#pragma unroll
+        for (int r = 0; r < kDistIPT; ++r) {
+            const int p = warp * (kDistIPT * 32) + r * 32 + lane;
+            if (p < tn) {
+                const uint32_t d = pack[r] & 0xFFFFu;
+                S.slot[S.cnt[d] + S.whist[warp][d] + (pack[r] >> 16)] = (uint32_t)p | (d << 16);
+            }
+        }
+        __syncthreads();
+        // ---- coalesced writes of every chunk's run
+        for (int q = threadIdx.x; q < tn; q += kDistNT) {
+            const uint32_t v = S.slot[q];
+            const uint32_t p = v & 0xFFFFu;
+            const uint64_t o = (uint32_t)(S.gbase[v >> 16] + (uint32_t)q);   // positions are below 2^30
+            if (o >= n) { raise(a.err, FP_ERR_CAPACITY, 15); continue; }   // offsets not those of these points
+            a.out[o] = S.raw[b][p];
+            if (a.perm) a.perm[o] = (uint32_t)(base + p);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------ distribution in one sweep
+// one segment [0, n) with K digits when k_lo < K <= 2048 (k_lo: 256, or 0 when
+// the cells are given and the double-buffered sweep takes the small counts
+// too): its tiles, the segment bounds, and the flag that gates the radix passes
+constexpr int kDistMidBits = 9;   // up to 512 chunks: two CTAs per SM
+static_assert(kDistMidBits == kDistBits, "the sweep with the cells given is the 9-bit variant");
+
+__global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint32_t k_lo, uint64_t* seg_off,
+                             uint32_t* seg_lo, uint32_t* seg_nb, SegTile* tiles, uint32_t* cnt, uint32_t* run_sort)
 {
     const uint32_t K = *num_chunks;
-    const bool wide = K > (1u << kSegSmallBits) && K <= (1u << kSegMaxBits);
+    const bool wide = K > k_lo && K <= (1u << kSegMaxBits);
     const uint64_t ntl = wide ? (n + kSortTile - 1) / kSortTile : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += stride)
@@ -163,7 +463,8 @@ __global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint64_t* s
 
 struct DistScratch {
     uint64_t* seg_off;
-    uint32_t *lo, *nb, *cnt, *status;
+    uint32_t *lo, *nb, *cnt, *status, *gstart;
+    uint16_t* tab;
     SegTile* tiles;
     uint64_t ntiles;
 };
@@ -179,6 +480,8 @@ static DistScratch dist_carve(const Workspace& ws, uint64_t n)
     d.cnt = ws.take<uint32_t>(8);
     d.tiles = ws.take<SegTile>(T);
     d.status = ws.take<uint32_t>(T << kSegMaxBits);
+    d.gstart = ws.take<uint32_t>(((T + kDistGroup - 1) / kDistGroup) << kDistBits);
+    d.tab = ws.take<uint16_t>(1u << (3 * kDistTabLevel));
     return d;
 }
 
@@ -206,13 +509,19 @@ size_t dist_wide_bytes(uint64_t n)
 
 cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
                       const uint64_t* offsets, const uint32_t* num_chunks, int4* out, uint32_t* perm,
-                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st, const uint32_t* cells)
+                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st, const uint32_t* cells,
+                      uint16_t* chunk_tmp)
 {
     const DistScratch d = dist_carve(ws, n);
+    // the cells given and a scratch array for every point's chunk: up to 512
+    // chunks take the double-buffered sweep
+    const bool sweep = cells && chunk_tmp && ((uintptr_t)chunk_tmp & 15) == 0 && ((uintptr_t)pts & 15) == 0;
     const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((d.ntiles + 255) / 256, (uint64_t)ws.num_sms * 4));
-    k_dist_setup<<<gs, 256, 0, st>>>(num_chunks, n, d.seg_off, d.lo, d.nb, d.tiles, d.cnt, run_sort);
+    k_dist_setup<<<gs, 256, 0, st>>>(num_chunks, n, sweep ? 0u : (1u << kSegSmallBits), d.seg_off, d.lo, d.nb,
+                                     d.tiles, d.cnt, run_sort);
     const int gz = std::max(1, ws.num_sms * 8);
-    k_seg_zero<kDistMidBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
+    if (!sweep)
+        k_seg_zero<kDistMidBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
     k_seg_zero<kSegMaxBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt + 3, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
     SegArgs a{};
     a.pt_in = pts; a.pt_out = out;
@@ -229,7 +538,29 @@ cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, c
     a.cube = cube; a.lut = lut; a.cells = cells; a.g = g;
     cudaError_t e;
     a.d_ntiles = d.cnt; a.counter = d.cnt + 1;
-    if ((e = dist_launch<kDistMidBits>(a, d.ntiles, ws.num_sms, st))) return e;
+    if (sweep) {
+        DistSweepArgs b{};
+        b.pts = pts; b.cells = cells; b.lut = lut; b.offsets = offsets;
+        b.out = out; b.perm = perm; b.tab = d.tab; b.chunk = chunk_tmp;
+        b.before = d.status; b.gstart = d.gstart; b.counter = d.cnt + 1;
+        b.d_ntiles = d.cnt; b.ntiles_max = d.ntiles; b.nb = d.nb;
+        b.n = n; b.ncell = 1u << (3 * g); b.g = g; b.tl = std::min(g, kDistTabLevel); b.err = ws.err;
+        const uint32_t nodes = 1u << (3 * b.tl);
+        k_dist_table<<<(nodes * 32 + 255) / 256, 256, 0, st>>>(b);
+        const uint64_t ngroups = (d.ntiles + kDistGroup - 1) / kDistGroup;
+        const int tsm = (int)(nodes * sizeof(uint16_t) < 16 ? 16 : nodes * sizeof(uint16_t));
+        if ((e = cudaFuncSetAttribute(k_dist_count, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm))) return e;
+        const int gc = (int)std::max<uint64_t>(1, std::min<uint64_t>(ngroups, (uint64_t)ws.num_sms * 3));
+        k_dist_count<<<gc, kDistCountNT, tsm, st>>>(b);
+        k_dist_colscan<<<kDistDig * 32 / 256, 256, 0, st>>>(b);
+        const int smem = (int)sizeof(DistSmem);
+        if ((e = cudaFuncSetAttribute(k_dist_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(d.ntiles, (uint64_t)ws.num_sms));
+        k_dist_sweep<<<grid, kDistNT, smem, st>>>(b);
+        if ((e = cudaGetLastError())) return e;
+    } else if ((e = dist_launch<kDistMidBits>(a, d.ntiles, ws.num_sms, st))) {
+        return e;
+    }
     a.d_ntiles = d.cnt + 3; a.counter = d.cnt + 4;
     return dist_launch<kSegMaxBits>(a, d.ntiles, ws.num_sms, st);
 }

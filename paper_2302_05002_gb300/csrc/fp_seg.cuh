@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
                     d = (uint32_t)(nb - 1);
                 }
             }
-            uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            const uint32_t peers = match_bits<MAXB>(d, d != 0xFFFFu);
             int leader = __ffs(peers) - 1;
             uint32_t old = 0;
             if (lane == leader && d != 0xFFFFu) {
@@ -300,14 +300,18 @@ struct SegCall {
     uint32_t *st_rank, *st_list, *st_nrank, *st_tiles;
 };
 
-// Distribution of n points into 257..2048 chunks in one sweep: one segment
-// (the whole array), digit = chunk of the point's cell, bucket bases = the
-// chunk offsets.  Runs only when *d_num_chunks lies in that range; *run_sort
-// is set to 1 otherwise (the radix passes run instead), 0 when it ran.
+// Distribution of n points into chunks without the radix passes: with the
+// cells and a 16-byte aligned scratch of n chunk ids given, 1..512 chunks take
+// the counting pass and the double-buffered sweep (fp_seg.cu); else 257..512
+// chunks the 9-bit segmented sweep; 513..2048 chunks the 11-bit one (digit =
+// chunk of the point's cell, bucket bases = the chunk offsets).  *run_sort is
+// set to 1 when the count is outside these ranges (the radix passes run
+// instead), 0 when one of them ran.
 size_t dist_wide_bytes(uint64_t n);
 cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, const uint32_t* lut,
                       const uint64_t* offsets, const uint32_t* num_chunks, int4* out, uint32_t* perm,
-                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st, const uint32_t* cells = nullptr);
+                      uint32_t* run_sort, const Workspace& ws, cudaStream_t st, const uint32_t* cells = nullptr,
+                      uint16_t* chunk_tmp = nullptr);
 
 // Setup (chunk node ids, digits, tiles), status reset, both pass variants.
 // Afterwards cnt[2] != 0 means a chunk did not fit (the caller's whole-array

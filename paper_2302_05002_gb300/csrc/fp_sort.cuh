@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kSortNT, 2) k_sort_pass(SortArgs a, int slot)
 #pragma unroll
         for (int r = 0; r < kSortIPT; ++r) {
             const uint32_t d = dg[r];
-            uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            const uint32_t peers = match_bits<kSortMaxBits>(d, d != 0xFFFFu);
             int leader = __ffs(peers) - 1;
             uint32_t old = 0;
             if (lane == leader && d != 0xFFFFu) {
