@@ -1246,34 +1246,71 @@ __global__ void k_node_children(const uint32_t* nnode, const uint64_t* sorted_st
 // level-g ancestor, whose ids are consecutive in preorder: the search runs over
 // that subtree only, with the point's key at max_level (32-bit for max_level
 // <= 10) -- only then is the point itself read.  leafid (nullable): the leaf id.
-template <bool SMALL>
-__global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp_cube* cube,
-                          const uint32_t* codes, const uint32_t* idxtab,
-                          const uint64_t* sorted_start, const uint8_t* sorted_level, const uint32_t* ndesc,
-                          const uint32_t* nnode, uint32_t* owner, uint32_t* leafid, uint32_t* n_own, int g, int lmax,
-                          uint32_t* err)
+// Owned counts are summed per tile of kResolveTile consecutive points in a
+// shared-memory table keyed by node id (open addressing, bounded probes; a point
+// that finds no slot adds to the global count directly), then flushed with one
+// global atomic per node of the tile: consecutive points lie in one chunk, whose
+// owners are few, and the nodes above the chunks (the root owns a point of every
+// occupied level-s cell) are not hit by an atomic per point.
+constexpr int kResolveNT = 256;
+constexpr int kResolveIPT = 16;
+constexpr int kResolveTile = kResolveNT * kResolveIPT;
+constexpr int kOwnSlots = 1024;   // power of two
+constexpr int kOwnProbes = 32;
+
+FP_DEV void own_add(uint32_t* keys, uint32_t* cnt, uint32_t* n_own, uint32_t id)
 {
+    uint32_t h = (id * 2654435761u) & (kOwnSlots - 1);
+    for (int q = 0; q < kOwnProbes; ++q) {
+        uint32_t k = keys[h];
+        if (k == kNone) {
+            k = atomicCAS(&keys[h], kNone, id);
+            if (k == kNone) k = id;
+        }
+        if (k == id) { atomicAdd(&cnt[h], 1u); return; }
+        h = (h + 1) & (kOwnSlots - 1);
+    }
+    atomicAdd(&n_own[id], 1u);   // the table is crowded: straight to the global count
+}
+
+template <bool SMALL>
+__global__ void __launch_bounds__(kResolveNT) k_resolve(const fp_point* __restrict__ pts, uint64_t n,
+                                                        const fp_cube* cube, const uint32_t* codes,
+                                                        const uint32_t* idxtab, const uint64_t* sorted_start,
+                                                        const uint8_t* sorted_level, const uint32_t* ndesc,
+                                                        const uint32_t* nnode, uint32_t* owner, uint32_t* leafid,
+                                                        uint32_t* n_own, int g, int lmax, uint32_t* err)
+{
+    __shared__ uint32_t s_key[kOwnSlots], s_cnt[kOwnSlots];
     const CubeDev cb = load_cube(cube);
     const float scale_l = SMALL ? scale_at(cb, lmax) : 0.f;
     const uint32_t M = *nnode;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
     const int nt = leafid ? 2 : 1;
-    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-        uint64_t j = i0 + threadIdx.x;
-        uint32_t oid = kNone;
-        if (j < n) {
-            const uint32_t cw = codes[j];
-            const uint32_t cell = code_cell(cw);
-            const int ks[2] = {code_own(cw), code_leaf(cw)};
+    const uint64_t ntiles = (n + kResolveTile - 1) / kResolveTile;
+    for (int q = threadIdx.x; q < kOwnSlots; q += kResolveNT) { s_key[q] = kNone; s_cnt[q] = 0; }
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        __syncthreads();   // the table is clear
+        const uint64_t base = t * kResolveTile;
+        uint32_t cw[kResolveIPT];
+#pragma unroll
+        for (int r = 0; r < kResolveIPT; ++r) {   // all loads in flight together
+            const uint64_t j = base + (uint64_t)r * kResolveNT + threadIdx.x;
+            cw[r] = j < n ? codes[j] : 0u;
+        }
+#pragma unroll 4
+        for (int r = 0; r < kResolveIPT; ++r) {
+            const uint64_t j = base + (uint64_t)r * kResolveNT + threadIdx.x;
+            if (j >= n) continue;
+            const uint32_t cell = code_cell(cw[r]);
+            const int ks[2] = {code_own(cw[r]), code_leaf(cw[r])};
             uint32_t ids[2] = {0u, 0u};
             const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + cell];
             uint64_t kl = 0;
             bool have_kl = false;
-            for (int t = 0; t < nt; ++t) {
-                const int L = ks[t];
+            for (int u = 0; u < nt; ++u) {
+                const int L = ks[u];
                 if (L <= g) {
-                    ids[t] = idxtab[((1ull << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
+                    ids[u] = idxtab[((1ull << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
                 } else {
                     if (!have_kl) {
                         const int4 p = ld_point(pts, j);
@@ -1281,12 +1318,12 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
                                    : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
                         have_kl = true;
                     }
-                    ids[t] = kNone;
+                    ids[u] = kNone;
                     if (L <= lmax && c0 < M) {
                         const uint64_t k = kl >> (3 * (lmax - L));
-                        const uint32_t r = node_lookup(sorted_start + c0, sorted_level + c0,
-                                                       min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
-                        if (r != kNone) ids[t] = c0 + r;
+                        const uint32_t rr = node_lookup(sorted_start + c0, sorted_level + c0,
+                                                        min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
+                        if (rr != kNone) ids[u] = c0 + rr;
                     }
                 }
             }
@@ -1296,10 +1333,17 @@ __global__ void k_resolve(const fp_point* __restrict__ pts, uint64_t n, const fp
             }
             owner[j] = ids[0];
             if (leafid) leafid[j] = ids[1];
-            oid = ids[0];
+            own_add(s_key, s_cnt, n_own, ids[0]);
         }
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, oid);
-        if (oid != kNone && lane == __ffs(peers) - 1) atomicAdd(&n_own[oid], (uint32_t)__popc(peers));
+        __syncthreads();
+        for (int q = threadIdx.x; q < kOwnSlots; q += kResolveNT) {   // flush, and clear for the next tile
+            const uint32_t k = s_key[q];
+            if (k != kNone) {
+                atomicAdd(&n_own[k], s_cnt[q]);
+                s_key[q] = kNone;
+                s_cnt[q] = 0;
+            }
+        }
     }
 }
 
@@ -1642,10 +1686,11 @@ cudaError_t launch_octree_impl(const fp_point* sorted, const uint32_t* perm, uin
     }
     // 8. owner and leaf ids per distributed point, owned counts
     {
-        int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)ws.num_sms * 16);
+        const int grid = (int)std::max<uint64_t>(
+            1, std::min<uint64_t>((N + kResolveTile - 1) / kResolveTile, (uint64_t)ws.num_sms * 8));
         auto kres = lmax <= 10 ? k_resolve<true> : k_resolve<false>;
         KTimerScope kt(FP_KERNEL_RESOLVE, st);
-        kres<<<grid, 256, 0, st>>>(sorted, N, cube, B.codes, B.idxtab, B.nk, B.slevel, B.ndesc, nnode, owner,
+        kres<<<grid, kResolveNT, 0, st>>>(sorted, N, cube, B.codes, B.idxtab, B.nk, B.slevel, B.ndesc, nnode, owner,
                                    (leaf_pts || leaf_perm) ? B.leafid : nullptr,
                                    B.nown, g, lmax, ws.err);
         k_write_nown<<<(unsigned)((Ly.node_cap + 255) / 256), 256, 0, st>>>(nodes, nnode, node_cap, B.nown);
@@ -1749,9 +1794,10 @@ cudaError_t launch_octree_resolve(const fp_point* pts, uint64_t n, const fp_cube
                                   uint32_t* owner, const Workspace& ws, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ws.num_sms * 16);
+    const int grid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((n + kResolveTile - 1) / kResolveTile, (uint64_t)ws.num_sms * 8));
     auto kres = prm.max_level <= 10 ? k_resolve<true> : k_resolve<false>;
-    kres<<<grid, 256, 0, st>>>(pts, n, cube, codes, T.idxtab, T.starts, T.slevel, T.ndesc, T.nnode, owner, nullptr,
+    kres<<<grid, kResolveNT, 0, st>>>(pts, n, cube, codes, T.idxtab, T.starts, T.slevel, T.ndesc, T.nnode, owner, nullptr,
                                T.nown, (int)prm.grid_log2, (int)prm.max_level, ws.err);
     return cudaGetLastError();
 }

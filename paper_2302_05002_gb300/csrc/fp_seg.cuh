@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
                     d = (uint32_t)(nb - 1);
                 }
             }
-            const uint32_t peers = match_bits<MAXB>(d, d != 0xFFFFu);
+            uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
             int leader = __ffs(peers) - 1;
             uint32_t old = 0;
             if (lane == leader && d != 0xFFFFu) {
