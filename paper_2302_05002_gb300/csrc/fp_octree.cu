@@ -1257,8 +1257,10 @@ constexpr int kResolveIPT = 16;
 constexpr int kResolveTile = kResolveNT * kResolveIPT;
 constexpr int kOwnSlots = 1024;   // power of two
 constexpr int kOwnProbes = 32;
+constexpr int kResolveTabLevel = 4;   // node ids of the levels 0..4 in shared memory
+constexpr int kResolveTab = ((1 << (3 * (kResolveTabLevel + 1))) - 1) / 7;
 
-FP_DEV void own_add(uint32_t* keys, uint32_t* cnt, uint32_t* n_own, uint32_t id)
+FP_DEV void own_add(uint32_t* keys, uint32_t* cnt, uint32_t* n_own, uint32_t id, uint32_t v)
 {
     uint32_t h = (id * 2654435761u) & (kOwnSlots - 1);
     for (int q = 0; q < kOwnProbes; ++q) {
@@ -1267,10 +1269,10 @@ FP_DEV void own_add(uint32_t* keys, uint32_t* cnt, uint32_t* n_own, uint32_t id)
             k = atomicCAS(&keys[h], kNone, id);
             if (k == kNone) k = id;
         }
-        if (k == id) { atomicAdd(&cnt[h], 1u); return; }
+        if (k == id) { atomicAdd(&cnt[h], v); return; }
         h = (h + 1) & (kOwnSlots - 1);
     }
-    atomicAdd(&n_own[id], 1u);   // the table is crowded: straight to the global count
+    atomicAdd(&n_own[id], v);   // the table is crowded: straight to the global count
 }
 
 template <bool SMALL>
@@ -1282,7 +1284,11 @@ __global__ void __launch_bounds__(kResolveNT) k_resolve(const fp_point* __restri
                                                         uint32_t* n_own, int g, int lmax, uint32_t* err)
 {
     __shared__ uint32_t s_key[kOwnSlots], s_cnt[kOwnSlots];
+    __shared__ uint32_t s_idx[kResolveTab];   // the node ids of the coarse levels' cells
     const CubeDev cb = load_cube(cube);
+    const int tl = min(g, kResolveTabLevel);
+    const uint32_t ntab = ((1u << (3 * (tl + 1))) - 1) / 7;
+    for (uint32_t q = threadIdx.x; q < ntab; q += kResolveNT) s_idx[q] = idxtab[q];
     const float scale_l = SMALL ? scale_at(cb, lmax) : 0.f;
     const uint32_t M = *nnode;
     const int nt = leafid ? 2 : 1;
@@ -1300,40 +1306,45 @@ __global__ void __launch_bounds__(kResolveNT) k_resolve(const fp_point* __restri
 #pragma unroll 4
         for (int r = 0; r < kResolveIPT; ++r) {
             const uint64_t j = base + (uint64_t)r * kResolveNT + threadIdx.x;
-            if (j >= n) continue;
-            const uint32_t cell = code_cell(cw[r]);
-            const int ks[2] = {code_own(cw[r]), code_leaf(cw[r])};
-            uint32_t ids[2] = {0u, 0u};
-            const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + cell];
-            uint64_t kl = 0;
-            bool have_kl = false;
-            for (int u = 0; u < nt; ++u) {
-                const int L = ks[u];
-                if (L <= g) {
-                    ids[u] = idxtab[((1ull << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
-                } else {
-                    if (!have_kl) {
-                        const int4 p = ld_point(pts, j);
-                        kl = SMALL ? (uint64_t)key_small(p.x, p.y, p.z, cb, scale_l, lmax)
-                                   : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
-                        have_kl = true;
-                    }
-                    ids[u] = kNone;
-                    if (L <= lmax && c0 < M) {
-                        const uint64_t k = kl >> (3 * (lmax - L));
-                        const uint32_t rr = node_lookup(sorted_start + c0, sorted_level + c0,
-                                                        min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
-                        if (rr != kNone) ids[u] = c0 + rr;
+            uint32_t oid = kNone;
+            if (j < n) {
+                const uint32_t cell = code_cell(cw[r]);
+                const int ks[2] = {code_own(cw[r]), code_leaf(cw[r])};
+                uint32_t ids[2] = {0u, 0u};
+                uint64_t kl = 0;
+                bool have_kl = false;
+                for (int u = 0; u < nt; ++u) {
+                    const int L = ks[u];
+                    if (L <= tl) {
+                        ids[u] = s_idx[((1u << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
+                    } else if (L <= g) {
+                        ids[u] = idxtab[((1ull << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
+                    } else {
+                        const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + cell];
+                        if (!have_kl) {
+                            const int4 p = ld_point(pts, j);
+                            kl = SMALL ? (uint64_t)key_small(p.x, p.y, p.z, cb, scale_l, lmax)
+                                       : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
+                            have_kl = true;
+                        }
+                        ids[u] = kNone;
+                        if (L <= lmax && c0 < M) {
+                            const uint64_t k = kl >> (3 * (lmax - L));
+                            const uint32_t rr = node_lookup(sorted_start + c0, sorted_level + c0,
+                                                            min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
+                            if (rr != kNone) ids[u] = c0 + rr;
+                        }
                     }
                 }
+                if (ids[0] >= M || ids[1] >= M) {   // never for a consistent tree
+                    raise(err, FP_ERR_CAPACITY, 9);
+                    ids[0] = ids[1] = 0;
+                }
+                owner[j] = ids[0];
+                if (leafid) leafid[j] = ids[1];
+                oid = ids[0];
             }
-            if (ids[0] >= M || ids[1] >= M) {   // never for a consistent tree
-                raise(err, FP_ERR_CAPACITY, 9);
-                ids[0] = ids[1] = 0;
-            }
-            owner[j] = ids[0];
-            if (leafid) leafid[j] = ids[1];
-            own_add(s_key, s_cnt, n_own, ids[0]);
+            if (oid != kNone) own_add(s_key, s_cnt, n_own, oid, 1u);
         }
         __syncthreads();
         for (int q = threadIdx.x; q < kOwnSlots; q += kResolveNT) {   // flush, and clear for the next tile
