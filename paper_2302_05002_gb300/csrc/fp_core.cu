@@ -272,7 +272,11 @@ __global__ void __launch_bounds__(256) k_count(const fp_point* __restrict__ pts,
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (AGG) {
+            // a warp whose neighbouring lanes never share a cell (spread-out
+            // points) adds directly; otherwise its equal cells are merged first
+            const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, key[u], 1);   // (lane 31: its own)
+            const bool twin = lane < 31 && key[u] != kNone && key[u] == knext;
+            if (AGG && __any_sync(0xFFFFFFFFu, twin)) {
                 uint32_t peers = __match_any_sync(0xFFFFFFFFu, key[u]);
                 if (key[u] != kNone && lane == __ffs(peers) - 1) {
                     const uint32_t slot = (key[u] * 2654435761u) >> 22;   // 10-bit multiplicative hash
