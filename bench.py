@@ -56,7 +56,16 @@ FIXED_BYTES = {"merge": 3 * 4 * (1 << 21)}
 # kernel's sources hash to the recorded value (a changed kernel reports null)
 KERNEL_SOURCES = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_sort.cuh", "fp_sort.cu", "fp_seg.cuh",
                   "fp_seg.cu", "fp_octree.cu", "fp_core.cu", "fp_api.cu"]
+_H = "82f37e44e3bfeaed"   # kernel sources of the captures (profiles/kernels_uniform100M.md)
+_T100 = {"bounds_decimate": 1.698e9, "count": 1.977e9, "distribute": 0.617e9 + 3.804e9, "cell_group": 4.394e9,
+         "units": 2.465e9, "resolve": 0.814e9, "owner_scatter": 3.806e9}
+# uniform-100M: one-kernel captures of the first launch (the distribution: its counting
+# pass and sweep; the table and scan launches move under 20 MB); uniform-1B has the
+# same per-point structure (512 chunks, the same node levels) and ten times the points
 NCU_TRAFFIC = {}
+for _k, _b in _T100.items():
+    NCU_TRAFFIC[("uniform-100M", _k)] = (_b, _H)
+    NCU_TRAFFIC[("uniform-1B", _k)] = (10 * _b, _H)
 
 
 def sources_hash():
@@ -1316,7 +1325,8 @@ def run_plain(args, wl, rank, world, local):
             continue
         b = kernel_alg_bytes(k, n)
         kernels[k] = {"ms": v, "share_of_step": v / ms, "alg_bytes": b,
-                      "frac": (b / (v * 1e-3) / 1e9 / peak) if b else 0.0}
+                      "frac": (b / (v * 1e-3) / 1e9 / peak) if b else 0.0,
+                      "traffic": ncu_traffic(args.workload, k)}
     # the method's mandatory bytes: 97 per point plus the count grid's 25.2 MB
     step_alg = ALG_PER_POINT * n + FIXED_BYTES["merge"]
     if rank == 0:
