@@ -154,8 +154,10 @@ constexpr int kDistIPT = kSortTile / kDistNT;
 constexpr int kDistWarps = kDistNT / 32;
 constexpr int kDistBits = 9;
 constexpr int kDistDig = 1 << kDistBits;
+constexpr int kDistWideBits = 12;               // the wide sweep: 513 .. 4096 chunks
+constexpr int kDistWideDig = 1 << kDistWideBits;
 constexpr int kDistGroup = 64;                  // tiles per block of k_dist_count
-constexpr int kDistCountNT = kDistDig;          // thread d of k_dist_count owns chunk d
+constexpr int kDistCountNT = 512;               // thread d of k_dist_count owns chunks d, d + 512, ...
 constexpr int kDistCountIPT = kSortTile / kDistCountNT;
 constexpr int kDistTabLevel = 5;                // level of the node -> chunk table
 constexpr uint16_t kDistSplit = 0xFFFFu;        // the node's points lie in several chunks
@@ -169,23 +171,22 @@ struct DistSweepArgs {
     uint32_t* perm;             // nullable
     uint16_t* tab;              // [8^tl]: chunk of a level-tl node, or kDistSplit
     uint16_t* chunk;            // chunk of every point, 16-byte aligned
-    uint32_t* before;           // [tile][kDistDig]: points of the chunk in the group's earlier tiles
-    uint32_t* gstart;           // [group][kDistDig]: group totals, then the group's start in the chunk
+    uint32_t* before;           // [tile][DIG]: points of the chunk in the group's earlier tiles
+    uint32_t* gstart;           // [group][DIG]: group totals, then the group's start in the chunk
     uint32_t* counter;
     const uint32_t* d_ntiles;   // tiles of this sweep (0: another path runs)
     uint64_t ntiles_max;
-    const uint32_t* nb;         // chunks (1 .. kDistDig)
+    const uint32_t* nb;         // chunks (1 .. DIG, the sweep's width)
     uint64_t n;
     uint32_t ncell;             // cells of the grid (bound of a cell id)
     int g, tl;                  // grid level, table level (tl <= g)
     uint32_t* err;
 };
 
-// one warp per level-tl node: the chunks of its occupied cells
+// one warp per level-tl node: the chunks of its occupied cells (built for both
+// sweeps, whichever of them runs)
 __global__ void k_dist_table(DistSweepArgs a)
 {
-    const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
-    if (ntiles == 0) return;
     const int lane = threadIdx.x & 31;
     const uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (k >= (1u << (3 * a.tl))) return;
@@ -197,17 +198,19 @@ __global__ void k_dist_table(DistSweepArgs a)
     }
     cmin = __reduce_min_sync(0xFFFFFFFFu, cmin);
     cmax = __reduce_max_sync(0xFFFFFFFFu, cmax);
-    if (lane == 0) a.tab[k] = (cmin == cmax && cmin < (uint32_t)kDistDig) ? (uint16_t)cmin : kDistSplit;
+    if (lane == 0) a.tab[k] = (cmin == cmax && cmin < (uint32_t)kDistWideDig) ? (uint16_t)cmin : kDistSplit;
 }
 
+template <int DIG>
 __global__ void __launch_bounds__(kDistCountNT) k_dist_count(DistSweepArgs a)
 {
+    constexpr int kOwn = DIG / kDistCountNT;   // chunks per thread
     extern __shared__ __align__(16) uint16_t dist_tab[];   // 8^tl entries
-    __shared__ uint32_t h[kDistDig];
+    __shared__ uint32_t h[DIG];
     const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
     if (ntiles == 0) return;
     const uint64_t ngroups = (ntiles + kDistGroup - 1) / kDistGroup;
-    const uint32_t nb = min(*a.nb, (uint32_t)kDistDig);
+    const uint32_t nb = min(*a.nb, (uint32_t)DIG);
     const uint32_t d = threadIdx.x;
     const int tsh = 3 * (a.g - a.tl);
     {
@@ -221,8 +224,9 @@ __global__ void __launch_bounds__(kDistCountNT) k_dist_count(DistSweepArgs a)
     }
     for (uint64_t gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
         const uint64_t t0 = gi * kDistGroup, t1 = min(ntiles, t0 + kDistGroup);
-        uint32_t run = 0;
-        h[d] = 0;
+        uint32_t run[kOwn];
+#pragma unroll
+        for (int o = 0; o < kOwn; ++o) { run[o] = 0; h[d + o * kDistCountNT] = 0; }
         // the cells of the next tile are loaded while the current one is counted
         uint32_t c[kDistCountIPT];
         auto load = [&](uint64_t t) {
@@ -258,37 +262,44 @@ __global__ void __launch_bounds__(kDistCountNT) k_dist_count(DistSweepArgs a)
                     atomicAdd(&h[k[r]], 1u);
                 }
             __syncthreads();
-            if (d < nb) {
-                a.before[t * kDistDig + d] = run;
-                run += h[d];
+#pragma unroll
+            for (int o = 0; o < kOwn; ++o) {
+                const uint32_t cd = d + o * kDistCountNT;
+                if (cd < nb) {
+                    a.before[t * DIG + cd] = run[o];
+                    run[o] += h[cd];
+                }
+                h[cd] = 0;
             }
-            h[d] = 0;
             __syncthreads();
         }
-        if (d < nb) a.gstart[gi * kDistDig + d] = run;
+#pragma unroll
+        for (int o = 0; o < kOwn; ++o)
+            if (d + o * kDistCountNT < nb) a.gstart[gi * DIG + d + o * kDistCountNT] = run[o];
     }
 }
 
 // one warp per chunk: exclusive prefix of the group totals, plus the chunk's offset
+template <int DIG>
 __global__ void k_dist_colscan(DistSweepArgs a)
 {
     const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
     const uint64_t ngroups = (ntiles + kDistGroup - 1) / kDistGroup;
-    const uint32_t nb = min(*a.nb, (uint32_t)kDistDig);
+    const uint32_t nb = min(*a.nb, (uint32_t)DIG);
     const int lane = threadIdx.x & 31;
     const uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (d >= nb || ngroups == 0) return;
     uint32_t run = (uint32_t)a.offsets[d];
     for (uint64_t g0 = 0; g0 < ngroups; g0 += 32) {
         const uint64_t gi = g0 + lane;
-        const uint32_t v = gi < ngroups ? a.gstart[gi * kDistDig + d] : 0u;
+        const uint32_t v = gi < ngroups ? a.gstart[gi * DIG + d] : 0u;
         uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
             if (lane >= o) x += y;
         }
-        if (gi < ngroups) a.gstart[gi * kDistDig + d] = run + x - v;
+        if (gi < ngroups) a.gstart[gi * DIG + d] = run + x - v;
         run += __shfl_sync(0xFFFFFFFFu, x, 31);
     }
 }
@@ -431,6 +442,155 @@ __global__ void __launch_bounds__(kDistNT, 1) k_dist_sweep(DistSweepArgs a)
     }
 }
 
+// The wide sweep: 513 .. 4096 chunks, 12-bit chunk ids.  Per-warp histograms of
+// 4096 chunks would not fit beside the double-buffered tile, so a tile ranks its
+// points by a stable two-pass sort of (chunk, position) in shared memory (6-bit
+// digits, ballot-matched per warp); every chunk present takes its output start
+// once (its group's start plus the points of the chunk in the group's earlier
+// tiles) and each point the start plus its place in the chunk's run.
+constexpr int kWideRadix = 6;
+constexpr int kWideBins = 1 << kWideRadix;
+
+struct WideSmem {
+    int4 raw[2][kSortTile];                  // the tile's points, as stored
+    uint16_t chk[2][kSortTile];              // and their chunks
+    uint32_t s0[kSortTile];                  // chunk << 12 | position, after the first pass
+    uint32_t s1[kSortTile];                  // the same, sorted by chunk (then position)
+    uint16_t whist[kDistWarps][kWideBins];   // per-warp digit counts, then their prefixes
+    uint32_t off[kWideBins];                 // first slot of every digit
+    uint16_t rstart[kDistWideDig];           // first slot of every chunk present
+    uint32_t startv[kDistWideDig];           // output position of the tile's first point of every chunk present
+    uint32_t scan[kDistWarps];
+    uint32_t tile[2];
+    uint64_t bar[2];
+};
+
+// one stable pass of the tile's (chunk << 12 | position) words by 6 chunk bits at `shift`;
+// pass 0 builds the words from the chunks in buffer b, later passes read `src`
+FP_DEV void wide_pass(WideSmem& S, int b, const uint32_t* src, uint32_t* dst, int tn, int shift, bool first)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < kDistWarps * kWideBins / 2; q += kDistNT)
+        reinterpret_cast<uint32_t*>(&S.whist[0][0])[q] = 0u;
+    __syncthreads();
+    uint32_t v[kDistIPT], pack[kDistIPT];
+#pragma unroll
+    for (int r = 0; r < kDistIPT; ++r) {
+        const int p = warp * (kDistIPT * 32) + r * 32 + lane;
+        const bool valid = p < tn;
+        v[r] = 0;
+        if (valid) v[r] = first ? ((uint32_t)S.chk[b][p] << 12) | (uint32_t)p : src[p];
+        const uint32_t d = valid ? (v[r] >> (12 + shift)) & (kWideBins - 1) : 0u;
+        const uint32_t peers = match_bits<kWideRadix>(d, valid);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && valid) {
+            old = S.whist[warp][d];
+            S.whist[warp][d] = (uint16_t)(old + __popc(peers));
+        }
+        old = __shfl_sync(0xFFFFFFFFu, old, leader < 0 ? 0 : leader);
+        pack[r] = valid ? (d | ((old + __popc(peers & lanemask_lt())) << 16)) : 0xFFFFFFFFu;
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot_d = 0;
+    if (threadIdx.x < kWideBins) {   // prefix over the warps of every digit
+        for (int w = 0; w < kDistWarps; ++w) {
+            const uint32_t x = S.whist[w][threadIdx.x];
+            S.whist[w][threadIdx.x] = (uint16_t)tot_d;
+            tot_d += x;
+        }
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<kDistNT, uint32_t>(threadIdx.x < kWideBins ? tot_d : 0u, S.scan, tot);
+    if (threadIdx.x < kWideBins) S.off[threadIdx.x] = ex;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kDistIPT; ++r) {
+        if (pack[r] == 0xFFFFFFFFu) continue;
+        const uint32_t d = pack[r] & 0xFFFFu;
+        dst[S.off[d] + S.whist[warp][d] + (pack[r] >> 16)] = v[r];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kDistNT, 1) k_dist_sweep_wide(DistSweepArgs a)
+{
+    extern __shared__ __align__(128) unsigned char wide_smem[];
+    WideSmem& S = *reinterpret_cast<WideSmem*>(wide_smem);
+    const uint64_t ntiles = min((uint64_t)*a.d_ntiles, a.ntiles_max);
+    if (ntiles == 0) return;
+    const uint64_t n = a.n;
+    const uint32_t nb = min(*a.nb, (uint32_t)kDistWideDig);
+    auto issue = [&](uint64_t t, int b) {
+        const uint64_t base = t * kSortTile;
+        if (base + kSortTile > n) return;
+        fence_async_smem();
+        mbar_expect_tx(&S.bar[b], kSortTile * (uint32_t)(sizeof(int4) + sizeof(uint16_t)));
+        bulk_g2s(S.raw[b], a.pts + base, kSortTile * (uint32_t)sizeof(int4), &S.bar[b]);
+        bulk_g2s(S.chk[b], a.chunk + base, kSortTile * (uint32_t)sizeof(uint16_t), &S.bar[b]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        const uint32_t t0 = atomicAdd(a.counter, 1u);
+        S.tile[0] = t0;
+        if (t0 < ntiles) issue(t0, 0);
+    }
+    __syncthreads();
+    uint32_t phase = 0;   // bit b: parity of buffer b's next completion
+    for (int it = 0;; ++it) {
+        const int b = it & 1;
+        const uint64_t tile = S.tile[b];
+        if (tile >= ntiles) break;
+        uint32_t nx = 0;
+        if (threadIdx.x == 0) nx = atomicAdd(a.counter, 1u);
+        const uint64_t base = tile * kSortTile;
+        const int tn = (int)(n - base < (uint64_t)kSortTile ? n - base : (uint64_t)kSortTile);
+        if (tn == kSortTile) {
+            if (!mbar_wait(&S.bar[b], (phase >> b) & 1u)) {
+                raise(a.err, FP_ERR_TIMEOUT);
+                mbar_wait(&S.bar[b], (phase >> b) & 1u);   // the copy in flight, once more (bounded)
+            }
+            phase ^= 1u << b;
+        } else {
+            for (int p = threadIdx.x; p < tn; p += kDistNT) {
+                S.raw[b][p] = __ldg(a.pts + base + p);
+                S.chk[b][p] = a.chunk[base + p];
+            }
+        }
+        // (the first pass's barrier also publishes the partial tile's loads)
+        wide_pass(S, b, nullptr, S.s0, tn, 0, true);
+        if (threadIdx.x == 0) {   // buffer b ^ 1 was released by the last tile's closing barrier
+            S.tile[b ^ 1] = nx;
+            if (nx < ntiles) issue(nx, b ^ 1);
+        }
+        wide_pass(S, b, S.s0, S.s1, tn, kWideRadix, false);
+        // ---- every chunk present: its first slot and its output start
+        const uint64_t g = tile / kDistGroup;
+        for (int q = threadIdx.x; q < tn; q += kDistNT) {
+            const uint32_t c = S.s1[q] >> 12;
+            if (q == 0 || (S.s1[q - 1] >> 12) != c) {
+                if (c >= nb) { raise(a.err, FP_ERR_CAPACITY, 13); continue; }   // not a chunk
+                S.rstart[c] = (uint16_t)q;
+                S.startv[c] = __ldg(a.gstart + g * kDistWideDig + c) + __ldg(a.before + tile * kDistWideDig + c);
+            }
+        }
+        __syncthreads();
+        // ---- writes: every chunk's run in position order
+        for (int q = threadIdx.x; q < tn; q += kDistNT) {
+            const uint32_t v = S.s1[q];
+            const uint32_t c = v >> 12, p = v & 0xFFFu;
+            if (c >= nb) continue;
+            const uint64_t o = (uint64_t)S.startv[c] + (uint64_t)(q - S.rstart[c]);
+            if (o >= n) { raise(a.err, FP_ERR_CAPACITY, 15); continue; }   // offsets not those of these points
+            a.out[o] = S.raw[b][p];
+            if (a.perm) a.perm[o] = (uint32_t)(base + p);
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------ distribution in one sweep
 // one segment [0, n) with K digits when k_lo < K <= 2048 (k_lo: 256, or 0 when
 // the cells are given and the double-buffered sweep takes the small counts
@@ -438,11 +598,11 @@ __global__ void __launch_bounds__(kDistNT, 1) k_dist_sweep(DistSweepArgs a)
 constexpr int kDistMidBits = 9;   // up to 512 chunks: two CTAs per SM
 static_assert(kDistMidBits == kDistBits, "the sweep with the cells given is the 9-bit variant");
 
-__global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint32_t k_lo, uint64_t* seg_off,
+__global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint32_t k_lo, uint32_t k_hi, uint64_t* seg_off,
                              uint32_t* seg_lo, uint32_t* seg_nb, SegTile* tiles, uint32_t* cnt, uint32_t* run_sort)
 {
     const uint32_t K = *num_chunks;
-    const bool wide = K > k_lo && K <= (1u << kSegMaxBits);
+    const bool wide = K > k_lo && K <= k_hi;
     const uint64_t ntl = wide ? (n + kSortTile - 1) / kSortTile : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += stride)
@@ -454,7 +614,7 @@ __global__ void k_dist_setup(const uint32_t* num_chunks, uint64_t n, uint32_t k_
         seg_lo[0] = 0;
         seg_nb[0] = wide ? K : 1u;
         cnt[0] = mid ? (uint32_t)ntl : 0u;   // tiles of the 9-bit pass
-        cnt[3] = mid ? 0u : (uint32_t)ntl;   // tiles of the 11-bit pass
+        cnt[3] = mid ? 0u : (uint32_t)ntl;   // tiles of the 11-bit pass (the wide sweep with the cells)
         cnt[1] = cnt[4] = 0;                 // tile counters
         cnt[2] = 0;                          // fail word (never set here)
         *run_sort = wide ? 0u : 1u;
@@ -479,8 +639,8 @@ static DistScratch dist_carve(const Workspace& ws, uint64_t n)
     d.nb = ws.take<uint32_t>(1);
     d.cnt = ws.take<uint32_t>(8);
     d.tiles = ws.take<SegTile>(T);
-    d.status = ws.take<uint32_t>(T << kSegMaxBits);
-    d.gstart = ws.take<uint32_t>(((T + kDistGroup - 1) / kDistGroup) << kDistBits);
+    d.status = ws.take<uint32_t>(T << kDistWideBits);   // (also the wide sweep's per-tile starts)
+    d.gstart = ws.take<uint32_t>(((T + kDistGroup - 1) / kDistGroup) << kDistWideBits);
     d.tab = ws.take<uint16_t>(1u << (3 * kDistTabLevel));
     return d;
 }
@@ -513,15 +673,49 @@ cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, c
                       uint16_t* chunk_tmp)
 {
     const DistScratch d = dist_carve(ws, n);
-    // the cells given and a scratch array for every point's chunk: up to 512
-    // chunks take the double-buffered sweep
+    // the cells given and a scratch array for every point's chunk: up to 4096
+    // chunks take the counting pass and a double-buffered sweep
     const bool sweep = cells && chunk_tmp && ((uintptr_t)chunk_tmp & 15) == 0 && ((uintptr_t)pts & 15) == 0;
     const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>((d.ntiles + 255) / 256, (uint64_t)ws.num_sms * 4));
-    k_dist_setup<<<gs, 256, 0, st>>>(num_chunks, n, sweep ? 0u : (1u << kSegSmallBits), d.seg_off, d.lo, d.nb,
+    k_dist_setup<<<gs, 256, 0, st>>>(num_chunks, n, sweep ? 0u : (1u << kSegSmallBits),
+                                     sweep ? (uint32_t)kDistWideDig : (1u << kSegMaxBits), d.seg_off, d.lo, d.nb,
                                      d.tiles, d.cnt, run_sort);
+    cudaError_t e;
+    if (sweep) {
+        DistSweepArgs b{};
+        b.pts = pts; b.cells = cells; b.lut = lut; b.offsets = offsets;
+        b.out = out; b.perm = perm; b.tab = d.tab; b.chunk = chunk_tmp;
+        b.before = d.status; b.gstart = d.gstart;
+        b.ntiles_max = d.ntiles; b.nb = d.nb;
+        b.n = n; b.ncell = 1u << (3 * g); b.g = g; b.tl = std::min(g, kDistTabLevel); b.err = ws.err;
+        const uint32_t nodes = 1u << (3 * b.tl);
+        k_dist_table<<<(nodes * 32 + 255) / 256, 256, 0, st>>>(b);
+        const uint64_t ngroups = (d.ntiles + kDistGroup - 1) / kDistGroup;
+        const int tsm = (int)(nodes * sizeof(uint16_t) < 16 ? 16 : nodes * sizeof(uint16_t));
+        const int gc = (int)std::max<uint64_t>(1, std::min<uint64_t>(ngroups, (uint64_t)ws.num_sms * 3));
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(d.ntiles, (uint64_t)ws.num_sms));
+        // up to 512 chunks: per-warp histograms in the sweep (tiles cnt[0], counter cnt[1])
+        b.d_ntiles = d.cnt; b.counter = d.cnt + 1;
+        if ((e = cudaFuncSetAttribute(k_dist_count<kDistDig>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm)))
+            return e;
+        k_dist_count<kDistDig><<<gc, kDistCountNT, tsm, st>>>(b);
+        k_dist_colscan<kDistDig><<<kDistDig * 32 / 256, 256, 0, st>>>(b);
+        const int smem = (int)sizeof(DistSmem);
+        if ((e = cudaFuncSetAttribute(k_dist_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+        k_dist_sweep<<<grid, kDistNT, smem, st>>>(b);
+        // 513 .. 4096 chunks: the tile's ranks by a two-pass sort (tiles cnt[3], counter cnt[4])
+        b.d_ntiles = d.cnt + 3; b.counter = d.cnt + 4;
+        if ((e = cudaFuncSetAttribute(k_dist_count<kDistWideDig>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm)))
+            return e;
+        k_dist_count<kDistWideDig><<<gc, kDistCountNT, tsm, st>>>(b);
+        k_dist_colscan<kDistWideDig><<<kDistWideDig * 32 / 256, 256, 0, st>>>(b);
+        const int wsm = (int)sizeof(WideSmem);
+        if ((e = cudaFuncSetAttribute(k_dist_sweep_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, wsm))) return e;
+        k_dist_sweep_wide<<<grid, kDistNT, wsm, st>>>(b);
+        return cudaGetLastError();
+    }
     const int gz = std::max(1, ws.num_sms * 8);
-    if (!sweep)
-        k_seg_zero<kDistMidBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
+    k_seg_zero<kDistMidBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
     k_seg_zero<kSegMaxBits><<<gz, 256, 0, st>>>(d.tiles, d.cnt + 3, d.ntiles, d.seg_off, d.nb, d.status, d.cnt + 2);
     SegArgs a{};
     a.pt_in = pts; a.pt_out = out;
@@ -536,31 +730,7 @@ cudaError_t dist_wide(const int4* pts, uint64_t n, const fp_cube* cube, int g, c
     a.d_fail = d.cnt + 2;
     a.err = ws.err;
     a.cube = cube; a.lut = lut; a.cells = cells; a.g = g;
-    cudaError_t e;
-    a.d_ntiles = d.cnt; a.counter = d.cnt + 1;
-    if (sweep) {
-        DistSweepArgs b{};
-        b.pts = pts; b.cells = cells; b.lut = lut; b.offsets = offsets;
-        b.out = out; b.perm = perm; b.tab = d.tab; b.chunk = chunk_tmp;
-        b.before = d.status; b.gstart = d.gstart; b.counter = d.cnt + 1;
-        b.d_ntiles = d.cnt; b.ntiles_max = d.ntiles; b.nb = d.nb;
-        b.n = n; b.ncell = 1u << (3 * g); b.g = g; b.tl = std::min(g, kDistTabLevel); b.err = ws.err;
-        const uint32_t nodes = 1u << (3 * b.tl);
-        k_dist_table<<<(nodes * 32 + 255) / 256, 256, 0, st>>>(b);
-        const uint64_t ngroups = (d.ntiles + kDistGroup - 1) / kDistGroup;
-        const int tsm = (int)(nodes * sizeof(uint16_t) < 16 ? 16 : nodes * sizeof(uint16_t));
-        if ((e = cudaFuncSetAttribute(k_dist_count, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm))) return e;
-        const int gc = (int)std::max<uint64_t>(1, std::min<uint64_t>(ngroups, (uint64_t)ws.num_sms * 3));
-        k_dist_count<<<gc, kDistCountNT, tsm, st>>>(b);
-        k_dist_colscan<<<kDistDig * 32 / 256, 256, 0, st>>>(b);
-        const int smem = (int)sizeof(DistSmem);
-        if ((e = cudaFuncSetAttribute(k_dist_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(d.ntiles, (uint64_t)ws.num_sms));
-        k_dist_sweep<<<grid, kDistNT, smem, st>>>(b);
-        if ((e = cudaGetLastError())) return e;
-    } else if ((e = dist_launch<kDistMidBits>(a, d.ntiles, ws.num_sms, st))) {
-        return e;
-    }
+    if ((e = dist_launch<kDistMidBits>(a, d.ntiles, ws.num_sms, st))) return e;
     a.d_ntiles = d.cnt + 3; a.counter = d.cnt + 4;
     return dist_launch<kSegMaxBits>(a, d.ntiles, ws.num_sms, st);
 }

@@ -1,6 +1,8 @@
 """fp_distribute_cells at every chunk count around the boundaries of its paths
-(1..512 chunks: counting pass + double-buffered sweep; 513..2048: the 11-bit
-segmented sweep; more: the radix passes), with a ragged last tile, against the
+(with a 16-byte aligned cells array: 1..512 chunks the counting pass and the
+sweep with per-warp histograms, 513..4096 the counting pass and the sweep that
+sorts each tile, more the radix passes; without: 257..2048 the segmented sweeps,
+else the radix passes), with a ragged last tile, against the
 oracle's stable scatter given the same cell -> chunk table and offsets
 (the paper's distribution, Sec. 4.4, is defined for any such table).  A cells
 array that is not 16-byte aligned takes the paths without the sweep and gives
@@ -42,7 +44,7 @@ def table(cells_np, K):
     return lut, offsets
 
 
-@pytest.mark.parametrize("K", [1, 2, 255, 256, 257, 511, 512, 513, 2048, 2049])
+@pytest.mark.parametrize("K", [1, 2, 255, 256, 257, 511, 512, 513, 2048, 2049, 3080, 4096, 4097])
 @pytest.mark.parametrize("aligned", [True, False])
 def test_distribute_cells_chunk_counts(cloud, K, aligned):
     fp, pts_np, pts, cube, want_cube, cells_np = cloud
@@ -72,7 +74,7 @@ def test_distribute_cells_chunk_counts(cloud, K, aligned):
 def test_distribute_cells_small_clouds(gpu_lib):
     """Clouds of one partial tile and of exactly one full tile."""
     fp = gpu_lib
-    for n, K in ((1, 1), (17, 3), (4095, 40), (4096, 512), (4097, 300)):
+    for n, K in ((1, 1), (17, 3), (4095, 40), (4096, 512), (4097, 300), (4097, 1000), (8193, 3000)):
         pts_np = synth.uniform(n, 40 + n)
         pts = dev_points(pts_np)
         cube = fp.fp_bounds(pts)
