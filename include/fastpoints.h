@@ -284,9 +284,12 @@ fp_status fp_distribute(const fp_point* d_pts, uint64_t n, const fp_cube* d_cube
                         void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* fp_distribute with the points' level-g cells given (d_cells from
- * fp_count_cells, same cube and grid_log2): up to 2048 chunks the one-sweep
- * scatter reads the chunk of point i as d_lut[d_cells[i]] instead of computing
- * the cell from the point; more chunks take the radix passes, which compute it.
+ * fp_count_cells, same cube and grid_log2): the chunk of point i is
+ * d_lut[d_cells[i]] instead of being computed from the point.  With d_cells
+ * 16-byte aligned, up to 4096 chunks take a counting pass and a double-buffered
+ * sweep (no wait between blocks); otherwise up to 2048 chunks the one-sweep
+ * scatter; more chunks take the radix passes, which compute the cell.  Every
+ * d_cells[i] must be below 8^grid_log2 (else FP_ERR_CAPACITY, outputs invalid).
  * Outputs identical to fp_distribute's. */
 fp_status fp_distribute_cells(const fp_point* d_pts, const uint32_t* d_cells, uint64_t n, const fp_cube* d_cube,
                               uint32_t grid_log2, const uint32_t* d_lut, const uint64_t* d_offsets,

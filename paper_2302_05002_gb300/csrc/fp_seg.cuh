@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kSortNT, (seg_ctas<CPT, MAXB, DIST>())) k_seg_
                 if (p < tn) {
                     if (a.cells) {
                         cell = __ldg(a.cells + base + p);
+                        if (cell >> (3 * a.g)) { raise(a.err, FP_ERR_CAPACITY, 19); cell = 0; }   // not a cell of the grid
                     } else {
                         const int4 q = __ldg(a.pt_in + base + p);
                         cell = key_small(q.x, q.y, q.z, cube, scale_g, a.g);
