@@ -133,8 +133,9 @@ static cudaError_t seg_launch(SegArgs a, const SegScratch& sc, int v, int num_sm
     return cudaGetLastError();
 }
 
-// ---- the distribution with each point's cell given, up to 512 chunks, in four
-// launches and without any wait between blocks:
+// ---- the distribution with each point's cell given, up to 4096 chunks, in four
+// launches and without any wait between blocks (the sweep below for up to 512
+// chunks, k_dist_sweep_wide further down for 513 .. 4096):
 //   k_dist_table: per node of level L = min(g, 5), its chunk when every
 //     occupied cell of the node lies in that one chunk (else none) -- a 64 KB
 //     table that spares most points the gather of the cell -> chunk table;

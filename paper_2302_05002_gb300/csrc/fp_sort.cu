@@ -185,11 +185,11 @@ cudaError_t launch_distribute(const fp_point* pts, uint64_t n, const fp_cube* cu
     uint32_t* run_sort = ws.take<uint32_t>(1);
     Workspace rest = ws;
     KTimerScope kt(FP_KERNEL_DISTRIBUTE, st);
-    // With the cells given, up to 512 chunks: the count, scan and double-buffered
-    // sweep (every point's chunk kept in val_tmp, which the radix passes below
-    // then do not use).  257..2048 chunks: one sweep with chunk digits (no plan,
-    // bases = offsets).  Otherwise the radix passes below (one pass up to 256
-    // chunks), which compute the cells from the points.
+    // With the cells given (16-byte aligned), up to 4096 chunks: the count, scan
+    // and double-buffered sweep (every point's chunk kept in val_tmp, which the
+    // radix passes below then do not use).  Otherwise 257..2048 chunks: one sweep
+    // with chunk digits (no plan, bases = offsets).  Else the radix passes below
+    // (one pass up to 256 chunks), which compute the cells from the points.
     cudaError_t e = dist_wide(reinterpret_cast<const int4*>(pts), n, cube, g, lut, offsets, num_chunks,
                               reinterpret_cast<int4*>(out), perm, run_sort, rest, st, cells,
                               reinterpret_cast<uint16_t*>(val_tmp));
