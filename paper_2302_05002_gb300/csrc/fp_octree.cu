@@ -1275,6 +1275,25 @@ FP_DEV void own_add(uint32_t* keys, uint32_t* cnt, uint32_t* n_own, uint32_t id,
     atomicAdd(&n_own[id], v);   // the table is crowded: straight to the global count
 }
 
+// id of the node at level L > g holding distributed point j (kNone when absent):
+// by binary search among the descendants of its level-g cell's node, on the
+// point's key at max_level
+template <bool SMALL>
+__device__ __noinline__ uint32_t deep_id(const fp_point* __restrict__ pts, uint64_t j, const CubeDev& cb, float scale_l,
+                                         uint32_t cell, int L, const uint32_t* idxtab, const uint64_t* sorted_start,
+                                         const uint8_t* sorted_level, const uint32_t* ndesc, uint32_t M, int g, int lmax)
+{
+    const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + cell];
+    if (L > lmax || c0 >= M) return kNone;
+    const int4 p = ld_point(pts, j);
+    const uint64_t kl = SMALL ? (uint64_t)key_small(p.x, p.y, p.z, cb, scale_l, lmax)
+                              : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
+    const uint64_t k = kl >> (3 * (lmax - L));
+    const uint32_t rr =
+        node_lookup(sorted_start + c0, sorted_level + c0, min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
+    return rr != kNone ? c0 + rr : kNone;
+}
+
 template <bool SMALL>
 __global__ void __launch_bounds__(kResolveNT) k_resolve(const fp_point* __restrict__ pts, uint64_t n,
                                                         const fp_cube* cube, const uint32_t* codes,
@@ -1311,30 +1330,15 @@ __global__ void __launch_bounds__(kResolveNT) k_resolve(const fp_point* __restri
                 const uint32_t cell = code_cell(cw[r]);
                 const int ks[2] = {code_own(cw[r]), code_leaf(cw[r])};
                 uint32_t ids[2] = {0u, 0u};
-                uint64_t kl = 0;
-                bool have_kl = false;
                 for (int u = 0; u < nt; ++u) {
                     const int L = ks[u];
-                    if (L <= tl) {
+                    if (L <= tl)
                         ids[u] = s_idx[((1u << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
-                    } else if (L <= g) {
+                    else if (L <= g)
                         ids[u] = idxtab[((1ull << (3 * L)) - 1) / 7 + (cell >> (3 * (g - L)))];
-                    } else {
-                        const uint32_t c0 = idxtab[((1ull << (3 * g)) - 1) / 7 + cell];
-                        if (!have_kl) {
-                            const int4 p = ld_point(pts, j);
-                            kl = SMALL ? (uint64_t)key_small(p.x, p.y, p.z, cb, scale_l, lmax)
-                                       : key21(p.x, p.y, p.z, cb) >> (3 * (kKeyLevels - lmax));
-                            have_kl = true;
-                        }
-                        ids[u] = kNone;
-                        if (L <= lmax && c0 < M) {
-                            const uint64_t k = kl >> (3 * (lmax - L));
-                            const uint32_t rr = node_lookup(sorted_start + c0, sorted_level + c0,
-                                                            min(ndesc[c0] + 1, M - c0), k << (3 * (lmax - L)), L);
-                            if (rr != kNone) ids[u] = c0 + rr;
-                        }
-                    }
+                    else   // (kept out of the unrolled loop: its code is large and rarely run)
+                        ids[u] = deep_id<SMALL>(pts, j, cb, scale_l, cell, L, idxtab, sorted_start, sorted_level,
+                                                ndesc, M, g, lmax);
                 }
                 if (ids[0] >= M || ids[1] >= M) {   // never for a consistent tree
                     raise(err, FP_ERR_CAPACITY, 9);
