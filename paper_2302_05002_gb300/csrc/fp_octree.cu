@@ -334,13 +334,21 @@ __global__ void k_round_copy(const OpenNode* open, const uint32_t* nopen, uint32
             jv = r.z;
             trec[p] = make_uint4(r.x, r.y, r.z, slot);
         }
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
-        if (slot != kNone) {   // every lane of a slot's group takes part in its reduction
-            const uint32_t m = __reduce_min_sync(peers, jv);
-            if (lane == __ffs(peers) - 1) {
-                atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
-                atomicMin(&smin[slot], m);
+        // a warp whose neighbouring lanes hold distinct slots adds per lane (no match,
+        // no reduction over each slot's lanes); otherwise equal slots are merged first
+        const uint32_t snext = __shfl_down_sync(0xFFFFFFFFu, slot, 1);   // (lane 31: its own)
+        if (__any_sync(0xFFFFFFFFu, lane < 31 && slot != kNone && slot == snext)) {
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
+            if (slot != kNone) {   // every lane of a slot's group takes part in its reduction
+                const uint32_t m = __reduce_min_sync(peers, jv);
+                if (lane == __ffs(peers) - 1) {
+                    atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
+                    atomicMin(&smin[slot], m);
+                }
             }
+        } else if (slot != kNone) {
+            atomicAdd(&cnt[slot], 1u);
+            atomicMin(&smin[slot], jv);
         }
     }
 }
@@ -389,11 +397,17 @@ __global__ void k_round_scatter(const uint32_t* total, const uint4* __restrict__
         const uint32_t p = p0 + lane;
         const uint4 r = p < T ? trec[p] : make_uint4(0u, 0u, 0u, kNone);
         const uint32_t slot = r.w;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
-        const int leader = __ffs(peers) - 1;
+        // as in k_round_copy: one slot per lane when neighbouring lanes differ
+        const uint32_t snext = __shfl_down_sync(0xFFFFFFFFu, slot, 1);   // (lane 31: its own)
         uint32_t at = 0;
-        if (slot != kNone && lane == leader) at = atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
-        at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
+        if (__any_sync(0xFFFFFFFFu, lane < 31 && slot != kNone && slot == snext)) {
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, slot);
+            const int leader = __ffs(peers) - 1;
+            if (slot != kNone && lane == leader) at = atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
+            at = __shfl_sync(0xFFFFFFFFu, at, leader) + (uint32_t)__popc(peers & lanemask_lt());
+        } else if (slot != kNone) {
+            at = atomicAdd(&cnt[slot], 1u);
+        }
         if (slot == kNone) continue;
         if (at >= n) { raise(err, FP_ERR_CAPACITY, 6); continue; }
         rec[at] = make_uint4(r.x, r.y, r.z, 0u);
