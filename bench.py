@@ -56,12 +56,9 @@ FIXED_BYTES = {"merge": 3 * 4 * (1 << 21)}
 # kernel's sources hash to the recorded value (a changed kernel reports null)
 KERNEL_SOURCES = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_sort.cuh", "fp_sort.cu", "fp_seg.cuh",
                   "fp_seg.cu", "fp_octree.cu", "fp_core.cu", "fp_api.cu"]
-# kernel sources of the captures (profiles/kernels_uniform100M.md), as of later comment
-# edits and a cell check in the segmented sweep's distribution variant, which leave
-# the captured kernels as they were
-_H = "016c3e9b17594a34"
-_T100 = {"bounds_decimate": 1.697e9, "count": 1.977e9, "distribute": 0.617e9 + 3.803e9, "cell_group": 4.530e9,
-         "units": 2.461e9, "resolve": 0.813e9, "owner_scatter": 3.806e9}
+_H = "d1c04ea72ffc4565"   # kernel sources of the captures (profiles/kernels_uniform100M.md)
+_T100 = {"bounds_decimate": 1.697e9, "count": 1.978e9, "distribute": 0.617e9 + 3.803e9, "cell_group": 4.424e9,
+         "units": 2.467e9, "resolve": 0.844e9, "owner_scatter": 3.806e9}
 # uniform-100M: one-kernel captures of the first launch (the distribution: its counting
 # pass and sweep; the table and scan launches move under 20 MB); uniform-1B has the
 # same per-point structure (512 chunks, the same node levels) and ten times the points
