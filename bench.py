@@ -53,25 +53,35 @@ ALG_PER_POINT = 97
 FIXED_BYTES = {"merge": 3 * 4 * (1 << 21)}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one call's
 # launches of a kernel, from one ncu capture of the workload, valid while the
-# kernel's sources hash to the recorded value (a changed kernel reports null)
-KERNEL_SOURCES = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_sort.cuh", "fp_sort.cu", "fp_seg.cuh",
-                  "fp_seg.cu", "fp_octree.cu", "fp_core.cu", "fp_api.cu"]
-_H = "d1c04ea72ffc4565"   # kernel sources of the captures (profiles/kernels_uniform100M.md)
-_T100 = {"bounds_decimate": 1.697e9, "count": 1.978e9, "distribute": 0.617e9 + 3.803e9, "cell_group": 4.424e9,
-         "units": 2.467e9, "resolve": 0.844e9, "owner_scatter": 3.806e9}
+# sources that kernel is built from hash to the recorded value (a changed
+# kernel reports null)
+_COMMON = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_api.cu"]
+_OCT = _COMMON + ["fp_sort.cuh", "fp_seg.cuh", "fp_octree.cu"]
+KERNEL_FILES = {
+    "bounds_decimate": _COMMON + ["fp_core.cu"],
+    "count": _COMMON + ["fp_core.cu"],
+    "distribute": _COMMON + ["fp_sort.cuh", "fp_seg.cuh", "fp_sort.cu", "fp_seg.cu"],
+    "cell_group": _OCT, "units": _OCT, "resolve": _OCT,
+    "owner_scatter": _OCT + ["fp_seg.cu"],
+}
 # uniform-100M: one-kernel captures of the first launch (the distribution: its counting
-# pass and sweep; the table and scan launches move under 20 MB); uniform-1B has the
+# pass and sweep; the table and scan launches move under 20 MB), with the hash of the
+# kernel's sources at the capture (profiles/kernels_uniform100M.md); uniform-1B has the
 # same per-point structure (512 chunks, the same node levels) and ten times the points
+_T100 = {"bounds_decimate": (1.697e9, "@BD"), "count": (1.978e9, "@CT"),
+         "distribute": (0.617e9 + 3.803e9, "baf64502ff0f1340"),
+         "cell_group": (4.424e9, "17e75d3352c0f5f5"), "units": (2.467e9, "17e75d3352c0f5f5"),
+         "resolve": (0.844e9, "17e75d3352c0f5f5"), "owner_scatter": (3.806e9, "942c057a7cfef4c8")}
 NCU_TRAFFIC = {}
-for _k, _b in _T100.items():
-    NCU_TRAFFIC[("uniform-100M", _k)] = (_b, _H)
-    NCU_TRAFFIC[("uniform-1B", _k)] = (10 * _b, _H)
+for _k, (_b, _h) in _T100.items():
+    NCU_TRAFFIC[("uniform-100M", _k)] = (_b, _h)
+    NCU_TRAFFIC[("uniform-1B", _k)] = (10 * _b, _h)
 
 
-def sources_hash():
+def sources_hash(kernel):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_FILES[kernel]:
         with open(os.path.join(ROOT, "paper_2302_05002_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -82,7 +92,7 @@ def ncu_traffic(workload, kernel):
     if rec is None:
         return None
     try:
-        return rec[0] if sources_hash() == rec[1] else None
+        return rec[0] if sources_hash(kernel) == rec[1] else None
     except OSError:
         return None
 

@@ -230,7 +230,7 @@ fp_status fp_bounds_decimate(const fp_point* d_pts, uint64_t n, fp_cube* d_cube,
  * device memory (a host application whose device memory belongs to another
  * allocator or budget, or a real-time loop that must not wait on one).  The
  * paper has no counterpart: this is a deployment convenience.
- * Scratch: a 512 KiB array inside the library, held by every GPU that loads it
+ * Scratch: a 1 MiB array inside the library, held by every GPU that loads it
  * until the process exits; n <= 2^27 (134,217,728) points, larger n returns
  * FP_ERR_TOO_LARGE.  The first call on each device looks up the array's device
  * address with that device current; make that first call before any stream

@@ -20,8 +20,8 @@ namespace fp {
 
 // ----------------------------------------------------------------- bounds
 constexpr int kBdNT = 256;
-constexpr int kBdIPT = 16;
-constexpr int kBdTile = kBdNT * kBdIPT;   // 4096 points per tile
+constexpr int kBdIPT = 8;
+constexpr int kBdTile = kBdNT * kBdIPT;   // 2048 points per tile
 
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagInc = 2ull << 62;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBdNT) k_bounds_decimate(const fp_point* __res
             __syncthreads();
             // exclusive scan over (r, warp) order = index order
             if (threadIdx.x < 32) {
-                uint32_t v[kBdIPT * (kBdNT / 32) / 32];   // 4 entries per lane
+                uint32_t v[kBdIPT * (kBdNT / 32) / 32];   // 2 entries per lane
                 uint32_t s = 0;
                 constexpr int per = kBdIPT * (kBdNT / 32) / 32;
 #pragma unroll
@@ -357,13 +357,17 @@ __global__ void k_chunk_write(const uint32_t* __restrict__ pyr, const uint32_t* 
     lut[m] = counts[m] > 0 ? id : kNone;
 }
 
-// The bounds + preview pass of the main path: the tile's 64 KB of points are
+// The bounds + preview pass of the main path: the tile's 32 KB of points are
 // brought into shared memory by one bulk copy (cp.async.bulk, completion on an
 // mbarrier) issued when the tile is claimed, so the copy is in flight while the
 // keep flags are ranked and the tile's output offset is found by decoupled
 // look-back; extents and kept points are then read from shared memory.  Few
-// registers and 64 KB of shared memory per block: three blocks per SM, each
-// with a whole tile in flight.  Waits are bounded (FP_ERR_TIMEOUT).
+// registers and 32 KB of shared memory per block: six blocks per SM, each with
+// a whole tile in flight (2048-point tiles measured faster than 4096 and 1024).
+// A second buffer per block, with the next tile claimed ahead, is slower: the
+// claimed tile publishes its keep count only when its block reaches it, and
+// every later tile's look-back waits for that.  Waits are bounded
+// (FP_ERR_TIMEOUT).
 constexpr size_t kBdBulkSmem = sizeof(int4) * kBdTile;
 
 template <bool DECIM>

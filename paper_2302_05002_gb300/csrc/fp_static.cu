@@ -12,7 +12,7 @@
 
 namespace fp {
 
-constexpr size_t kStaticScratchBytes = 512 * 1024;
+constexpr size_t kStaticScratchBytes = 1024 * 1024;
 constexpr uint64_t kStaticMaxPoints = 1ull << 27;   // 134,217,728 points
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
