@@ -68,7 +68,7 @@ KERNEL_FILES = {
 # pass and sweep; the table and scan launches move under 20 MB), with the hash of the
 # kernel's sources at the capture (profiles/kernels_uniform100M.md); uniform-1B has the
 # same per-point structure (512 chunks, the same node levels) and ten times the points
-_T100 = {"bounds_decimate": (1.697e9, "@BD"), "count": (1.978e9, "@CT"),
+_T100 = {"bounds_decimate": (1.698e9, "352f33370cec43e1"), "count": (1.977e9, "352f33370cec43e1"),
          "distribute": (0.617e9 + 3.803e9, "baf64502ff0f1340"),
          "cell_group": (4.424e9, "17e75d3352c0f5f5"), "units": (2.467e9, "17e75d3352c0f5f5"),
          "resolve": (0.844e9, "17e75d3352c0f5f5"), "owner_scatter": (3.806e9, "942c057a7cfef4c8")}
