@@ -94,13 +94,6 @@ fp_status check_params(const fp_params* p)
 // workspace view over a caller-provided (or library-held) buffer
 fp_status make_workspace(void* base, size_t bytes, size_t need, Workspace& ws) { return make_ws(base, bytes, need, ws); }
 
-size_t bounds_ws_bytes(uint64_t n, int num_sms)
-{
-    // block partials, one look-back word per tile, tile counter
-    const size_t nt = (size_t)((n + 4095) / 4096);
-    return Workspace::bytes_for({6 * 4 * (size_t)num_sms * 8, 8 * (nt ? nt : 1), 16});
-}
-
 }  // namespace fp
 
 using namespace fp;

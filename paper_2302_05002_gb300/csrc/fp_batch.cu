@@ -54,7 +54,7 @@ fp_status lanes_of_device(Lanes*& out)
 constexpr int kFusedMax = 256;
 constexpr int kFbNT = 256;
 constexpr int kFbIPT = 16;
-constexpr int kFbTile = kFbNT * kFbIPT;   // 4096 points: the preview tile of fp_bounds_decimate
+constexpr int kFbTile = kFbNT * kFbIPT;   // 4096 points per preview tile (the layout does not depend on it)
 constexpr int kFcTiles = 16;              // count work item: 16 tiles (65,536 points)
 
 struct FusedCloud {

@@ -533,6 +533,14 @@ __global__ void __launch_bounds__(kBdNT) k_bounds_bulk(const fp_point* __restric
 }
 
 // ----------------------------------------------------------------- host side
+// the carve of launch_bounds_decimate: block partials (grid <= 8 per SM), one
+// look-back word per tile, the tile counter
+size_t bounds_ws_bytes(uint64_t n, int num_sms)
+{
+    const size_t nt = (size_t)((n + kBdTile - 1) / kBdTile);
+    return Workspace::bytes_for({6 * 4 * (size_t)num_sms * 8, 8 * (nt ? nt : 1), 4 * sizeof(uint32_t)});
+}
+
 cudaError_t launch_bounds_decimate(const fp_point* pts, uint64_t n, fp_cube* cube, bool bounds, bool decim,
                                    uint64_t first, uint32_t modulus, fp_point* out, uint64_t out_cap,
                                    uint64_t* out_count, const Workspace& ws, cudaStream_t st)
