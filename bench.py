@@ -55,7 +55,7 @@ FIXED_BYTES = {"merge": 3 * 4 * (1 << 21)}
 # launches of a kernel, from one ncu capture of the workload, valid while the
 # sources that kernel is built from hash to the recorded value (a changed
 # kernel reports null)
-_COMMON = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh", "fp_api.cu"]
+_COMMON = ["fp_common.cuh", "fp_internal.cuh", "fp_scan.cuh"]   # (fp_api.cu: argument checks, no kernel)
 _OCT = _COMMON + ["fp_sort.cuh", "fp_seg.cuh", "fp_octree.cu"]
 KERNEL_FILES = {
     "bounds_decimate": _COMMON + ["fp_core.cu"],
@@ -68,10 +68,10 @@ KERNEL_FILES = {
 # pass and sweep; the table and scan launches move under 20 MB), with the hash of the
 # kernel's sources at the capture (profiles/kernels_uniform100M.md); uniform-1B has the
 # same per-point structure (512 chunks, the same node levels) and ten times the points
-_T100 = {"bounds_decimate": (1.698e9, "352f33370cec43e1"), "count": (1.977e9, "352f33370cec43e1"),
-         "distribute": (0.617e9 + 3.803e9, "baf64502ff0f1340"),
-         "cell_group": (4.424e9, "17e75d3352c0f5f5"), "units": (2.467e9, "17e75d3352c0f5f5"),
-         "resolve": (0.844e9, "17e75d3352c0f5f5"), "owner_scatter": (3.806e9, "942c057a7cfef4c8")}
+_T100 = {"bounds_decimate": (1.698e9, "745ecb4644c62907"), "count": (1.977e9, "745ecb4644c62907"),
+         "distribute": (0.617e9 + 3.803e9, "6f0641cb0d48e153"),
+         "cell_group": (4.424e9, "f33f4efb97ca77c1"), "units": (2.467e9, "f33f4efb97ca77c1"),
+         "resolve": (0.844e9, "f33f4efb97ca77c1"), "owner_scatter": (3.806e9, "78b841f4a17e80b4")}
 NCU_TRAFFIC = {}
 for _k, (_b, _h) in _T100.items():
     NCU_TRAFFIC[("uniform-100M", _k)] = (_b, _h)
